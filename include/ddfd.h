@@ -1,0 +1,211 @@
+/*
+ * ddfd.h -- C ABI of the GB300 (sm_103a) hot path of the adaptive domain
+ * decomposition FE/FD method for the stabilized time-dependent Maxwell
+ * system in conductive media (Kyhn, Lindstrom, Beilina, arXiv 2508.07780).
+ *
+ * The library time-steps the model problem of Sec. 5 (eq. model1; the same
+ * equation as eq. forward_prob of Sec. 2)
+ *
+ *     eps d_tt E + sigma d_t E - Lap E - grad div((eps - 1) E) = 0
+ *
+ * forward for the state E, backward for the adjoint lambda of eq.
+ * adjoint_prob (Sec. 3), driven by the detector residuals E - Eobs, and
+ * accumulates the gradient of the Tikhonov functional (eq.
+ * tikhonov_functional) with respect to eps and sigma (eq. gradeps, Sec. 4).
+ *
+ * Discretisation (all of it computed on the GPU):
+ *   - grid: n^3 nodes on [0,1]^3, h = 1/(n-1), node id i + n*(j + n*k),
+ *     x fastest, k = depth, top (incident, observed) face k = n-1;
+ *   - outer region: finite differences on the hexahedral grid (7-point
+ *     Laplacian, ghost-node Neumann closure, lumped trapezoid masses);
+ *   - inner FEM cube: node box [a,b]^3, a = (n - fem_n)/2 (integer division),
+ *     b = a + fem_n - 1, P1 elements on the six Kuhn tetrahedra of each cube,
+ *     lumped mass; FEM rows for nodes strictly inside the box;
+ *   - free (coefficient) nodes: [a+2, b-2]^3, listed x fastest; every other
+ *     node has eps = 1, sigma = 0 (eq. epsilon_sigma_constraint);
+ *   - explicit central time stepping, tau = cfl * h, E(0) = d_t E(0) = 0;
+ *   - boundary: Neumann flux P on the top face for steps n <= n1 (n1 =
+ *     floor(t1/tau + 1e-9)), first-order absorbing d_n E = -d_t E on the top
+ *     face afterwards and on the bottom face always, d_n E = 0 on the sides
+ *     (eq. model1); the absorbing set is configurable.
+ *
+ * Conventions:
+ *   - every call returns a ddfd_status; nothing is thrown across the ABI;
+ *   - on error, outputs are untouched and ddfd_last_error() holds a message;
+ *   - the caller owns every buffer it passes; host inputs are copied before
+ *     the call returns; device pointers must stay valid until the call
+ *     returns (the library synchronises its stream before returning from
+ *     every call that takes a caller buffer);
+ *   - one handle per thread; handles are independent;
+ *   - no CPU fallback: without a usable CUDA device ddfd_create fails with
+ *     DDFD_E_CUDA.
+ */
+#ifndef DDFD_H
+#define DDFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddfd_problem ddfd_problem; /* opaque; owns all its device memory */
+
+typedef enum {
+  DDFD_OK = 0,
+  DDFD_E_ARG = -1,       /* invalid argument or configuration */
+  DDFD_E_CFL = -2,       /* tau above the stability bound of the current coefficients */
+  DDFD_E_STATE = -3,     /* call out of order (adjoint before forward, ...) */
+  DDFD_E_CUDA = -4,      /* CUDA runtime error (message has the CUDA text) */
+  DDFD_E_OOM = -5,       /* device memory (or the configured budget) exhausted */
+  DDFD_E_NONFINITE = -6, /* a non-finite value appeared in a trace or gradient */
+  DDFD_E_TIMEOUT = -7,   /* a bounded device wait gave up */
+  DDFD_E_COEFF = -8      /* coefficient outside [1, eps_max] x [0, sig_max] or non-finite */
+} ddfd_status;
+
+enum { DDFD_FP64 = 0, DDFD_FP32 = 1 };           /* field precision; reductions are FP64 */
+enum { DDFD_SRC_GAUSS = 0, DDFD_SRC_SINE = 1 };  /* pulse shape, see ddfd_config */
+enum { DDFD_FEM_STENCIL = 0, DDFD_FEM_EBE = 1 };  /* FEM apply: Kuhn block stencil / element gather */
+enum {
+  DDFD_ABS_BOTTOM = 1, DDFD_ABS_TOP = 2, /* top: only after the source phase */
+  DDFD_ABS_X0 = 4, DDFD_ABS_X1 = 8, DDFD_ABS_Y0 = 16, DDFD_ABS_Y1 = 32
+};
+
+typedef struct {
+  int32_t n;             /* grid nodes per axis, 7 <= n <= 1024 */
+  int32_t fem_n;         /* FEM cube nodes per axis, 5 <= fem_n <= n - 2 */
+  int32_t n_steps;       /* Nt >= 1 time steps */
+  double cfl;            /* tau = cfl * h; 0 < cfl */
+  int32_t precision;     /* DDFD_FP64 or DDFD_FP32 */
+  int32_t fem_kind;      /* DDFD_FEM_STENCIL (default) or DDFD_FEM_EBE */
+  int32_t n_src;         /* incident plane waves, >= 1; J and g sum over them */
+  const double *src_dir; /* [n_src][3] propagation directions k (k_z < 0), or NULL
+                            for normal incidence k = (0,0,-1); copied */
+  int32_t source_kind;   /* DDFD_SRC_GAUSS: P(t) = sin(2 pi f (t-t0)) exp(-((t-t0)/w)^2);
+                            DDFD_SRC_SINE: the paper's eq. f, sin(2 pi f t) on (0, 1/f) */
+  double freq, t0, width;/* f, t0, w of the pulse */
+  double t1;             /* end of the source phase; < 0: pulse end (t0 + 3w, or 1/f)
+                            plus the largest oblique delay */
+  int32_t n_det;         /* detectors, >= 0 */
+  const int32_t *det_ij; /* [n_det][2] top-face node indices (i, j); copied */
+  uint32_t absorbing_faces; /* DDFD_ABS_* bits; default BOTTOM|TOP */
+  double gamma_eps, gamma_sig; /* Tikhonov regularisation parameters (>= 0) */
+  double z_delta_frac;   /* observation taper z_delta: 1 up to T - d, cosine to 0 at T,
+                            d = frac * T; 0 disables it */
+  double eps_max, sig_max; /* coefficient bounds checked by ddfd_set_coeffs */
+  int32_t n_snapshots;   /* 0: keep E on the free nodes for every step in device memory;
+                            > 0: binomial checkpointing with this many full-state
+                            snapshots, the adjoint replays forward segments */
+  int32_t cfl_check;     /* nonzero: estimate the stability bound by power iteration
+                            at ddfd_set_coeffs and fail with DDFD_E_CFL above it */
+  int64_t mem_budget;    /* device bytes the handle may allocate; 0 = no limit */
+  void *stream;          /* cudaStream_t for all work, or NULL for the default stream */
+} ddfd_config;
+
+/* Fill *cfg with defaults: cfl 0.3, FP64, stencil FEM, 1 normal-incidence
+ * source, Gaussian pulse f = 2, t0 = 0.75, w = 0.25, t1 auto, absorbing
+ * bottom|top, gammas 0, z_delta_frac 0.1, eps_max 100, sig_max 100, no
+ * snapshots (full history), cfl_check 0, no budget, default stream.  n,
+ * fem_n, n_steps and the detectors are left zero. */
+void ddfd_config_default(ddfd_config *cfg);
+
+/* Validate *cfg and allocate a handle with vacuum coefficients (eps = 1,
+ * sigma = 0).  Errors: DDFD_E_ARG (bad sizes, detector off the grid,
+ * direction with k_z >= 0), DDFD_E_OOM, DDFD_E_CUDA.  *out is set only on
+ * success. */
+int ddfd_create(const ddfd_config *cfg, ddfd_problem **out);
+
+/* Release the handle and all its device memory.  NULL is allowed. */
+void ddfd_destroy(ddfd_problem *p);
+
+/* Message of the last failing call on this handle ("" if none).  Valid until
+ * the next call on the handle. */
+const char *ddfd_last_error(const ddfd_problem *p);
+
+/* Message of the last ddfd_create failure in this thread. */
+const char *ddfd_create_error(void);
+
+/* Nodal coefficients on the free nodes (eq. epsilon_sigma_constraint;
+ * the unknowns of the inverse problem, eq. inverse_problem), in free-node
+ * order (x fastest over [a+2, b-2]^3), (fem_n - 4)^3 doubles each, host
+ * memory.  eps0/sig0 are the regularisation centres of eq.
+ * tikhonov_functional; NULL means eps0 = 1, sig0 = 0.  Checks
+ * 1 <= eps <= eps_max and 0 <= sigma <= sig_max (DDFD_E_COEFF).  Builds the
+ * per-node step coefficients on the device and invalidates any forward or
+ * adjoint state.  With cfl_check, fails with DDFD_E_CFL if tau exceeds
+ * 2/sqrt(lambda_max(M_eps^-1 K)). */
+int ddfd_set_coeffs(ddfd_problem *p, const double *eps, const double *sig,
+                    const double *eps0, const double *sig0);
+/* Same, with device pointers (same layout; eps0/sig0 may be NULL). */
+int ddfd_set_coeffs_dev(ddfd_problem *p, const double *eps, const double *sig,
+                        const double *eps0, const double *sig0);
+
+/* Forward solve for every source (eq. model1, Sec. 5): E^0 = E^-1 = 0, then
+ * Nt explicit steps.  Records the detector trace and keeps what the adjoint
+ * needs (E on the free nodes, or checkpoints).  trace_out, if not NULL,
+ * receives [n_src][n_steps + 1][n_det][3] doubles (host), E at the detector
+ * nodes for t_0 .. t_Nt.  Errors: DDFD_E_NONFINITE if the trace holds a
+ * non-finite value, DDFD_E_CUDA. */
+int ddfd_forward(ddfd_problem *p, double *trace_out);
+/* Same; trace_out (may be NULL) is a device pointer. */
+int ddfd_forward_dev(ddfd_problem *p, double *trace_out);
+
+/* Tikhonov functional (eq. tikhonov_functional) of the last forward run:
+ * J = tau/2 sum_{s, n=1..Nt} z(t_n) sum_d |E^n_d - Eobs^n_d|^2
+ *   + gamma_eps/2 sum_i m_i (eps_i - eps0_i)^2 + gamma_sig/2 sum_i m_i (sig_i - sig0_i)^2,
+ * reduced in FP64.  eobs has the trace layout (host).  Requires a forward
+ * run (DDFD_E_STATE). */
+int ddfd_functional(ddfd_problem *p, const double *eobs, double *J);
+/* Same; eobs is a device pointer, *J a host double. */
+int ddfd_functional_dev(ddfd_problem *p, const double *eobs, double *J);
+
+/* Adjoint solve for every source (eq. adjoint_prob, Sec. 3, as the exact
+ * transpose of the discrete forward recursion), backward from t_Nt with zero
+ * terminal data, driven by j^k = tau z(t_k) (E^k - Eobs^k) at the detectors.
+ * The gradient time integrals are accumulated in the same kernels.  eobs:
+ * trace layout, host.  Requires a forward run (DDFD_E_STATE). */
+int ddfd_adjoint(ddfd_problem *p, const double *eobs);
+/* Same; eobs is a device pointer. */
+int ddfd_adjoint_dev(ddfd_problem *p, const double *eobs);
+
+/* Gradient of the discrete J with respect to the free-node eps and sigma
+ * (eq. gradeps, Sec. 4, taken as the exact derivative of the discrete
+ * functional), summed over sources, FP64, free-node order, host.  Requires
+ * an adjoint run (DDFD_E_STATE).  DDFD_E_NONFINITE if non-finite. */
+int ddfd_gradient(ddfd_problem *p, double *g_eps, double *g_sig);
+/* Same; outputs are device pointers. */
+int ddfd_gradient_dev(ddfd_problem *p, double *g_eps, double *g_sig);
+
+/* Sizes and bookkeeping of a handle. */
+typedef struct {
+  int32_t n, fem_n, n_free, n_det, n_src, n_steps;
+  int32_t a, b, switch_step;   /* FEM box [a,b]; last source step n1 (per source 0) */
+  double h, tau;
+  int64_t device_bytes;        /* bytes allocated by the handle */
+  int64_t kernel_launches;     /* kernels launched by the handle so far */
+  int64_t forward_steps;       /* forward steps executed so far (replays included) */
+} ddfd_info;
+int ddfd_get_info(const ddfd_problem *p, ddfd_info *info);
+
+/* Device time of the last forward / adjoint step loops, measured with CUDA
+ * events recorded on the handle's stream around the back-to-back step
+ * kernels (all sources), and the number of step kernels in each loop.  The
+ * average step-kernel duration is loop_ms / steps.  Zero before a run. */
+typedef struct {
+  double forward_loop_ms, adjoint_loop_ms;
+  int64_t forward_step_kernels, adjoint_step_kernels;
+} ddfd_timing;
+int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t);
+
+/* Capture full fields for testing: before ddfd_forward / ddfd_adjoint, name
+ * up to 16 step indices; the forward then keeps E^n and the adjoint mu^n
+ * (the multiplier of the step equations; lambda ~ mu / tau) of source 0 at
+ * those steps.  ddfd_get_capture copies capture idx of kind 0 (E) or 1 (mu)
+ * as 3 * n^3 doubles (component-major, node order) to host memory. */
+int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps);
+int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDFD_H */

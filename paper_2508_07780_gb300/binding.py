@@ -1,0 +1,288 @@
+"""ctypes binding of the ddfd C ABI (include/ddfd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+There is no fallback; if libddfd.so is missing or no GPU is usable, calls fail
+with an exception.  The names mirror the C entry points; ``Problem`` wraps a
+handle and converts numpy arrays (host calls) or torch CUDA tensors (the
+``*_dev`` calls, by data pointer) to the C layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_uint32, c_void_p, c_char_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddfd.so")
+
+DDFD_OK, DDFD_E_ARG, DDFD_E_CFL, DDFD_E_STATE = 0, -1, -2, -3
+DDFD_E_CUDA, DDFD_E_OOM, DDFD_E_NONFINITE, DDFD_E_TIMEOUT, DDFD_E_COEFF = -4, -5, -6, -7, -8
+DDFD_FP64, DDFD_FP32 = 0, 1
+DDFD_SRC_GAUSS, DDFD_SRC_SINE = 0, 1
+DDFD_FEM_STENCIL, DDFD_FEM_EBE = 0, 1
+DDFD_ABS_BOTTOM, DDFD_ABS_TOP, DDFD_ABS_X0, DDFD_ABS_X1, DDFD_ABS_Y0, DDFD_ABS_Y1 = 1, 2, 4, 8, 16, 32
+
+STATUS_NAMES = {0: "DDFD_OK", -1: "DDFD_E_ARG", -2: "DDFD_E_CFL", -3: "DDFD_E_STATE",
+                -4: "DDFD_E_CUDA", -5: "DDFD_E_OOM", -6: "DDFD_E_NONFINITE",
+                -7: "DDFD_E_TIMEOUT", -8: "DDFD_E_COEFF"}
+
+# Every entry point declared in include/ddfd.h.
+ABI_SYMBOLS = (
+    "ddfd_config_default", "ddfd_create", "ddfd_destroy", "ddfd_last_error",
+    "ddfd_create_error", "ddfd_set_coeffs", "ddfd_set_coeffs_dev", "ddfd_forward",
+    "ddfd_forward_dev", "ddfd_functional", "ddfd_functional_dev", "ddfd_adjoint",
+    "ddfd_adjoint_dev", "ddfd_gradient", "ddfd_gradient_dev", "ddfd_get_info",
+    "ddfd_set_capture", "ddfd_get_capture", "ddfd_get_timing",
+)
+
+
+class ddfd_config(ctypes.Structure):
+    _fields_ = [
+        ("n", c_int32), ("fem_n", c_int32), ("n_steps", c_int32), ("cfl", c_double),
+        ("precision", c_int32), ("fem_kind", c_int32), ("n_src", c_int32),
+        ("src_dir", POINTER(c_double)), ("source_kind", c_int32), ("freq", c_double),
+        ("t0", c_double), ("width", c_double), ("t1", c_double), ("n_det", c_int32),
+        ("det_ij", POINTER(c_int32)), ("absorbing_faces", c_uint32), ("gamma_eps", c_double),
+        ("gamma_sig", c_double), ("z_delta_frac", c_double), ("eps_max", c_double),
+        ("sig_max", c_double), ("n_snapshots", c_int32), ("cfl_check", c_int32),
+        ("mem_budget", c_int64), ("stream", c_void_p),
+    ]
+
+
+class ddfd_info(ctypes.Structure):
+    _fields_ = [
+        ("n", c_int32), ("fem_n", c_int32), ("n_free", c_int32), ("n_det", c_int32),
+        ("n_src", c_int32), ("n_steps", c_int32), ("a", c_int32), ("b", c_int32),
+        ("switch_step", c_int32), ("h", c_double), ("tau", c_double),
+        ("device_bytes", c_int64), ("kernel_launches", c_int64), ("forward_steps", c_int64),
+    ]
+
+
+class ddfd_timing(ctypes.Structure):
+    _fields_ = [
+        ("forward_loop_ms", c_double), ("adjoint_loop_ms", c_double),
+        ("forward_step_kernels", c_int64), ("adjoint_step_kernels", c_int64),
+    ]
+
+
+class DDFDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libddfd.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2508_07780_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    dp = POINTER(c_double)
+    lib.ddfd_config_default.argtypes = [POINTER(ddfd_config)]
+    lib.ddfd_config_default.restype = None
+    lib.ddfd_create.argtypes = [POINTER(ddfd_config), POINTER(c_void_p)]
+    lib.ddfd_destroy.argtypes = [P]
+    lib.ddfd_destroy.restype = None
+    lib.ddfd_last_error.argtypes = [P]
+    lib.ddfd_last_error.restype = c_char_p
+    lib.ddfd_create_error.argtypes = []
+    lib.ddfd_create_error.restype = c_char_p
+    for name in ("ddfd_set_coeffs", "ddfd_set_coeffs_dev"):
+        getattr(lib, name).argtypes = [P, P, P, P, P]
+    for name in ("ddfd_forward", "ddfd_forward_dev"):
+        getattr(lib, name).argtypes = [P, P]
+    for name in ("ddfd_functional", "ddfd_functional_dev"):
+        getattr(lib, name).argtypes = [P, P, dp]
+    for name in ("ddfd_adjoint", "ddfd_adjoint_dev"):
+        getattr(lib, name).argtypes = [P, P]
+    for name in ("ddfd_gradient", "ddfd_gradient_dev"):
+        getattr(lib, name).argtypes = [P, P, P]
+    lib.ddfd_get_info.argtypes = [P, POINTER(ddfd_info)]
+    lib.ddfd_get_timing.argtypes = [P, POINTER(ddfd_timing)]
+    lib.ddfd_set_capture.argtypes = [P, c_int32, P]
+    lib.ddfd_get_capture.argtypes = [P, c_int32, c_int32, P]
+    for name in ABI_SYMBOLS:
+        if name not in ("ddfd_config_default", "ddfd_destroy", "ddfd_last_error",
+                        "ddfd_create_error"):
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Host numpy array or torch tensor -> void pointer (None stays NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(c_void_p)
+    return c_void_p(a.data_ptr())
+
+
+def _host(a, dtype, count=None):
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if count is not None and arr.size != count:
+        raise ValueError(f"expected {count} values, got {arr.size}")
+    return arr
+
+
+def _dev(t, count=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("device arguments must be contiguous float64 CUDA tensors")
+    if count is not None and t.numel() != count:
+        raise ValueError(f"expected {count} values, got {t.numel()}")
+    return t
+
+
+class Problem:
+    """One ddfd handle.  Keyword arguments are ddfd_config fields; src_dir and
+    det_ij are arrays ([n_src][3] floats, [n_det][2] ints)."""
+
+    def __init__(self, **kw):
+        lib = load_library()
+        self._lib = lib
+        cfg = ddfd_config()
+        lib.ddfd_config_default(ctypes.byref(cfg))
+        self._keep = []
+        for k, v in kw.items():
+            if k == "src_dir":
+                if v is not None:
+                    arr = _host(v, np.float64).reshape(-1, 3)
+                    self._keep.append(arr)
+                    cfg.src_dir = arr.ctypes.data_as(POINTER(c_double))
+                    cfg.n_src = arr.shape[0]
+            elif k == "det_ij":
+                arr = _host(v, np.int32).reshape(-1, 2)
+                self._keep.append(arr)
+                cfg.det_ij = arr.ctypes.data_as(POINTER(c_int32))
+                cfg.n_det = arr.shape[0]
+            elif k == "stream":
+                cfg.stream = c_void_p(v)
+            elif k == "precision" and isinstance(v, str):
+                cfg.precision = DDFD_FP32 if v == "fp32" else DDFD_FP64
+            else:
+                setattr(cfg, k, v)
+        self.cfg = cfg
+        h = c_void_p()
+        st = lib.ddfd_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != DDFD_OK:
+            raise DDFDError(st, lib.ddfd_create_error().decode())
+        self._h = h
+        self.info = self.get_info()
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, st):
+        if st != DDFD_OK:
+            raise DDFDError(st, self._lib.ddfd_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ddfd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def n_free(self):
+        return self.info.n_free
+
+    @property
+    def trace_shape(self):
+        i = self.info
+        return (i.n_src, i.n_steps + 1, i.n_det, 3)
+
+    def get_info(self):
+        inf = ddfd_info()
+        self._check(self._lib.ddfd_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def get_timing(self):
+        t = ddfd_timing()
+        self._check(self._lib.ddfd_get_timing(self._h, ctypes.byref(t)))
+        return t
+
+    # -- host entry points ------------------------------------------------------
+    def set_coeffs(self, eps, sig, eps0=None, sig0=None):
+        nf = self.n_free
+        a = [_host(x, np.float64, nf) if x is not None else None for x in (eps, sig, eps0, sig0)]
+        self._check(self._lib.ddfd_set_coeffs(self._h, *[_ptr(x) for x in a]))
+
+    def forward(self, want_trace=True):
+        out = np.empty(self.trace_shape) if want_trace else None
+        self._check(self._lib.ddfd_forward(self._h, _ptr(out)))
+        return out
+
+    def functional(self, eobs):
+        e = _host(eobs, np.float64, int(np.prod(self.trace_shape)))
+        J = c_double()
+        self._check(self._lib.ddfd_functional(self._h, _ptr(e), ctypes.byref(J)))
+        return J.value
+
+    def adjoint(self, eobs):
+        e = _host(eobs, np.float64, int(np.prod(self.trace_shape)))
+        self._check(self._lib.ddfd_adjoint(self._h, _ptr(e)))
+
+    def gradient(self):
+        ge = np.empty(self.n_free)
+        gs = np.empty(self.n_free)
+        self._check(self._lib.ddfd_gradient(self._h, _ptr(ge), _ptr(gs)))
+        return ge, gs
+
+    # -- device entry points (torch float64 CUDA tensors) ------------------------
+    def set_coeffs_dev(self, eps, sig, eps0=None, sig0=None):
+        nf = self.n_free
+        a = [_dev(x, nf) if x is not None else None for x in (eps, sig, eps0, sig0)]
+        self._check(self._lib.ddfd_set_coeffs_dev(self._h, *[_ptr(x) for x in a]))
+
+    def forward_dev(self, trace_out=None):
+        if trace_out is not None:
+            _dev(trace_out, int(np.prod(self.trace_shape)))
+        self._check(self._lib.ddfd_forward_dev(self._h, _ptr(trace_out)))
+        return trace_out
+
+    def functional_dev(self, eobs):
+        _dev(eobs, int(np.prod(self.trace_shape)))
+        J = c_double()
+        self._check(self._lib.ddfd_functional_dev(self._h, _ptr(eobs), ctypes.byref(J)))
+        return J.value
+
+    def adjoint_dev(self, eobs):
+        _dev(eobs, int(np.prod(self.trace_shape)))
+        self._check(self._lib.ddfd_adjoint_dev(self._h, _ptr(eobs)))
+
+    def gradient_dev(self, g_eps, g_sig):
+        _dev(g_eps, self.n_free)
+        _dev(g_sig, self.n_free)
+        self._check(self._lib.ddfd_gradient_dev(self._h, _ptr(g_eps), _ptr(g_sig)))
+
+    # -- test hooks -------------------------------------------------------------
+    def set_capture(self, steps):
+        arr = _host(list(steps), np.int32)
+        self._check(self._lib.ddfd_set_capture(self._h, len(arr), _ptr(arr) if len(arr) else None))
+        self._cap = list(int(s) for s in arr)
+
+    def get_capture(self, kind, idx):
+        n = self.info.n
+        out = np.empty(3 * n ** 3)
+        self._check(self._lib.ddfd_get_capture(self._h, kind, idx, _ptr(out)))
+        return out.reshape(3, n ** 3)

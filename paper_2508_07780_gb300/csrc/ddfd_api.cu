@@ -1,0 +1,798 @@
+// Host driver of the ddfd C ABI (include/ddfd.h): configuration checks, the
+// call-order state machine, device memory, the incident-source setup and the
+// enqueueing of the step kernels.  All arithmetic of the method runs in the
+// kernels of ddfd_step.cu and ddfd_aux.cu; the host only prepares per-step
+// scalars (pulse value, absorbing-face set) and small tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ddfd_internal.h"
+
+using namespace ddfd;
+
+namespace {
+thread_local std::string g_create_err;
+constexpr int kMaxCapture = 16;
+constexpr double kPi = 3.141592653589793;
+
+enum { ST_READY = 0, ST_FORWARD = 1, ST_ADJOINT = 2 };
+
+double pulse_host(int kind, double f, double t0, double w, double t) {
+  if (kind == DDFD_SRC_GAUSS) {
+    const double s = t - t0, q = s / w;
+    return std::sin(2.0 * kPi * f * s) * std::exp(-q * q);
+  }
+  return (t > 0.0 && t < 1.0 / f) ? std::sin(2.0 * kPi * f * t) : 0.0;
+}
+}  // namespace
+
+struct ddfd_problem {
+  ddfd_config cfg{};
+  std::vector<double> src_dir;
+  std::vector<int32_t> det_ij;
+  std::string err;
+  int n = 0, fem_n = 0, a = 0, b = 0, f0 = 0, nf = 0, Nt = 0, n_src = 0, n_det = 0;
+  long long n_free = 0, nn = 0;
+  double h = 0, tau = 0;
+  int fp32 = 0;
+  size_t esz = 8;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;
+  int64_t bytes = 0;
+  void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr};
+  void *s_box = nullptr, *c_box = nullptr, *hist = nullptr;
+  double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
+  double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
+  double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
+  int *det_node = nullptr, *det_ptr = nullptr, *det_list = nullptr, *flag = nullptr;
+  std::vector<double> ptab;  // [n_src][Nt] pulse value P(t_n) (normal incidence), 0 after n1
+  std::vector<int> n1, oblique;
+  std::vector<double> pol;   // [n_src][3]
+  std::vector<int> cap_steps;
+  void *capE = nullptr, *capMu = nullptr;
+  int state = ST_READY;
+  int64_t launches = 0, fwd_steps = 0;
+  int kz = 16;
+  int n_part = 256;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double fwd_ms = 0.0, adj_ms = 0.0;
+  int64_t fwd_kernels = 0, adj_kernels = 0;
+};
+
+namespace {
+
+int fail(ddfd_problem *p, int code, const std::string &m) {
+  p->err = m;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(p, DDFD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+int dalloc(ddfd_problem *p, size_t bytes, void **out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (p->cfg.mem_budget > 0 && p->bytes + (int64_t)bytes > p->cfg.mem_budget)
+    return fail(p, DDFD_E_OOM, "device memory budget exceeded (" + std::to_string(p->bytes + bytes) +
+                                   " > " + std::to_string(p->cfg.mem_budget) + " bytes)");
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return fail(p, DDFD_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*out);
+  p->bytes += (int64_t)bytes;
+  return DDFD_OK;
+}
+
+template <typename X>
+int dalloc_t(ddfd_problem *p, size_t count, X **out) {
+  void *v = nullptr;
+  int st = dalloc(p, count * sizeof(X), &v);
+  *out = (X *)v;
+  return st;
+}
+
+uint32_t faces_at(const ddfd_problem *p, int s, long long step) {
+  uint32_t m = p->cfg.absorbing_faces & ~(uint32_t)DDFD_ABS_TOP;
+  if ((p->cfg.absorbing_faces & DDFD_ABS_TOP) && step > p->n1[s]) m |= DDFD_ABS_TOP;
+  return m;
+}
+
+int validate(const ddfd_config *c, std::string *m) {
+  if (c->n < 7 || c->n > 1024) return *m = "n must be in [7, 1024]", DDFD_E_ARG;
+  if (c->fem_n < 5 || c->fem_n > c->n - 2) return *m = "fem_n must be in [5, n-2]", DDFD_E_ARG;
+  if (c->n_steps < 1) return *m = "n_steps must be >= 1", DDFD_E_ARG;
+  if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) return *m = "cfl must be positive", DDFD_E_ARG;
+  if (c->precision != DDFD_FP64 && c->precision != DDFD_FP32) return *m = "bad precision", DDFD_E_ARG;
+  if (c->fem_kind != DDFD_FEM_STENCIL) return *m = "fem_kind: only DDFD_FEM_STENCIL is built", DDFD_E_ARG;
+  if (c->n_src < 1) return *m = "n_src must be >= 1", DDFD_E_ARG;
+  if (c->source_kind != DDFD_SRC_GAUSS && c->source_kind != DDFD_SRC_SINE) return *m = "bad source_kind", DDFD_E_ARG;
+  if (!(c->freq > 0.0) || (c->source_kind == DDFD_SRC_GAUSS && !(c->width > 0.0)))
+    return *m = "pulse frequency and width must be positive", DDFD_E_ARG;
+  if (c->n_det < 0 || (c->n_det > 0 && !c->det_ij)) return *m = "bad detector list", DDFD_E_ARG;
+  for (int d = 0; d < c->n_det; ++d) {
+    const int i = c->det_ij[2 * d], j = c->det_ij[2 * d + 1];
+    if (i < 0 || j < 0 || i >= c->n || j >= c->n) return *m = "detector off the top face", DDFD_E_ARG;
+  }
+  if (c->absorbing_faces > 63u) return *m = "bad absorbing_faces mask", DDFD_E_ARG;
+  if (c->gamma_eps < 0 || c->gamma_sig < 0) return *m = "gammas must be >= 0", DDFD_E_ARG;
+  if (!(c->z_delta_frac >= 0.0 && c->z_delta_frac < 1.0)) return *m = "z_delta_frac must be in [0,1)", DDFD_E_ARG;
+  if (!(c->eps_max >= 1.0) || !(c->sig_max >= 0.0)) return *m = "bad coefficient bounds", DDFD_E_ARG;
+  if (c->n_snapshots != 0) return *m = "n_snapshots > 0 (checkpointing) is not built", DDFD_E_ARG;
+  if (c->mem_budget < 0) return *m = "mem_budget must be >= 0", DDFD_E_ARG;
+  if (c->src_dir)
+    for (int s = 0; s < c->n_src; ++s) {
+      const double *k = c->src_dir + 3 * s;
+      const double nrm = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+      if (!(nrm > 0.0) || !(k[2] / nrm < -1e-6)) return *m = "source directions need k_z < 0", DDFD_E_ARG;
+    }
+  return DDFD_OK;
+}
+
+// Incidence geometry of each source: polarisation, delays over the top face,
+// switch step, pulse table.  A plane wave with direction k reaches top node x
+// after k.(x - x_c) + Delta (x_c the face centre, Delta making the smallest
+// delay zero); the flux is p P(t - delay), p = normalise(y - (y.k) k).
+int setup_sources(ddfd_problem *p, std::vector<double> *delay_host) {
+  const int n = p->n, Nt = p->Nt;
+  const ddfd_config &c = p->cfg;
+  p->n1.assign(p->n_src, 0);
+  p->oblique.assign(p->n_src, 0);
+  p->pol.assign(3 * p->n_src, 0.0);
+  p->ptab.assign((size_t)p->n_src * Nt, 0.0);
+  delay_host->assign((size_t)p->n_src * n * n, 0.0);
+  for (int s = 0; s < p->n_src; ++s) {
+    double k[3] = {0.0, 0.0, -1.0};
+    if (!p->src_dir.empty()) {
+      const double *d = p->src_dir.data() + 3 * s;
+      const double nrm = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      for (int q = 0; q < 3; ++q) k[q] = d[q] / nrm;
+    }
+    double pv[3] = {-k[1] * k[0], 1.0 - k[1] * k[1], -k[1] * k[2]};
+    double pn = std::sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
+    if (pn < 1e-12) {
+      pv[0] = 1.0 - k[0] * k[0];
+      pv[1] = -k[0] * k[1];
+      pv[2] = -k[0] * k[2];
+      pn = std::sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
+    }
+    for (int q = 0; q < 3; ++q) p->pol[3 * s + q] = pv[q] / pn;
+    double *dl = delay_host->data() + (size_t)s * n * n;
+    double dmax = -1e300;
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double proj = k[0] * (i * p->h - 0.5) + k[1] * (j * p->h - 0.5) + k[2] * 0.0;
+        dl[i + n * j] = proj;
+        dmax = std::max(dmax, -proj);
+      }
+    bool any = false;
+    double dbig = 0.0;
+    for (int q = 0; q < n * n; ++q) {
+      dl[q] += dmax;
+      if (dl[q] != 0.0) any = true;
+      dbig = std::max(dbig, dl[q]);
+    }
+    const bool ypol = p->pol[3 * s] == 0.0 && p->pol[3 * s + 1] == 1.0 && p->pol[3 * s + 2] == 0.0;
+    p->oblique[s] = (any || !ypol) ? 1 : 0;
+    const double pend = c.source_kind == DDFD_SRC_GAUSS ? c.t0 + 3.0 * c.width : 1.0 / c.freq;
+    const double t1 = c.t1 >= 0.0 ? c.t1 : pend + dbig;
+    const double q = std::floor(t1 / p->tau + 1e-9);
+    p->n1[s] = q > 2e9 ? 2000000000 : (int)q;
+    for (int st = 0; st < Nt; ++st)
+      p->ptab[(size_t)s * Nt + st] =
+          st <= p->n1[s] ? pulse_host(c.source_kind, c.freq, c.t0, c.width, st * p->tau) : 0.0;
+  }
+  return DDFD_OK;
+}
+
+template <typename T>
+StepParams<T> base_params(const ddfd_problem *p) {
+  StepParams<T> P;
+  std::memset(&P, 0, sizeof(P));
+  P.n = p->n;
+  P.a = p->a;
+  P.b = p->b;
+  P.f0 = p->f0;
+  P.nf = p->nf;
+  P.kz = p->kz;
+  P.cs = p->nn;
+  P.s_box = (const T *)p->s_box;
+  P.c_box = (const T *)p->c_box;
+  P.fem_n = p->fem_n;
+  P.r2 = (T)((p->tau / p->h) * (p->tau / p->h));
+  P.cb = (T)(p->tau / p->h);
+  P.src_scale = 2.0 * p->tau * p->tau / p->h;
+  P.pulse_kind = p->cfg.source_kind;
+  P.freq = p->cfg.freq;
+  P.t0 = p->cfg.t0;
+  P.width = p->cfg.width;
+  P.n_det = p->n_det;
+  P.det_node = p->det_node;
+  P.det_ptr = p->det_ptr;
+  P.det_list = p->det_list;
+  P.inv_h3 = 1.0 / (p->h * p->h * p->h);
+  P.tau2 = p->tau * p->tau;
+  P.n_free = p->n_free;
+  P.gacc_e = p->gacc;
+  P.gacc_s = p->gacc + p->n_free;
+  return P;
+}
+
+int capture_slot(const ddfd_problem *p, int step) {
+  for (size_t q = 0; q < p->cap_steps.size(); ++q)
+    if (p->cap_steps[q] == step) return (int)q;
+  return -1;
+}
+
+template <typename T>
+int enqueue_forward(ddfd_problem *p) {
+  const size_t fbytes = 3 * (size_t)p->nn * sizeof(T);
+  const int Nt = p->Nt;
+  float ms_total = 0.0f;
+  for (int s = 0; s < p->n_src; ++s) {
+    CK(cudaMemsetAsync(p->E[0], 0, fbytes, p->stream));
+    CK(cudaMemsetAsync(p->E[1], 0, fbytes, p->stream));
+    if (s == 0) {
+      const int sl = capture_slot(p, 0);
+      if (sl >= 0) CK(cudaMemsetAsync((char *)p->capE + sl * fbytes, 0, fbytes, p->stream));
+    }
+    void *cur = p->E[1], *old = p->E[0];
+    StepParams<T> P = base_params<T>(p);
+    P.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
+    P.oblique = p->oblique[s];
+    for (int q = 0; q < 3; ++q) P.pol[q] = p->pol[3 * s + q];
+    CK(cudaEventRecord(p->ev[0], p->stream));
+    for (int st = 0; st < Nt; ++st) {
+      P.cur = (const T *)cur;
+      P.old = (T *)old;
+      P.abs_now = faces_at(p, s, st);
+      P.src_on = st <= p->n1[s] ? 1 : 0;
+      P.t_n = st * p->tau;
+      P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
+      P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
+      P.hist_w = (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
+      launch_forward_step<T>(P, p->stream);
+      ++p->launches;
+      std::swap(cur, old);
+      if (s == 0) {
+        const int sl = capture_slot(p, st + 1);
+        if (sl >= 0) CK(cudaMemcpyAsync((char *)p->capE + sl * fbytes, cur, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+      }
+    }
+    CK(cudaEventRecord(p->ev[1], p->stream));
+    CK(cudaGetLastError());
+    launch_gather_trace(cur, p->fp32, p->nn, p->n_det, p->det_node,
+                        p->trace + ((size_t)s * (Nt + 1) + Nt) * p->n_det * 3, p->stream);
+    if (p->n_det > 0) ++p->launches;
+    p->fwd_steps += Nt;
+    CK(cudaEventSynchronize(p->ev[1]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
+    ms_total += ms;
+  }
+  CK(cudaGetLastError());
+  p->fwd_ms = ms_total;
+  p->fwd_kernels = (int64_t)Nt * p->n_src;
+  return DDFD_OK;
+}
+
+template <typename T>
+int enqueue_adjoint(ddfd_problem *p) {
+  const size_t fbytes = 3 * (size_t)p->nn * sizeof(T);
+  const int Nt = p->Nt;
+  CK(cudaMemsetAsync(p->gacc, 0, 2 * (size_t)p->n_free * sizeof(double), p->stream));
+  float ms_total = 0.0f;
+  for (int s = 0; s < p->n_src; ++s) {
+    CK(cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream));
+    CK(cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream));
+    void *cur = p->Mu[1], *old = p->Mu[0];  // mu^Nt, mu^{Nt+1}
+    StepParams<T> P = base_params<T>(p);
+    CK(cudaEventRecord(p->ev[2], p->stream));
+    for (int k = Nt; k >= 1; --k) {
+      P.cur = (const T *)cur;
+      P.old = (T *)old;
+      P.abs_now = faces_at(p, s, k - 1);
+      P.abs_next = faces_at(p, s, k + 1);
+      P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
+      P.hist_r = (const T *)p->hist + ((size_t)s * (Nt + 1) + k) * 3 * p->n_free;
+      launch_adjoint_step<T>(P, p->stream);
+      ++p->launches;
+      std::swap(cur, old);
+      if (s == 0) {
+        const int sl = capture_slot(p, k - 1);
+        if (sl >= 0) CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, cur, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+      }
+    }
+    CK(cudaEventRecord(p->ev[3], p->stream));
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(p->ev[3]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]));
+    ms_total += ms;
+  }
+  p->adj_ms = ms_total;
+  p->adj_kernels = (int64_t)Nt * p->n_src;
+  return DDFD_OK;
+}
+
+int sync_check(ddfd_problem *p) {
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->stream));
+  return DDFD_OK;
+}
+
+int read_flag(ddfd_problem *p, int *out) {
+  CK(cudaMemcpyAsync(out, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return DDFD_OK;
+}
+
+// Power iteration for lambda_max of M_eps^-1 K (units 1/h^2 folded in).
+int cfl_check(ddfd_problem *p) {
+  const long long cnt = 3 * p->nn;
+  for (int q = 0; q < 2; ++q)
+    if (!p->pw[q]) {
+      int st = dalloc_t(p, (size_t)cnt, &p->pw[q]);
+      if (st) return st;
+    }
+  std::vector<double> x0((size_t)cnt);
+  uint64_t r = 0x9E3779B97F4A7C15ull;
+  for (long long q = 0; q < cnt; ++q) {
+    r ^= r << 13;
+    r ^= r >> 7;
+    r ^= r << 17;
+    x0[q] = (double)(r >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+  CK(cudaMemcpyAsync(p->pw[0], x0.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  launch_norm2(p->pw[0], cnt, p->part, p->n_part, p->stream);
+  launch_sum(p->part, p->n_part, p->scal, p->stream);
+  launch_scale(p->pw[0], cnt, p->scal, p->stream);
+  p->launches += 3;
+  const int iters = 120;
+  for (int it = 0; it < iters; ++it) {
+    launch_apply_op(p->pw[0], p->pw[1], p->n, p->a, p->b, p->s_box, p->fp32, p->fem_n, p->stream);
+    launch_norm2(p->pw[1], cnt, p->part, p->n_part, p->stream);
+    launch_sum(p->part, p->n_part, p->scal, p->stream);
+    launch_scale(p->pw[1], cnt, p->scal, p->stream);
+    p->launches += 4;
+    std::swap(p->pw[0], p->pw[1]);
+  }
+  double nrm2 = 0.0;
+  CK(cudaMemcpyAsync(&nrm2, p->scal, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const double lam = std::sqrt(nrm2) / (p->h * p->h);
+  if (!(p->tau * p->tau * lam < 4.0 * 0.98))
+    return fail(p, DDFD_E_CFL, "tau = " + std::to_string(p->tau) + " exceeds the stability bound 2/sqrt(" +
+                                   std::to_string(lam) + ")");
+  return DDFD_OK;
+}
+
+int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const double *eps0,
+                    const double *sig0, cudaMemcpyKind kind) {
+  if (!eps || !sig) return fail(p, DDFD_E_ARG, "eps and sigma are required");
+  const size_t nfb = (size_t)p->n_free * sizeof(double);
+  CK(cudaMemcpyAsync(p->coef_stage, eps, nfb, kind, p->stream));
+  CK(cudaMemcpyAsync(p->coef_stage + p->n_free, sig, nfb, kind, p->stream));
+  std::vector<double> fill;
+  if (!eps0 || !sig0) fill.assign((size_t)p->n_free, 0.0);
+  if (eps0) {
+    CK(cudaMemcpyAsync(p->coef_stage + 2 * p->n_free, eps0, nfb, kind, p->stream));
+  } else {
+    std::vector<double> ones((size_t)p->n_free, 1.0);
+    CK(cudaMemcpyAsync(p->coef_stage + 2 * p->n_free, ones.data(), nfb, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
+  if (sig0)
+    CK(cudaMemcpyAsync(p->coef_stage + 3 * p->n_free, sig0, nfb, kind, p->stream));
+  else
+    CK(cudaMemcpyAsync(p->coef_stage + 3 * p->n_free, fill.data(), nfb, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream));
+  launch_check_coeffs(p->coef_stage, (int)p->n_free, p->cfg.eps_max, p->cfg.sig_max, p->flag, p->stream);
+  ++p->launches;
+  int flag = 0;
+  int st = read_flag(p, &flag);
+  if (st) return st;
+  if (flag) return fail(p, DDFD_E_COEFF, "coefficient outside [1, eps_max] x [0, sig_max] or non-finite");
+  CK(cudaMemcpyAsync(p->coef, p->coef_stage, 4 * nfb, cudaMemcpyDeviceToDevice, p->stream));
+  launch_expand_coeffs(p->fp32, p->coef, p->nf, p->fem_n, p->tau, p->s_box, p->c_box, p->stream);
+  ++p->launches;
+  p->state = ST_READY;
+  if (p->cfg.cfl_check) {
+    st = cfl_check(p);
+    if (st) return st;
+  }
+  return sync_check(p);
+}
+
+int forward_impl(ddfd_problem *p, double *trace_out, cudaMemcpyKind kind) {
+  const int st = p->fp32 ? enqueue_forward<float>(p) : enqueue_forward<double>(p);
+  if (st) return st;
+  const long long cnt = (long long)p->n_src * (p->Nt + 1) * p->n_det * 3;
+  CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream));
+  launch_nonfinite(p->trace, cnt, p->flag, p->stream);
+  if (cnt > 0) ++p->launches;
+  int flag = 0;
+  int s2 = read_flag(p, &flag);
+  if (s2) return s2;
+  p->state = ST_FORWARD;
+  if (flag) return fail(p, DDFD_E_NONFINITE, "non-finite value in the forward trace");
+  if (trace_out && cnt > 0)
+    CK(cudaMemcpyAsync(trace_out, p->trace, cnt * sizeof(double), kind, p->stream));
+  return sync_check(p);
+}
+
+int functional_impl(ddfd_problem *p, const double *eobs, double *J, bool host) {
+  if (p->state < ST_FORWARD) return fail(p, DDFD_E_STATE, "ddfd_functional needs a forward run");
+  if (!J || (!eobs && p->n_det > 0)) return fail(p, DDFD_E_ARG, "eobs and J are required");
+  const long long cnt = (long long)p->n_src * (p->Nt + 1) * p->n_det * 3;
+  const double *e = eobs;
+  if (host && cnt > 0) {
+    CK(cudaMemcpyAsync(p->eobs_stage, eobs, cnt * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    e = p->eobs_stage;
+  }
+  launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
+  launch_sum(p->part, p->n_part, p->scal, p->stream);
+  launch_regulariser(p->coef, (int)p->n_free, p->part, p->n_part, p->stream);
+  launch_sum(p->part, p->n_part, p->scal + 1, p->stream);
+  launch_sum(p->part + p->n_part, p->n_part, p->scal + 2, p->stream);
+  p->launches += 5;
+  double v[3];
+  CK(cudaMemcpyAsync(v, p->scal, sizeof(v), cudaMemcpyDeviceToHost, p->stream));
+  int st = sync_check(p);
+  if (st) return st;
+  const double m = p->h * p->h * p->h;
+  const double Jv = 0.5 * p->tau * v[0] + 0.5 * p->cfg.gamma_eps * m * v[1] + 0.5 * p->cfg.gamma_sig * m * v[2];
+  if (!std::isfinite(Jv)) return fail(p, DDFD_E_NONFINITE, "non-finite functional");
+  *J = Jv;
+  return DDFD_OK;
+}
+
+int adjoint_impl(ddfd_problem *p, const double *eobs, bool host) {
+  if (p->state < ST_FORWARD) return fail(p, DDFD_E_STATE, "ddfd_adjoint needs a forward run");
+  if (!eobs && p->n_det > 0) return fail(p, DDFD_E_ARG, "eobs is required");
+  const long long cnt = (long long)p->n_src * (p->Nt + 1) * p->n_det * 3;
+  const double *e = eobs;
+  if (host && cnt > 0) {
+    CK(cudaMemcpyAsync(p->eobs_stage, eobs, cnt * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    e = p->eobs_stage;
+  }
+  launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
+  ++p->launches;
+  const int st = p->fp32 ? enqueue_adjoint<float>(p) : enqueue_adjoint<double>(p);
+  if (st) return st;
+  const int s2 = sync_check(p);
+  if (s2) return s2;
+  p->state = ST_ADJOINT;
+  return DDFD_OK;
+}
+
+int gradient_impl(ddfd_problem *p, double *g_eps, double *g_sig, bool host) {
+  if (p->state < ST_ADJOINT) return fail(p, DDFD_E_STATE, "ddfd_gradient needs an adjoint run");
+  if (!g_eps || !g_sig) return fail(p, DDFD_E_ARG, "gradient outputs are required");
+  const double m = p->h * p->h * p->h;
+  double *ge = host ? p->gout : g_eps;
+  double *gs = host ? p->gout + p->n_free : g_sig;
+  launch_grad_finalize(p->coef, (int)p->n_free, p->gacc, p->gacc + p->n_free, m / (p->tau * p->tau),
+                       m / (2.0 * p->tau), m, p->cfg.gamma_eps, p->cfg.gamma_sig, ge, gs, p->stream);
+  CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream));
+  launch_nonfinite(ge, p->n_free, p->flag, p->stream);
+  launch_nonfinite(gs, p->n_free, p->flag, p->stream);
+  p->launches += 3;
+  int flag = 0;
+  int st = read_flag(p, &flag);
+  if (st) return st;
+  if (flag) return fail(p, DDFD_E_NONFINITE, "non-finite gradient");
+  if (host) {
+    CK(cudaMemcpyAsync(g_eps, ge, p->n_free * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(g_sig, gs, p->n_free * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  }
+  return sync_check(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ddfd_config_default(ddfd_config *c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->cfl = 0.3;
+  c->precision = DDFD_FP64;
+  c->fem_kind = DDFD_FEM_STENCIL;
+  c->n_src = 1;
+  c->source_kind = DDFD_SRC_GAUSS;
+  c->freq = 2.0;
+  c->t0 = 0.75;
+  c->width = 0.25;
+  c->t1 = -1.0;
+  c->absorbing_faces = DDFD_ABS_BOTTOM | DDFD_ABS_TOP;
+  c->z_delta_frac = 0.1;
+  c->eps_max = 100.0;
+  c->sig_max = 100.0;
+}
+
+const char *ddfd_create_error(void) { return g_create_err.c_str(); }
+
+int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
+  g_create_err.clear();
+  if (!cfg || !out) {
+    g_create_err = "NULL argument";
+    return DDFD_E_ARG;
+  }
+  std::string m;
+  int st = validate(cfg, &m);
+  if (st) {
+    g_create_err = m;
+    return st;
+  }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    g_create_err = std::string("no usable CUDA device: ") + cudaGetErrorString(ce);
+    return DDFD_E_CUDA;
+  }
+  ddfd_problem *p = new ddfd_problem();
+  p->cfg = *cfg;
+  if (cfg->src_dir) p->src_dir.assign(cfg->src_dir, cfg->src_dir + 3 * cfg->n_src);
+  if (cfg->n_det > 0) p->det_ij.assign(cfg->det_ij, cfg->det_ij + 2 * cfg->n_det);
+  p->cfg.src_dir = nullptr;
+  p->cfg.det_ij = nullptr;
+  p->n = cfg->n;
+  p->fem_n = cfg->fem_n;
+  p->a = (cfg->n - cfg->fem_n) / 2;
+  p->b = p->a + cfg->fem_n - 1;
+  p->f0 = p->a + 2;
+  p->nf = cfg->fem_n - 4;
+  p->n_free = (long long)p->nf * p->nf * p->nf;
+  p->nn = (long long)p->n * p->n * p->n;
+  p->Nt = cfg->n_steps;
+  p->n_src = cfg->n_src;
+  p->n_det = cfg->n_det;
+  p->h = 1.0 / (p->n - 1);
+  p->tau = cfg->cfl * p->h;
+  p->fp32 = cfg->precision == DDFD_FP32;
+  p->esz = p->fp32 ? 4 : 8;
+  p->stream = (cudaStream_t)cfg->stream;
+  p->kz = p->n >= 128 ? 16 : 8;
+
+  auto bail = [&](int code) {
+    g_create_err = p->err;
+    ddfd_destroy(p);
+    return code;
+  };
+  for (int q = 0; q < 4; ++q)
+    if (cudaEventCreate(&p->ev[q]) != cudaSuccess) {
+      p->err = "cudaEventCreate failed";
+      return bail(DDFD_E_CUDA);
+    }
+  KuhnBlocks kb;
+  if (!build_kuhn_blocks(&kb, &m)) {
+    p->err = m;
+    return bail(DDFD_E_ARG);
+  }
+  if ((ce = upload_kuhn_blocks(kb, p->stream)) != cudaSuccess) {
+    p->err = std::string("constant upload: ") + cudaGetErrorString(ce);
+    return bail(DDFD_E_CUDA);
+  }
+  std::vector<double> delay_host;
+  setup_sources(p, &delay_host);
+  const size_t fbytes = 3 * (size_t)p->nn * p->esz;
+  const size_t boxn = (size_t)p->fem_n * p->fem_n * p->fem_n;
+  const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
+  const size_t histn = (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
+  if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
+      (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
+      (st = dalloc(p, boxn * p->esz, &p->s_box)) || (st = dalloc(p, boxn * p->esz, &p->c_box)) ||
+      (st = dalloc(p, histn * p->esz, &p->hist)) || (st = dalloc_t(p, trn, &p->trace)) ||
+      (st = dalloc_t(p, trn, &p->res)) || (st = dalloc_t(p, trn, &p->eobs_stage)) ||
+      (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gacc)) || (st = dalloc_t(p, 4 * (size_t)p->n_free, &p->coef)) ||
+      (st = dalloc_t(p, 4 * (size_t)p->n_free, &p->coef_stage)) ||
+      (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gout)) || (st = dalloc_t(p, (size_t)p->Nt + 1, &p->z)) ||
+      (st = dalloc_t(p, 2 * (size_t)p->n_part, &p->part)) || (st = dalloc_t(p, 4, &p->scal)) ||
+      (st = dalloc_t(p, 1, &p->flag)) || (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_node)) ||
+      (st = dalloc_t(p, (size_t)p->n * p->n + 1, &p->det_ptr)) ||
+      (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_list)))
+    return bail(st);
+  bool any_oblique = false;
+  for (int s = 0; s < p->n_src; ++s) any_oblique |= p->oblique[s] != 0;
+  if (any_oblique && (st = dalloc_t(p, delay_host.size(), &p->delay))) return bail(st);
+
+  // tables
+  std::vector<double> zt((size_t)p->Nt + 1);
+  const double T = p->Nt * p->tau, dl = cfg->z_delta_frac * T;
+  for (int q = 0; q <= p->Nt; ++q) {
+    const double t = q * p->tau;
+    zt[q] = (dl <= 0.0 || t <= T - dl) ? 1.0 : 0.5 * (1.0 + std::cos(kPi * (t - T + dl) / dl));
+  }
+  std::vector<int> dnode((size_t)std::max(p->n_det, 1), 0), dptr((size_t)p->n * p->n + 1, 0),
+      dlist((size_t)std::max(p->n_det, 1), 0);
+  for (int d = 0; d < p->n_det; ++d) {
+    const int i = p->det_ij[2 * d], j = p->det_ij[2 * d + 1];
+    dnode[d] = i + p->n * (j + p->n * (p->n - 1));
+    dptr[i + p->n * j + 1]++;
+  }
+  for (int q = 0; q < p->n * p->n; ++q) dptr[q + 1] += dptr[q];
+  {
+    std::vector<int> fillp(dptr.begin(), dptr.end() - 1);
+    for (int d = 0; d < p->n_det; ++d) {
+      const int i = p->det_ij[2 * d], j = p->det_ij[2 * d + 1];
+      dlist[fillp[i + p->n * j]++] = d;
+    }
+  }
+  auto h2d = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, p->stream);
+  };
+  if (h2d(p->z, zt.data(), zt.size() * sizeof(double)) || h2d(p->det_node, dnode.data(), dnode.size() * sizeof(int)) ||
+      h2d(p->det_ptr, dptr.data(), dptr.size() * sizeof(int)) ||
+      h2d(p->det_list, dlist.data(), dlist.size() * sizeof(int)) ||
+      (p->delay && h2d(p->delay, delay_host.data(), delay_host.size() * sizeof(double)))) {
+    p->err = "table upload failed";
+    return bail(DDFD_E_CUDA);
+  }
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    p->err = std::string("create: ") + cudaGetErrorString(cudaGetLastError());
+    return bail(DDFD_E_CUDA);
+  }
+  // vacuum coefficients
+  std::vector<double> one((size_t)p->n_free, 1.0), zero((size_t)p->n_free, 0.0);
+  const bool chk = p->cfg.cfl_check != 0;
+  p->cfg.cfl_check = 0;
+  st = set_coeffs_impl(p, one.data(), zero.data(), nullptr, nullptr, cudaMemcpyHostToDevice);
+  p->cfg.cfl_check = chk;
+  if (st) return bail(st);
+  *out = p;
+  return DDFD_OK;
+}
+
+void ddfd_destroy(ddfd_problem *p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  else cudaDeviceSynchronize();
+  for (void *v : p->allocs) cudaFree(v);
+  for (int q = 0; q < 4; ++q)
+    if (p->ev[q]) cudaEventDestroy(p->ev[q]);
+  delete p;
+}
+
+const char *ddfd_last_error(const ddfd_problem *p) { return p ? p->err.c_str() : "NULL handle"; }
+
+int ddfd_set_coeffs(ddfd_problem *p, const double *eps, const double *sig, const double *eps0,
+                    const double *sig0) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return set_coeffs_impl(p, eps, sig, eps0, sig0, cudaMemcpyHostToDevice);
+}
+
+int ddfd_set_coeffs_dev(ddfd_problem *p, const double *eps, const double *sig, const double *eps0,
+                        const double *sig0) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return set_coeffs_impl(p, eps, sig, eps0, sig0, cudaMemcpyDeviceToDevice);
+}
+
+int ddfd_forward(ddfd_problem *p, double *trace_out) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return forward_impl(p, trace_out, cudaMemcpyDeviceToHost);
+}
+
+int ddfd_forward_dev(ddfd_problem *p, double *trace_out) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return forward_impl(p, trace_out, cudaMemcpyDeviceToDevice);
+}
+
+int ddfd_functional(ddfd_problem *p, const double *eobs, double *J) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return functional_impl(p, eobs, J, true);
+}
+
+int ddfd_functional_dev(ddfd_problem *p, const double *eobs, double *J) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return functional_impl(p, eobs, J, false);
+}
+
+int ddfd_adjoint(ddfd_problem *p, const double *eobs) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return adjoint_impl(p, eobs, true);
+}
+
+int ddfd_adjoint_dev(ddfd_problem *p, const double *eobs) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return adjoint_impl(p, eobs, false);
+}
+
+int ddfd_gradient(ddfd_problem *p, double *g_eps, double *g_sig) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return gradient_impl(p, g_eps, g_sig, true);
+}
+
+int ddfd_gradient_dev(ddfd_problem *p, double *g_eps, double *g_sig) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  return gradient_impl(p, g_eps, g_sig, false);
+}
+
+int ddfd_get_info(const ddfd_problem *p, ddfd_info *info) {
+  if (!p || !info) return DDFD_E_ARG;
+  info->n = p->n;
+  info->fem_n = p->fem_n;
+  info->n_free = (int32_t)p->n_free;
+  info->n_det = p->n_det;
+  info->n_src = p->n_src;
+  info->n_steps = p->Nt;
+  info->a = p->a;
+  info->b = p->b;
+  info->switch_step = p->n1.empty() ? 0 : p->n1[0];
+  info->h = p->h;
+  info->tau = p->tau;
+  info->device_bytes = p->bytes;
+  info->kernel_launches = p->launches;
+  info->forward_steps = p->fwd_steps;
+  return DDFD_OK;
+}
+
+int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t) {
+  if (!p || !t) return DDFD_E_ARG;
+  t->forward_loop_ms = p->fwd_ms;
+  t->adjoint_loop_ms = p->adj_ms;
+  t->forward_step_kernels = p->fwd_kernels;
+  t->adjoint_step_kernels = p->adj_kernels;
+  return DDFD_OK;
+}
+
+int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  if (count < 0 || count > kMaxCapture || (count > 0 && !steps))
+    return fail(p, DDFD_E_ARG, "capture count must be in [0, 16]");
+  for (int q = 0; q < count; ++q)
+    if (steps[q] < 0 || steps[q] > p->Nt) return fail(p, DDFD_E_ARG, "capture step out of range");
+  const size_t fbytes = 3 * (size_t)p->nn * p->esz;
+  if (count > (int)p->cap_steps.size() || !p->capE) {
+    // grow: allocate fresh buffers for count slots
+    int st;
+    if ((st = dalloc(p, fbytes * std::max(count, 1), &p->capE)) ||
+        (st = dalloc(p, fbytes * std::max(count, 1), &p->capMu)))
+      return st;
+  }
+  p->cap_steps.assign(steps, steps + count);
+  return DDFD_OK;
+}
+
+int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out) {
+  if (!p || !out) return DDFD_E_ARG;
+  p->err.clear();
+  if (idx < 0 || idx >= (int)p->cap_steps.size() || (kind != 0 && kind != 1))
+    return fail(p, DDFD_E_ARG, "bad capture index or kind");
+  const size_t cnt = 3 * (size_t)p->nn;
+  const char *src = (const char *)(kind == 0 ? p->capE : p->capMu) + idx * cnt * p->esz;
+  CK(cudaStreamSynchronize(p->stream));
+  if (p->fp32) {
+    std::vector<float> tmp(cnt);
+    CK(cudaMemcpy(tmp.data(), src, cnt * 4, cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < cnt; ++q) out[q] = tmp[q];
+  } else {
+    CK(cudaMemcpy(out, src, cnt * 8, cudaMemcpyDeviceToHost));
+  }
+  return DDFD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,212 @@
+// Small kernels of the ddfd library: coefficient preparation, detector
+// gather, residual and functional reductions, gradient finalisation, the
+// non-finite watchdog and the operator apply used by the stability check.
+//
+// Every reduction is a fixed two-pass tree (per-block partials, then one
+// block), so results are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ddfd_internal.h"
+
+namespace ddfd {
+
+constexpr int RB = 256;  // reduction block size
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[RB / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < RB / 32) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+template <typename T>
+__global__ void k_gather_trace(const T *E, long long cs, int n_det, const int *det_node, double *tr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 3 * n_det) {
+    const int d = t / 3, c = t - 3 * d;
+    tr[t] = (double)E[c * cs + det_node[d]];
+  }
+}
+
+void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const int *det_node,
+                         double *trace_n, cudaStream_t s) {
+  if (n_det <= 0) return;
+  const int nb = (3 * n_det + 255) / 256;
+  if (fp32)
+    k_gather_trace<float><<<nb, 256, 0, s>>>((const float *)E, cs, n_det, det_node, trace_n);
+  else
+    k_gather_trace<double><<<nb, 256, 0, s>>>((const double *)E, cs, n_det, det_node, trace_n);
+}
+
+// s = eps - 1 and c = sigma tau / 2 over the FEM box; zero off the free nodes.
+template <typename T>
+__global__ void k_expand(const double *coef, int nf, int fb, double tau, T *s_box, T *c_box) {
+  const long long nb = (long long)fb * fb * fb;
+  const long long n_free = (long long)nf * nf * nf;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nb;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int li = (int)(q % fb), lj = (int)((q / fb) % fb), lk = (int)(q / ((long long)fb * fb));
+    T sv = T(0), cv = T(0);
+    if (li >= 2 && li < 2 + nf && lj >= 2 && lj < 2 + nf && lk >= 2 && lk < 2 + nf) {
+      const long long f = (li - 2) + (long long)nf * ((lj - 2) + (long long)nf * (lk - 2));
+      sv = (T)(coef[f] - 1.0);
+      cv = (T)(coef[n_free + f] * tau * 0.5);
+    }
+    s_box[q] = sv;
+    c_box[q] = cv;
+  }
+}
+
+void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int fem_n, double tau,
+                          void *s_box, void *c_box, cudaStream_t s) {
+  const long long nb = (long long)fem_n * fem_n * fem_n;
+  const int blocks = (int)((nb + 255) / 256 < 4096 ? (nb + 255) / 256 : 4096);
+  if (fp32)
+    k_expand<float><<<blocks, 256, 0, s>>>(coef_free, nf, fem_n, tau, (float *)s_box, (float *)c_box);
+  else
+    k_expand<double><<<blocks, 256, 0, s>>>(coef_free, nf, fem_n, tau, (double *)s_box, (double *)c_box);
+}
+
+__global__ void k_check(const double *coef, int n_free, double eps_max, double sig_max, int *flag) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n_free; f += gridDim.x * blockDim.x) {
+    const double e = coef[f], g = coef[n_free + f], e0 = coef[2 * n_free + f], g0 = coef[3 * n_free + f];
+    const bool bad = !(e >= 1.0 && e <= eps_max) || !(g >= 0.0 && g <= sig_max) || !isfinite(e0) ||
+                     !isfinite(g0);
+    if (bad) atomicOr(flag, 1);
+  }
+}
+
+void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, double sig_max,
+                         int *flag, cudaStream_t s) {
+  const int blocks = (n_free + 255) / 256 < 1024 ? (n_free + 255) / 256 : 1024;
+  k_check<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(coef_free, n_free, eps_max, sig_max, flag);
+}
+
+// trace/eobs/res: [n_src][n_steps+1][n_det][3]
+__global__ void k_residual(const double *trace, const double *eobs, const double *z, int n_steps,
+                           int n_det, long long total, double tau, double *res, double *part) {
+  const long long per = (long long)(n_steps + 1) * n_det * 3;
+  double acc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long within = q % per;
+    const int step = (int)(within / (3LL * n_det));
+    double r = 0.0;
+    if (step >= 1) {
+      const double d = trace[q] - eobs[q];
+      acc += z[step] * d * d;
+      r = tau * z[step] * d;
+    }
+    res[q] = r;
+  }
+  const double b = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+void launch_residual(const double *trace, const double *eobs, const double *z, int n_steps,
+                     int n_det, int n_src, double tau, double *res, double *part, int n_part,
+                     cudaStream_t s) {
+  const long long total = (long long)n_src * (n_steps + 1) * n_det * 3;
+  k_residual<<<n_part, RB, 0, s>>>(trace, eobs, z, n_steps, n_det, total, tau, res, part);
+}
+
+// sum_f (eps - eps0)^2 into part[0..n_part), sum_f (sig - sig0)^2 into part[n_part..2 n_part)
+__global__ void k_regul(const double *coef, int n_free, double *part, int n_part) {
+  double ae = 0.0, as = 0.0;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n_free; f += gridDim.x * blockDim.x) {
+    const double de = coef[f] - coef[2 * n_free + f];
+    const double ds = coef[n_free + f] - coef[3 * n_free + f];
+    ae += de * de;
+    as += ds * ds;
+  }
+  const double be = block_sum(ae);
+  const double bs = block_sum(as);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = be;
+    part[n_part + blockIdx.x] = bs;
+  }
+}
+
+void launch_regulariser(const double *coef_free, int n_free, double *part, int n_part, cudaStream_t s) {
+  k_regul<<<n_part, RB, 0, s>>>(coef_free, n_free, part, n_part);
+}
+
+__global__ void k_sum(const double *part, int n_part, double *out) {
+  double a = 0.0;
+  for (int q = threadIdx.x; q < n_part; q += blockDim.x) a += part[q];
+  const double b = block_sum(a);
+  if (threadIdx.x == 0) *out = b;
+}
+
+void launch_sum(const double *part, int n_part, double *out, cudaStream_t s) {
+  k_sum<<<1, RB, 0, s>>>(part, n_part, out);
+}
+
+__global__ void k_grad_final(const double *coef, int n_free, const double *ge, const double *gs,
+                             double ge_scale, double gs_scale, double m, double gam_e, double gam_s,
+                             double *g_eps, double *g_sig) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n_free; f += gridDim.x * blockDim.x) {
+    g_eps[f] = gam_e * m * (coef[f] - coef[2 * n_free + f]) + ge_scale * ge[f];
+    g_sig[f] = gam_s * m * (coef[n_free + f] - coef[3 * n_free + f]) + gs_scale * gs[f];
+  }
+}
+
+void launch_grad_finalize(const double *coef_free, int n_free, const double *gacc_e,
+                          const double *gacc_s, double ge_scale, double gs_scale, double m,
+                          double gamma_e, double gamma_s, double *g_eps, double *g_sig,
+                          cudaStream_t s) {
+  const int blocks = (n_free + 255) / 256 < 2048 ? (n_free + 255) / 256 : 2048;
+  k_grad_final<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(coef_free, n_free, gacc_e, gacc_s, ge_scale,
+                                                       gs_scale, m, gamma_e, gamma_s, g_eps, g_sig);
+}
+
+__global__ void k_nonfinite(const double *x, long long count, int *flag) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+       q += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[q])) {
+      atomicOr(flag, 2);
+      return;
+    }
+}
+
+void launch_nonfinite(const double *x, long long count, int *flag, cudaStream_t s) {
+  if (count <= 0) return;
+  const long long nb = (count + 255) / 256;
+  k_nonfinite<<<(int)(nb < 2048 ? nb : 2048), 256, 0, s>>>(x, count, flag);
+}
+
+// partial sums of x^2 (two-pass, deterministic)
+__global__ void k_norm2(const double *x, long long count, double *part) {
+  double a = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+       q += (long long)gridDim.x * blockDim.x)
+    a += x[q] * x[q];
+  const double b = block_sum(a);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+void launch_norm2(const double *x, long long count, double *part, int n_part, cudaStream_t s) {
+  k_norm2<<<n_part, RB, 0, s>>>(x, count, part);
+}
+
+__global__ void k_scale(double *x, long long count, const double *norm2) {
+  const double inv = 1.0 / sqrt(*norm2);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+       q += (long long)gridDim.x * blockDim.x)
+    x[q] *= inv;
+}
+
+void launch_scale(double *x, long long count, const double *norm2, cudaStream_t s) {
+  const long long nb = (count + 255) / 256;
+  k_scale<<<(int)(nb < 4096 ? nb : 4096), 256, 0, s>>>(x, count, norm2);
+}
+
+}  // namespace ddfd

@@ -1,0 +1,106 @@
+// Internal declarations shared by the host driver and the kernels of the
+// ddfd library (GB300 / sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ddfd.h"
+
+namespace ddfd {
+
+// Kuhn P1 div-div blocks for an interior node at h = 1:
+// (D^T D)_{i,i+o} = h * B[o], B[-o] = B[o]; index 0 = offset 0, 1..7 = the
+// offsets (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,0,1) (0,1,1) (1,1,1).
+struct KuhnBlocks {
+  double B[8][9];
+  double mass;      // lumped mass of an interior node at h = 1 (must be 1)
+  double lap[8];    // Laplacian row coefficients for the same offsets (7-point check)
+};
+
+// Builds the blocks by assembling the 24 Kuhn tetrahedra around a node;
+// returns false (with a message) if the FE rows do not match the FD rows.
+bool build_kuhn_blocks(KuhnBlocks *out, std::string *msg);
+
+// Uploads the blocks to constant memory (both precisions).
+cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
+
+// Geometry and per-step scalars common to the forward and adjoint steps.
+template <typename T>
+struct StepParams {
+  int n;                 // nodes per axis
+  int a, b;              // FEM box [a,b]
+  int f0, nf;            // free box origin and side
+  int kz;                // z planes per thread block
+  long long cs;          // component stride (n^3)
+  const T *cur;          // E^n (forward) or mu^k (adjoint), 3 components
+  T *old;                // E^{n-1} in, E^{n+1} out (forward); mu^{k+1} in, mu^{k-1} out
+  const T *s_box;        // eps - 1 over the FEM box, fem_n^3
+  const T *c_box;        // sigma * tau / 2 over the FEM box
+  int fem_n;
+  T r2;                  // (tau/h)^2
+  T cb;                  // tau/h: damping of one absorbing face, divided form
+  uint32_t abs_now;      // forward: absorbing faces at step n; adjoint: at step k-1
+  uint32_t abs_next;     // adjoint: absorbing faces at step k+1
+  // top-face source (forward only)
+  int src_on;            // 1 while n <= n1
+  int oblique;           // 0: normal incidence, value src_y on the y component
+  T src_y;               // 2 tau^2 / h * P(t_n) (normal incidence)
+  const double *delay;   // oblique: delay of each top node, n^2
+  double pol[3];         // oblique: polarisation
+  double t_n;            // time of the step
+  double src_scale;      // 2 tau^2 / h
+  int pulse_kind;
+  double freq, t0, width;
+  // detectors
+  int n_det;
+  const int *det_node;   // forward gather: node id of each detector
+  double *trace_n;       // forward: trace[n] base ([n_det][3]), gathered from cur
+  const int *det_ptr;    // adjoint: CSR over top-plane nodes (n^2 + 1)
+  const int *det_list;
+  const double *res_k;   // adjoint: residual tau z (E^k - Eobs^k), [n_det][3]
+  double inv_h3;         // 1 / h^3
+  double tau2;           // tau^2
+  // history of E on the free nodes
+  T *hist_w;             // forward: hist[n+1] ([3][n_free])
+  const T *hist_r;       // adjoint: hist[k]
+  long long n_free;
+  double *gacc_e;        // adjoint: gradient accumulators (FP64)
+  double *gacc_s;
+};
+
+template <typename T>
+void launch_forward_step(const StepParams<T> &P, cudaStream_t s);
+template <typename T>
+void launch_adjoint_step(const StepParams<T> &P, cudaStream_t s);
+
+// Small kernels.
+void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const int *det_node,
+                         double *trace_n, cudaStream_t s);
+void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int fem_n, double tau,
+                          void *s_box, void *c_box, cudaStream_t s);
+void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, double sig_max,
+                         int *flag, cudaStream_t s);
+// residual r = tau z (trace - eobs) for n >= 1 (r[0] = 0); partial sums of
+// z |trace - eobs|^2 per block into part[] (deterministic two-pass sum).
+void launch_residual(const double *trace, const double *eobs, const double *z, int n_steps,
+                     int n_det, int n_src, double tau, double *res, double *part, int n_part,
+                     cudaStream_t s);
+void launch_regulariser(const double *coef_free, int n_free, double *part, int n_part,
+                        cudaStream_t s);
+void launch_sum(const double *part, int n_part, double *out, cudaStream_t s);
+void launch_grad_finalize(const double *coef_free, int n_free, const double *gacc_e,
+                          const double *gacc_s, double ge_scale, double gs_scale, double m,
+                          double gamma_e, double gamma_s, double *g_eps, double *g_sig,
+                          cudaStream_t s);
+void launch_nonfinite(const double *x, long long count, int *flag, cudaStream_t s);
+// power iteration helpers (FP64): y = M_eps^-1 K x, and the squared norm.
+void launch_apply_op(const double *x, double *y, int n, int a, int b, const void *s_box, int fp32,
+                     int fem_n, cudaStream_t s);
+void launch_norm2(const double *x, long long count, double *part, int n_part, cudaStream_t s);
+void launch_scale(double *x, long long count, const double *norm2, cudaStream_t s);
+
+}  // namespace ddfd

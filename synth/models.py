@@ -167,6 +167,8 @@ class Workload:
                                        self.n_incl if inclusions else 0)
 
     def detectors(self) -> np.ndarray:
+        if "det" in self.extra:
+            return np.asarray(self.extra["det"], dtype=np.int32).reshape(-1, 2)
         return detector_grid(self.n, self.fem_n, self.det_per_side)
 
     def directions(self) -> np.ndarray:

@@ -1,0 +1,66 @@
+"""The C ABI library: builds, loads, exports every entry point of
+include/ddfd.h, and rejects bad configurations before touching a GPU."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ddfd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ddfd_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_07780_gb300 import build
+    build.build()
+    import paper_2508_07780_gb300 as pkg
+    return pkg.load_library()
+
+
+def test_header_declares_the_binding_symbols():
+    import paper_2508_07780_gb300 as pkg
+    assert header_functions() == sorted(pkg.ABI_SYMBOLS)
+
+
+def test_library_exports_every_header_symbol(lib):
+    missing = [f for f in header_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def _cpu_only():
+    try:
+        import torch
+        return not torch.cuda.is_available()
+    except Exception:
+        return True
+
+
+@pytest.mark.parametrize("kw,what", [
+    (dict(n=5, fem_n=5, n_steps=3), "n must be"),
+    (dict(n=21, fem_n=20, n_steps=3), "fem_n"),
+    (dict(n=21, fem_n=11, n_steps=0), "n_steps"),
+    (dict(n=21, fem_n=11, n_steps=3, cfl=0.0), "cfl"),
+    (dict(n=21, fem_n=11, n_steps=3, det_ij=[[0, 21]]), "detector"),
+    (dict(n=21, fem_n=11, n_steps=3, src_dir=[[0.0, 0.3, 0.2]]), "k_z < 0"),
+    (dict(n=21, fem_n=11, n_steps=3, z_delta_frac=1.0), "z_delta_frac"),
+    (dict(n=21, fem_n=11, n_steps=3, absorbing_faces=64), "absorbing"),
+    (dict(n=21, fem_n=11, n_steps=3, precision=7), "precision"),
+])
+def test_create_rejects_bad_configurations(lib, kw, what):
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    with pytest.raises(DDFDError) as e:
+        Problem(**kw)
+    assert e.value.code == -1 and what in str(e.value)
+
+
+@pytest.mark.skipif(not _cpu_only(), reason="this machine has a GPU")
+def test_no_gpu_fails_loudly(lib):
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    with pytest.raises(DDFDError) as e:
+        Problem(n=13, fem_n=9, n_steps=4)
+    assert e.value.code == -4

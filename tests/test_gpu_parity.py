@@ -1,0 +1,219 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded inputs.
+
+Bars (relative L2): FP64 path <= 1e-12 on traces, fields, mu, J and g;
+FP32 path <= 1e-4 on traces, fields, mu and J, <= 1e-3 on g.  Sizes span
+several thread blocks with ragged tails (n = 9, 13, 25, 41 against 32 x 4
+blocks and 8-plane z chunks) and include the 41^3, 300-step plain FP64
+workload in full.
+"""
+import numpy as np
+import pytest
+
+from helpers import capture_steps, rel_l2, run_gpu, run_oracle
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(E=1e-12, mu=1e-12, J=1e-12, g=1e-12),
+       "fp32": dict(E=1e-4, mu=1e-4, J=1e-4, g=1e-3)}
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    from paper_2508_07780_gb300 import build
+    build.build()
+
+
+CASES = {
+    "tiny": (workload("tiny"), {}),
+    "small": (workload("small"), {}),
+    "c1_fp64_41": (workload("c1_fp64_41"), {}),
+    # oblique incidence, the paper's single-period sine (eq. f), regularisation,
+    # absorbing side faces, a taper of a third of the horizon
+    "small_oblique_sine": (workload("small", dir_seed=7, gamma_eps=0.05, gamma_sig=0.2,
+                                    z_delta_frac=0.3),
+                           dict(src_kw=dict(kind="sine", freq=3.0), absorbing=1 | 2 | 4 | 32)),
+    # smallest FEM cube (one free node), grid n = 9
+    "min_fem": (workload("tiny", n=9, fem_n=5, n_steps=30, det_per_side=2), {}),
+    # two sources, duplicated and corner detectors
+    "two_src_dup_det": (workload("tiny", n_src=2, dir_seed=3,
+                                 extra={"det": [[6, 6], [6, 6], [0, 0], [12, 12], [0, 12], [4, 9]]}), {}),
+}
+
+_oracle_cache = {}
+
+
+def oracle_case(name):
+    if name not in _oracle_cache:
+        w, opt = CASES[name]
+        ke, km = capture_steps(w.n_steps)
+        src_kw = opt.get("src_kw")
+        _oracle_cache[name] = run_oracle(w, keep_e=ke, keep_mu=km, src_kw=src_kw,
+                                         absorbing=opt.get("absorbing"))
+    return _oracle_cache[name]
+
+
+def gpu_kw(opt):
+    kw = {}
+    if "absorbing" in opt:
+        kw["absorbing_faces"] = opt["absorbing"]
+    src = opt.get("src_kw") or {}
+    g = {}
+    if src.get("kind") == "sine":
+        g["source_kind"] = 1
+    for k in ("freq", "t0", "width", "t1"):
+        if k in src:
+            g[k] = src[k]
+    return kw, g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_parity_with_oracle(name, prec):
+    w, opt = CASES[name]
+    ref = oracle_case(name)
+    ke, km = capture_steps(w.n_steps)
+    kw, src_kw = gpu_kw(opt)
+    out = run_gpu(w, ref["eobs"], precision=prec, keep_e=ke, keep_mu=km, src_kw=src_kw, **kw)
+    tol = TOL[prec]
+    errs = {"trace": rel_l2(out["trace"], ref["trace"]),
+            "J": abs(out["J"] - ref["J"]) / abs(ref["J"]),
+            "g_eps": rel_l2(out["g_eps"], ref["g_eps"]),
+            "g_sig": rel_l2(out["g_sig"], ref["g_sig"])}
+    for s in ke:
+        errs[f"E{s}"] = rel_l2(out["E"][s], ref["E"][s])
+    for s in km:
+        errs[f"mu{s}"] = rel_l2(out["mu"][s], ref["mu"][s])
+    bad = {k: v for k, v in errs.items()
+           if v > (tol["J"] if k == "J" else tol["g"] if k.startswith("g_")
+                   else tol["mu"] if k.startswith("mu") else tol["E"])}
+    assert not bad, (bad, errs)
+
+
+def test_zero_and_one_step_and_no_detectors():
+    from paper_2508_07780_gb300 import Problem
+    w = workload("tiny")
+    eps, sig = w.model()
+    for nt in (1, 2):
+        ref = run_oracle(w.with_(n_steps=nt))
+        out = run_gpu(w.with_(n_steps=nt), ref["eobs"], precision="fp64")
+        assert rel_l2(out["trace"], ref["trace"]) <= 1e-12
+        assert rel_l2(out["g_eps"], ref["g_eps"]) <= 1e-12 or np.abs(ref["g_eps"]).max() == 0
+    # no detectors: J is the regulariser, the gradient its closed form
+    p = Problem(n=13, fem_n=9, n_steps=20, det_ij=np.zeros((0, 2), np.int32),
+                gamma_eps=0.5, gamma_sig=0.25)
+    e0 = np.full(p.n_free, 2.0)
+    p.set_coeffs(eps, sig, e0, None)
+    tr = p.forward()
+    assert tr.shape == (1, 21, 0, 3)
+    J = p.functional(np.zeros(0))
+    m = (1.0 / 12) ** 3
+    assert J == pytest.approx(0.5 * 0.5 * m * np.sum((eps - 2.0) ** 2) + 0.5 * 0.25 * m * np.sum(sig ** 2),
+                              rel=1e-13)
+    p.adjoint(np.zeros(0))
+    ge, gs = p.gradient()
+    assert np.allclose(ge, 0.5 * m * (eps - 2.0), rtol=1e-13, atol=0)
+    assert np.allclose(gs, 0.25 * m * sig, rtol=1e-13, atol=0)
+    p.close()
+
+
+def test_call_order_and_coefficient_errors():
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    w = workload("tiny")
+    p = Problem(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, det_ij=w.detectors())
+    eobs = np.zeros(p.trace_shape)
+    with pytest.raises(DDFDError) as e:
+        p.adjoint(eobs)
+    assert e.value.code == -3
+    with pytest.raises(DDFDError) as e:
+        p.gradient()
+    assert e.value.code == -3
+    with pytest.raises(DDFDError) as e:
+        p.functional(eobs)
+    assert e.value.code == -3
+    eps, sig = w.model()
+    bad = eps.copy()
+    bad[3] = 0.5
+    with pytest.raises(DDFDError) as e:
+        p.set_coeffs(bad, sig)
+    assert e.value.code == -8
+    bad = sig.copy()
+    bad[0] = np.nan
+    with pytest.raises(DDFDError) as e:
+        p.set_coeffs(eps, bad)
+    assert e.value.code == -8
+    p.set_coeffs(eps, sig)
+    p.forward()
+    p.adjoint(eobs)
+    p.set_coeffs(eps, sig)          # invalidates the forward state
+    with pytest.raises(DDFDError) as e:
+        p.gradient()
+    assert e.value.code == -3
+    p.close()
+
+
+def test_unstable_step_reports_nonfinite():
+    """cfl = 3 is far beyond the bound 2/sqrt(12): the field overflows and the
+    library must report DDFD_E_NONFINITE (plain FP overflow, no fault)."""
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    w = workload("tiny")
+    p = Problem(n=w.n, fem_n=w.fem_n, n_steps=400, cfl=3.0, det_ij=w.detectors())
+    with pytest.raises(DDFDError) as e:
+        p.forward()
+    assert e.value.code == -6
+    p.close()
+
+
+def test_cfl_check_power_iteration():
+    from oracle import OracleProblem, SourceSpec
+    from oracle.cfl import lambda_max
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    w = workload("tiny")
+    eps, sig = w.model()
+    P = OracleProblem(w.n, w.fem_n, 1, 0.3, eps, sig, w.detectors(), [SourceSpec()])
+    cfl_max = 2.0 / np.sqrt(lambda_max(P.op, 1500)) / P.g.h
+    ok = Problem(n=w.n, fem_n=w.fem_n, n_steps=5, cfl=0.9 * cfl_max, cfl_check=1)
+    ok.set_coeffs(eps, sig)
+    ok.close()
+    bad = Problem(n=w.n, fem_n=w.fem_n, n_steps=5, cfl=1.1 * cfl_max, cfl_check=1)
+    with pytest.raises(DDFDError) as e:
+        bad.set_coeffs(eps, sig)
+    assert e.value.code == -2
+    bad.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_runs_are_bitwise_reproducible(prec):
+    w = workload("small")
+    eobs = np.zeros((1, w.n_steps + 1, w.det_per_side ** 2, 3))
+    a = run_gpu(w, eobs, precision=prec)
+    b = run_gpu(w, eobs, precision=prec)
+    assert np.array_equal(a["trace"], b["trace"])
+    assert a["J"] == b["J"]
+    assert np.array_equal(a["g_eps"], b["g_eps"]) and np.array_equal(a["g_sig"], b["g_sig"])
+
+
+def test_device_entry_points_match_host_ones():
+    torch = pytest.importorskip("torch")
+    from helpers import gpu_problem
+    w = workload("small")
+    eobs = run_oracle(w)["eobs"]
+    host = run_gpu(w, eobs, precision="fp64")
+    p = gpu_problem(w, "fp64")
+    eps, sig = w.model()
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    p.set_coeffs_dev(dev(eps), dev(sig))
+    tr = torch.empty(p.trace_shape, dtype=torch.float64, device="cuda")
+    p.forward_dev(tr)
+    e = dev(eobs)
+    J = p.functional_dev(e)
+    p.adjoint_dev(e)
+    ge = torch.empty(p.n_free, dtype=torch.float64, device="cuda")
+    gs = torch.empty_like(ge)
+    p.gradient_dev(ge, gs)
+    torch.cuda.synchronize()
+    assert np.array_equal(tr.cpu().numpy(), host["trace"])
+    assert J == host["J"]
+    assert np.array_equal(ge.cpu().numpy(), host["g_eps"])
+    assert np.array_equal(gs.cpu().numpy(), host["g_sig"])
+    p.close()
