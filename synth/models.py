@@ -196,6 +196,10 @@ WORKLOADS = {
     # 1 + (seed mod 3) = 3 inclusions, 1024 detectors
     "c2_fp32_201": Workload("c2_fp32_201", 201, 101, 2000, precision="fp32",
                             seed=2, n_incl=3, det_per_side=32),
+    # the same grid and kernels for 20 steps: small device footprint for
+    # profiler captures
+    "c2_profile": Workload("c2_profile", 201, 101, 20, precision="fp32",
+                           seed=2, n_incl=3, det_per_side=32),
     # differentiable FP32 run, 301^3 grid, 151^3 FEM cube, 4000 steps
     "c4_fp32_301": Workload("c4_fp32_301", 301, 151, 4000, precision="fp32",
                             seed=4, n_incl=2, det_per_side=32),
