@@ -3,6 +3,8 @@
 // enqueueing of the step kernels.  All arithmetic of the method runs in the
 // kernels of ddfd_step.cu and ddfd_aux.cu; the host only prepares per-step
 // scalars (pulse value, absorbing-face set) and small tables.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,7 +39,8 @@ struct ddfd_problem {
   std::vector<int32_t> det_ij;
   std::string err;
   int n = 0, fem_n = 0, a = 0, b = 0, f0 = 0, nf = 0, Nt = 0, n_src = 0, n_det = 0;
-  long long n_free = 0, nn = 0;
+  int px = 0;                 // x pitch of the padded field layout
+  long long n_free = 0, nn = 0, cs = 0;  // cs = px n^2, the component stride
   double h = 0, tau = 0;
   int fp32 = 0;
   size_t esz = 8;
@@ -45,11 +48,15 @@ struct ddfd_problem {
   std::vector<void *> allocs;
   int64_t bytes = 0;
   void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr};
-  void *s_box = nullptr, *c_box = nullptr, *hist = nullptr;
+  void *kcoef = nullptr;      // padded full-grid (eps - 1, sigma tau / 2), 2 channels
+  void *hist = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
   double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
   double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
   int *det_node = nullptr, *det_ptr = nullptr, *det_list = nullptr, *flag = nullptr;
+  int *errflag = nullptr;     // kernel-side error bits (bounded waits)
+  // TMA descriptors: [buffer] halo-box (current level) and centre-box (old level)
+  CUtensorMap mE_halo[2], mE_ctr[2], mM_halo[2], mM_ctr[2], mK;
   std::vector<double> ptab;  // [n_src][Nt] pulse value P(t_n) (normal incidence), 0 after n1
   std::vector<int> n1, oblique;
   std::vector<double> pol;   // [n_src][3]
@@ -201,15 +208,15 @@ StepParams<T> base_params(const ddfd_problem *p) {
   StepParams<T> P;
   std::memset(&P, 0, sizeof(P));
   P.n = p->n;
+  P.px = p->px;
   P.a = p->a;
   P.b = p->b;
   P.f0 = p->f0;
   P.nf = p->nf;
   P.kz = p->kz;
-  P.cs = p->nn;
-  P.s_box = (const T *)p->s_box;
-  P.c_box = (const T *)p->c_box;
-  P.fem_n = p->fem_n;
+  P.cs = p->cs;
+  P.err = p->errflag;
+  P.spin_limit = 1u << 22;
   P.r2 = (T)((p->tau / p->h) * (p->tau / p->h));
   P.cb = (T)(p->tau / p->h);
   P.src_scale = 2.0 * p->tau * p->tau / p->h;
@@ -237,7 +244,7 @@ int capture_slot(const ddfd_problem *p, int step) {
 
 template <typename T>
 int enqueue_forward(ddfd_problem *p) {
-  const size_t fbytes = 3 * (size_t)p->nn * sizeof(T);
+  const size_t fbytes = 3 * (size_t)p->cs * sizeof(T);
   const int Nt = p->Nt;
   float ms_total = 0.0f;
   for (int s = 0; s < p->n_src; ++s) {
@@ -247,32 +254,33 @@ int enqueue_forward(ddfd_problem *p) {
       const int sl = capture_slot(p, 0);
       if (sl >= 0) CK(cudaMemsetAsync((char *)p->capE + sl * fbytes, 0, fbytes, p->stream));
     }
-    void *cur = p->E[1], *old = p->E[0];
+    int ic = 1, io = 0;  // buffer holding E^n, and E^{n-1}
     StepParams<T> P = base_params<T>(p);
     P.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
     P.oblique = p->oblique[s];
     for (int q = 0; q < 3; ++q) P.pol[q] = p->pol[3 * s + q];
     CK(cudaEventRecord(p->ev[0], p->stream));
     for (int st = 0; st < Nt; ++st) {
-      P.cur = (const T *)cur;
-      P.old = (T *)old;
+      P.cur = (const T *)p->E[ic];
+      P.old = (T *)p->E[io];
       P.abs_now = faces_at(p, s, st);
       P.src_on = st <= p->n1[s] ? 1 : 0;
       P.t_n = st * p->tau;
       P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
       P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
       P.hist_w = (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
-      launch_forward_step<T>(P, p->stream);
+      launch_forward_step<T>(p->mE_halo[ic], p->mE_ctr[io], p->mK, P, p->stream);
       ++p->launches;
-      std::swap(cur, old);
+      std::swap(ic, io);
       if (s == 0) {
         const int sl = capture_slot(p, st + 1);
-        if (sl >= 0) CK(cudaMemcpyAsync((char *)p->capE + sl * fbytes, cur, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+        if (sl >= 0)
+          CK(cudaMemcpyAsync((char *)p->capE + sl * fbytes, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, p->stream));
       }
     }
     CK(cudaEventRecord(p->ev[1], p->stream));
     CK(cudaGetLastError());
-    launch_gather_trace(cur, p->fp32, p->nn, p->n_det, p->det_node,
+    launch_gather_trace(p->E[ic], p->fp32, p->cs, p->n_det, p->det_node,
                         p->trace + ((size_t)s * (Nt + 1) + Nt) * p->n_det * 3, p->stream);
     if (p->n_det > 0) ++p->launches;
     p->fwd_steps += Nt;
@@ -289,29 +297,30 @@ int enqueue_forward(ddfd_problem *p) {
 
 template <typename T>
 int enqueue_adjoint(ddfd_problem *p) {
-  const size_t fbytes = 3 * (size_t)p->nn * sizeof(T);
+  const size_t fbytes = 3 * (size_t)p->cs * sizeof(T);
   const int Nt = p->Nt;
   CK(cudaMemsetAsync(p->gacc, 0, 2 * (size_t)p->n_free * sizeof(double), p->stream));
   float ms_total = 0.0f;
   for (int s = 0; s < p->n_src; ++s) {
     CK(cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream));
     CK(cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream));
-    void *cur = p->Mu[1], *old = p->Mu[0];  // mu^Nt, mu^{Nt+1}
+    int ic = 1, io = 0;  // buffers holding mu^k and mu^{k+1}
     StepParams<T> P = base_params<T>(p);
     CK(cudaEventRecord(p->ev[2], p->stream));
     for (int k = Nt; k >= 1; --k) {
-      P.cur = (const T *)cur;
-      P.old = (T *)old;
+      P.cur = (const T *)p->Mu[ic];
+      P.old = (T *)p->Mu[io];
       P.abs_now = faces_at(p, s, k - 1);
       P.abs_next = faces_at(p, s, k + 1);
       P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
       P.hist_r = (const T *)p->hist + ((size_t)s * (Nt + 1) + k) * 3 * p->n_free;
-      launch_adjoint_step<T>(P, p->stream);
+      launch_adjoint_step<T>(p->mM_halo[ic], p->mM_ctr[io], p->mK, P, p->stream);
       ++p->launches;
-      std::swap(cur, old);
+      std::swap(ic, io);
       if (s == 0) {
         const int sl = capture_slot(p, k - 1);
-        if (sl >= 0) CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, cur, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+        if (sl >= 0)
+          CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, p->Mu[ic], fbytes, cudaMemcpyDeviceToDevice, p->stream));
       }
     }
     CK(cudaEventRecord(p->ev[3], p->stream));
@@ -361,7 +370,7 @@ int cfl_check(ddfd_problem *p) {
   p->launches += 3;
   const int iters = 120;
   for (int it = 0; it < iters; ++it) {
-    launch_apply_op(p->pw[0], p->pw[1], p->n, p->a, p->b, p->s_box, p->fp32, p->fem_n, p->stream);
+    launch_apply_op(p->pw[0], p->pw[1], p->n, p->px, p->a, p->b, p->kcoef, p->fp32, p->stream);
     launch_norm2(p->pw[1], cnt, p->part, p->n_part, p->stream);
     launch_sum(p->part, p->n_part, p->scal, p->stream);
     launch_scale(p->pw[1], cnt, p->scal, p->stream);
@@ -375,6 +384,57 @@ int cfl_check(ddfd_problem *p) {
   if (!(p->tau * p->tau * lam < 4.0 * 0.98))
     return fail(p, DDFD_E_CFL, "tau = " + std::to_string(p->tau) + " exceeds the stability bound 2/sqrt(" +
                                    std::to_string(lam) + ")");
+  return DDFD_OK;
+}
+
+// TMA descriptors of one padded field: a 4-D tensor (x, y, z, channel) with
+// row stride px, plane stride px n, channel stride px n^2; the halo box is
+// (32 + 2 hx) x 10 x 1 x ch starting hx elements (16 bytes) left of the tile,
+// the centre box 32 x 8 x 1 x ch.  Out-of-range elements read as zero.
+int encode_map(ddfd_problem *p, CUtensorMap *m, void *base, int channels, bool halo) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(p, DDFD_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t esz = p->esz;
+  const cuuint64_t dims[4] = {(cuuint64_t)p->n, (cuuint64_t)p->n, (cuuint64_t)p->n, (cuuint64_t)channels};
+  const cuuint64_t strides[3] = {(cuuint64_t)p->px * esz, (cuuint64_t)p->px * p->n * esz,
+                                 (cuuint64_t)p->cs * esz};
+  const cuuint32_t hx = (cuuint32_t)(16 / esz);
+  const cuuint32_t box[4] = {halo ? (cuuint32_t)STEP_TX + 2 * hx : (cuuint32_t)STEP_TX,
+                             halo ? (cuuint32_t)STEP_TY + 2 : (cuuint32_t)STEP_TY, 1, (cuuint32_t)channels};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(m, p->fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                            base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(p, DDFD_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return DDFD_OK;
+}
+
+int build_maps(ddfd_problem *p) {
+  int st;
+  for (int q = 0; q < 2; ++q)
+    if ((st = encode_map(p, &p->mE_halo[q], p->E[q], 3, true)) || (st = encode_map(p, &p->mE_ctr[q], p->E[q], 3, false)) ||
+        (st = encode_map(p, &p->mM_halo[q], p->Mu[q], 3, true)) || (st = encode_map(p, &p->mM_ctr[q], p->Mu[q], 3, false)))
+      return st;
+  return encode_map(p, &p->mK, p->kcoef, 2, true);
+}
+
+int check_err(ddfd_problem *p) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, p->errflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (e) {
+    CK(cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream));
+    return fail(p, DDFD_E_TIMEOUT, "a step kernel gave up a bounded wait on its TMA pipeline");
+  }
   return DDFD_OK;
 }
 
@@ -405,7 +465,7 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
   if (st) return st;
   if (flag) return fail(p, DDFD_E_COEFF, "coefficient outside [1, eps_max] x [0, sig_max] or non-finite");
   CK(cudaMemcpyAsync(p->coef, p->coef_stage, 4 * nfb, cudaMemcpyDeviceToDevice, p->stream));
-  launch_expand_coeffs(p->fp32, p->coef, p->nf, p->fem_n, p->tau, p->s_box, p->c_box, p->stream);
+  launch_expand_coeffs(p->fp32, p->coef, p->nf, p->f0, p->n, p->px, p->cs, p->tau, p->kcoef, p->stream);
   ++p->launches;
   p->state = ST_READY;
   if (p->cfg.cfl_check) {
@@ -416,8 +476,9 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
 }
 
 int forward_impl(ddfd_problem *p, double *trace_out, cudaMemcpyKind kind) {
-  const int st = p->fp32 ? enqueue_forward<float>(p) : enqueue_forward<double>(p);
+  int st = p->fp32 ? enqueue_forward<float>(p) : enqueue_forward<double>(p);
   if (st) return st;
+  if ((st = check_err(p))) return st;
   const long long cnt = (long long)p->n_src * (p->Nt + 1) * p->n_det * 3;
   CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream));
   launch_nonfinite(p->trace, cnt, p->flag, p->stream);
@@ -469,8 +530,9 @@ int adjoint_impl(ddfd_problem *p, const double *eobs, bool host) {
   }
   launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
   ++p->launches;
-  const int st = p->fp32 ? enqueue_adjoint<float>(p) : enqueue_adjoint<double>(p);
+  int st = p->fp32 ? enqueue_adjoint<float>(p) : enqueue_adjoint<double>(p);
   if (st) return st;
+  if ((st = check_err(p))) return st;
   const int s2 = sync_check(p);
   if (s2) return s2;
   p->state = ST_ADJOINT;
@@ -557,6 +619,8 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   p->nf = cfg->fem_n - 4;
   p->n_free = (long long)p->nf * p->nf * p->nf;
   p->nn = (long long)p->n * p->n * p->n;
+  p->px = (p->n + 7) / 8 * 8;
+  p->cs = (long long)p->px * p->n * p->n;
   p->Nt = cfg->n_steps;
   p->n_src = cfg->n_src;
   p->n_det = cfg->n_det;
@@ -588,13 +652,12 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   }
   std::vector<double> delay_host;
   setup_sources(p, &delay_host);
-  const size_t fbytes = 3 * (size_t)p->nn * p->esz;
-  const size_t boxn = (size_t)p->fem_n * p->fem_n * p->fem_n;
+  const size_t fbytes = 3 * (size_t)p->cs * p->esz;
   const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
   const size_t histn = (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
   if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
       (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
-      (st = dalloc(p, boxn * p->esz, &p->s_box)) || (st = dalloc(p, boxn * p->esz, &p->c_box)) ||
+      (st = dalloc(p, 2 * (size_t)p->cs * p->esz, &p->kcoef)) || (st = dalloc_t(p, 1, &p->errflag)) ||
       (st = dalloc(p, histn * p->esz, &p->hist)) || (st = dalloc_t(p, trn, &p->trace)) ||
       (st = dalloc_t(p, trn, &p->res)) || (st = dalloc_t(p, trn, &p->eobs_stage)) ||
       (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gacc)) || (st = dalloc_t(p, 4 * (size_t)p->n_free, &p->coef)) ||
@@ -620,7 +683,7 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
       dlist((size_t)std::max(p->n_det, 1), 0);
   for (int d = 0; d < p->n_det; ++d) {
     const int i = p->det_ij[2 * d], j = p->det_ij[2 * d + 1];
-    dnode[d] = i + p->n * (j + p->n * (p->n - 1));
+    dnode[d] = (int)(i + (long long)p->px * (j + (long long)p->n * (p->n - 1)));
     dptr[i + p->n * j + 1]++;
   }
   for (int q = 0; q < p->n * p->n; ++q) dptr[q + 1] += dptr[q];
@@ -641,10 +704,18 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
     p->err = "table upload failed";
     return bail(DDFD_E_CUDA);
   }
+  if (cudaMemsetAsync(p->kcoef, 0, 2 * (size_t)p->cs * p->esz, p->stream) ||
+      cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream) || cudaMemsetAsync(p->E[0], 0, fbytes, p->stream) ||
+      cudaMemsetAsync(p->E[1], 0, fbytes, p->stream) || cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream) ||
+      cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream)) {
+    p->err = "memset failed";
+    return bail(DDFD_E_CUDA);
+  }
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
     p->err = std::string("create: ") + cudaGetErrorString(cudaGetLastError());
     return bail(DDFD_E_CUDA);
   }
+  if ((st = build_maps(p))) return bail(st);
   // vacuum coefficients
   std::vector<double> one((size_t)p->n_free, 1.0), zero((size_t)p->n_free, 0.0);
   const bool chk = p->cfg.cfl_check != 0;
@@ -765,7 +836,7 @@ int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps) {
     return fail(p, DDFD_E_ARG, "capture count must be in [0, 16]");
   for (int q = 0; q < count; ++q)
     if (steps[q] < 0 || steps[q] > p->Nt) return fail(p, DDFD_E_ARG, "capture step out of range");
-  const size_t fbytes = 3 * (size_t)p->nn * p->esz;
+  const size_t fbytes = 3 * (size_t)p->cs * p->esz;
   if (count > (int)p->cap_steps.size() || !p->capE) {
     // grow: allocate fresh buffers for count slots
     int st;
@@ -782,16 +853,22 @@ int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out) {
   p->err.clear();
   if (idx < 0 || idx >= (int)p->cap_steps.size() || (kind != 0 && kind != 1))
     return fail(p, DDFD_E_ARG, "bad capture index or kind");
-  const size_t cnt = 3 * (size_t)p->nn;
+  const size_t cnt = 3 * (size_t)p->cs;
   const char *src = (const char *)(kind == 0 ? p->capE : p->capMu) + idx * cnt * p->esz;
   CK(cudaStreamSynchronize(p->stream));
+  std::vector<double> tmp(cnt);
   if (p->fp32) {
-    std::vector<float> tmp(cnt);
-    CK(cudaMemcpy(tmp.data(), src, cnt * 4, cudaMemcpyDeviceToHost));
-    for (size_t q = 0; q < cnt; ++q) out[q] = tmp[q];
+    std::vector<float> tf(cnt);
+    CK(cudaMemcpy(tf.data(), src, cnt * 4, cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < cnt; ++q) tmp[q] = tf[q];
   } else {
-    CK(cudaMemcpy(out, src, cnt * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tmp.data(), src, cnt * 8, cudaMemcpyDeviceToHost));
   }
+  const int n = p->n;
+  for (int c = 0; c < 3; ++c)
+    for (long long kj = 0; kj < (long long)n * n; ++kj)
+      for (int i = 0; i < n; ++i)
+        out[(size_t)c * p->nn + kj * n + i] = tmp[(size_t)c * p->cs + kj * p->px + i];
   return DDFD_OK;
 }
 

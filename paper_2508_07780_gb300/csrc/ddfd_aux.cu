@@ -46,33 +46,28 @@ void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const
     k_gather_trace<double><<<nb, 256, 0, s>>>((const double *)E, cs, n_det, det_node, trace_n);
 }
 
-// s = eps - 1 and c = sigma tau / 2 over the FEM box; zero off the free nodes.
+// s = eps - 1 (channel 0) and c = sigma tau / 2 (channel 1) at the free
+// nodes of the padded full-grid coefficient field.
 template <typename T>
-__global__ void k_expand(const double *coef, int nf, int fb, double tau, T *s_box, T *c_box) {
-  const long long nb = (long long)fb * fb * fb;
+__global__ void k_expand(const double *coef, int nf, int f0, int n, int px, long long cs, double tau, T *out) {
   const long long n_free = (long long)nf * nf * nf;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nb;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int li = (int)(q % fb), lj = (int)((q / fb) % fb), lk = (int)(q / ((long long)fb * fb));
-    T sv = T(0), cv = T(0);
-    if (li >= 2 && li < 2 + nf && lj >= 2 && lj < 2 + nf && lk >= 2 && lk < 2 + nf) {
-      const long long f = (li - 2) + (long long)nf * ((lj - 2) + (long long)nf * (lk - 2));
-      sv = (T)(coef[f] - 1.0);
-      cv = (T)(coef[n_free + f] * tau * 0.5);
-    }
-    s_box[q] = sv;
-    c_box[q] = cv;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n_free;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int li = (int)(f % nf), lj = (int)((f / nf) % nf), lk = (int)(f / ((long long)nf * nf));
+    const long long off = (f0 + li) + (long long)px * ((f0 + lj) + (long long)n * (f0 + lk));
+    out[off] = (T)(coef[f] - 1.0);
+    out[cs + off] = (T)(coef[n_free + f] * tau * 0.5);
   }
 }
 
-void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int fem_n, double tau,
-                          void *s_box, void *c_box, cudaStream_t s) {
-  const long long nb = (long long)fem_n * fem_n * fem_n;
-  const int blocks = (int)((nb + 255) / 256 < 4096 ? (nb + 255) / 256 : 4096);
+void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int n, int px,
+                          long long cs, double tau, void *coef, cudaStream_t s) {
+  const long long nfree = (long long)nf * nf * nf;
+  const int blocks = (int)((nfree + 255) / 256 < 4096 ? (nfree + 255) / 256 : 4096);
   if (fp32)
-    k_expand<float><<<blocks, 256, 0, s>>>(coef_free, nf, fem_n, tau, (float *)s_box, (float *)c_box);
+    k_expand<float><<<blocks, 256, 0, s>>>(coef_free, nf, f0, n, px, cs, tau, (float *)coef);
   else
-    k_expand<double><<<blocks, 256, 0, s>>>(coef_free, nf, fem_n, tau, (double *)s_box, (double *)c_box);
+    k_expand<double><<<blocks, 256, 0, s>>>(coef_free, nf, f0, n, px, cs, tau, (double *)coef);
 }
 
 __global__ void k_check(const double *coef, int n_free, double eps_max, double sig_max, int *flag) {

@@ -2,6 +2,7 @@
 // ddfd library (GB300 / sm_103a).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,19 +29,24 @@ bool build_kuhn_blocks(KuhnBlocks *out, std::string *msg);
 // Uploads the blocks to constant memory (both precisions).
 cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
 
+// Step-kernel tiling: a CTA owns a STEP_TX x STEP_TY (x, y) tile of one z
+// chunk; STEP_RING shared-memory stages hold staged planes.
+constexpr int STEP_TX = 32;
+constexpr int STEP_TY = 8;
+constexpr int STEP_RING = 6;
+
 // Geometry and per-step scalars common to the forward and adjoint steps.
+// Fields are component-major with x pitch px: offset i + px (j + n k).
 template <typename T>
 struct StepParams {
   int n;                 // nodes per axis
+  int px;                // x pitch of the padded layout (multiple of 8)
   int a, b;              // FEM box [a,b]
   int f0, nf;            // free box origin and side
-  int kz;                // z planes per thread block
-  long long cs;          // component stride (n^3)
-  const T *cur;          // E^n (forward) or mu^k (adjoint), 3 components
-  T *old;                // E^{n-1} in, E^{n+1} out (forward); mu^{k+1} in, mu^{k-1} out
-  const T *s_box;        // eps - 1 over the FEM box, fem_n^3
-  const T *c_box;        // sigma * tau / 2 over the FEM box
-  int fem_n;
+  int kz;                // z planes per CTA
+  long long cs;          // component stride (px n^2)
+  const T *cur;          // E^n (forward) or mu^k (adjoint): detector gather only
+  T *old;                // written: E^{n+1} (forward) or mu^{k-1} (adjoint)
   T r2;                  // (tau/h)^2
   T cb;                  // tau/h: damping of one absorbing face, divided form
   uint32_t abs_now;      // forward: absorbing faces at step n; adjoint: at step k-1
@@ -49,7 +55,7 @@ struct StepParams {
   int src_on;            // 1 while n <= n1
   int oblique;           // 0: normal incidence, value src_y on the y component
   T src_y;               // 2 tau^2 / h * P(t_n) (normal incidence)
-  const double *delay;   // oblique: delay of each top node, n^2
+  const double *delay;   // oblique: delay of each top node, n^2 (i + n j)
   double pol[3];         // oblique: polarisation
   double t_n;            // time of the step
   double src_scale;      // 2 tau^2 / h
@@ -57,9 +63,9 @@ struct StepParams {
   double freq, t0, width;
   // detectors
   int n_det;
-  const int *det_node;   // forward gather: node id of each detector
+  const int *det_node;   // forward gather: padded offset of each detector node
   double *trace_n;       // forward: trace[n] base ([n_det][3]), gathered from cur
-  const int *det_ptr;    // adjoint: CSR over top-plane nodes (n^2 + 1)
+  const int *det_ptr;    // adjoint: CSR over top-plane nodes (i + n j; n^2 + 1)
   const int *det_list;
   const double *res_k;   // adjoint: residual tau z (E^k - Eobs^k), [n_det][3]
   double inv_h3;         // 1 / h^3
@@ -70,18 +76,24 @@ struct StepParams {
   long long n_free;
   double *gacc_e;        // adjoint: gradient accumulators (FP64)
   double *gacc_s;
+  int *err;              // bit 4: a bounded mbarrier wait gave up
+  uint32_t spin_limit;   // polls per bounded wait
 };
 
 template <typename T>
-void launch_forward_step(const StepParams<T> &P, cudaStream_t s);
+void launch_forward_step(const CUtensorMap &mcur, const CUtensorMap &mold, const CUtensorMap &mcoef,
+                         const StepParams<T> &P, cudaStream_t s);
 template <typename T>
-void launch_adjoint_step(const StepParams<T> &P, cudaStream_t s);
+void launch_adjoint_step(const CUtensorMap &mcur, const CUtensorMap &mold, const CUtensorMap &mcoef,
+                         const StepParams<T> &P, cudaStream_t s);
 
 // Small kernels.
 void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const int *det_node,
                          double *trace_n, cudaStream_t s);
-void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int fem_n, double tau,
-                          void *s_box, void *c_box, cudaStream_t s);
+// eps - 1 and sigma tau / 2 of the free nodes into the padded full-grid
+// coefficient field (channel 0 and 1); other nodes are never written (zero).
+void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int n, int px,
+                          long long cs, double tau, void *coef, cudaStream_t s);
 void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, double sig_max,
                          int *flag, cudaStream_t s);
 // residual r = tau z (trace - eobs) for n >= 1 (r[0] = 0); partial sums of
@@ -98,8 +110,8 @@ void launch_grad_finalize(const double *coef_free, int n_free, const double *gac
                           cudaStream_t s);
 void launch_nonfinite(const double *x, long long count, int *flag, cudaStream_t s);
 // power iteration helpers (FP64): y = M_eps^-1 K x, and the squared norm.
-void launch_apply_op(const double *x, double *y, int n, int a, int b, const void *s_box, int fp32,
-                     int fem_n, cudaStream_t s);
+void launch_apply_op(const double *x, double *y, int n, int px, int a, int b, const void *coef_s, int fp32,
+                     cudaStream_t s);
 void launch_norm2(const double *x, long long count, double *part, int n_part, cudaStream_t s);
 void launch_scale(double *x, long long count, const double *norm2, cudaStream_t s);
 

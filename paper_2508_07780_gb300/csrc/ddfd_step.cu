@@ -1,12 +1,18 @@
 // Explicit step kernels of the hybrid FE/FD scheme (forward and adjoint).
 //
-// One thread owns a grid column (i, j) over kz consecutive planes and keeps
-// the planes k-1, k, k+1 of its own column in registers; in-plane neighbours
-// come through the read-only cache.  Per node and step:
+// Work decomposition: one CTA owns a 32 x 8 (x, y) tile and a chunk of kz
+// consecutive z planes; one thread per (x, y) column.  The planes of the
+// current field (with a one-node halo in y and a 16-byte-aligned halo in x),
+// the centre tile of the previous level, and (on tiles that touch the FEM
+// cube) the coefficient planes are staged into shared memory by TMA tile
+// loads through a ring of RING stages guarded by mbarriers, so that
+// several planes are in flight per CTA while the previous ones are computed.
+//
+// Per node and step:
 //   FD part (every node): 7-point Laplacian with ghost-node (mirror) Neumann
 //     closure, i.e. h^2 M^-1 L of the hexahedral FD scheme;
 //   FEM part (nodes strictly inside the FEM cube): the P1 Gauss-law term of
-//     eq. forward_prob / eq. model1 on the Kuhn mesh, as a 15-point block
+//     eq. forward_prob / eq. model1 on the Kuhn mesh as a 15-point block
 //     stencil: forward h^2 M^-1 (D^T D S E)_i = sum_o B_o (s E)_{i+o},
 //     adjoint h^2 M^-1 (S D^T D mu)_i = s_i sum_o B_o mu_{i+o};
 //   boundary: damping tau/h per absorbing face (first-order absorbing
@@ -20,9 +26,14 @@
 //     steps k-1 and k+1, detector residuals j^k / m as sources, and the
 //     gradient time sums (eq. gradeps, summation-by-parts form) accumulated in
 //     FP64 at the free nodes.
+//
+// Field layout: component-major, x pitch px (a multiple of 8 elements, so
+// TMA row strides are 16-byte multiples), offset i + px (j + n k).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ddfd_internal.h"
+#include "ddfd_tma.h"
 
 namespace ddfd {
 
@@ -51,9 +62,6 @@ cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s) {
   return cudaStreamSynchronize(s);
 }
 
-constexpr int BX = 32;
-constexpr int BY = 4;
-
 __device__ __forceinline__ double pulse_value(int kind, double f, double t0, double w, double t) {
   if (kind == DDFD_SRC_GAUSS) {
     const double s = t - t0;
@@ -78,232 +86,311 @@ __device__ __forceinline__ void block_apply(const T v0[3], const T vp[7][3], T o
   }
 }
 
-__device__ __forceinline__ int face_count_xy(int i, int j, int n, uint32_t abs) {
+__device__ __forceinline__ int face_count(int i, int j, int k, int n, uint32_t abs) {
   int f = 0;
   if (i == 0 && (abs & DDFD_ABS_X0)) ++f;
   if (i == n - 1 && (abs & DDFD_ABS_X1)) ++f;
   if (j == 0 && (abs & DDFD_ABS_Y0)) ++f;
   if (j == n - 1 && (abs & DDFD_ABS_Y1)) ++f;
-  return f;
-}
-
-__device__ __forceinline__ int face_count_z(int k, int n, uint32_t abs) {
-  int f = 0;
   if (k == 0 && (abs & DDFD_ABS_BOTTOM)) ++f;
   if (k == n - 1 && (abs & DDFD_ABS_TOP)) ++f;
   return f;
 }
 
+template <typename T>
+struct Stage {
+  static constexpr int HX = 16 / (int)sizeof(T);  // x halo: one 16-byte unit
+  static constexpr int BXW = STEP_TX + 2 * HX;     // staged row length
+  static constexpr int ROWS = STEP_TY + 2;
+  static constexpr int E_ELEMS = 3 * ROWS * BXW;
+  static constexpr int O_ELEMS = 3 * STEP_TY * STEP_TX;
+  static constexpr int C_ELEMS = 2 * ROWS * BXW;
+  static constexpr int up128(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int E_BYTES = E_ELEMS * (int)sizeof(T);
+  static constexpr int O_BYTES = O_ELEMS * (int)sizeof(T);
+  static constexpr int C_BYTES = C_ELEMS * (int)sizeof(T);
+  static constexpr int E_OFF = 0;
+  static constexpr int O_OFF = up128(E_BYTES);
+  static constexpr int C_OFF = O_OFF + up128(O_BYTES);
+  static constexpr int BYTES = C_OFF + up128(C_BYTES);
+  // FP32: 6 stages (3 CTAs per SM); FP64: 4 stages (2 CTAs per SM)
+  static constexpr int RING = sizeof(T) == 4 ? STEP_RING : 4;
+  static constexpr int SMEM = RING * BYTES + RING * 8 + 128;
+};
+
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(BX *BY) k_step(const StepParams<T> P) {
+__global__ void __launch_bounds__(STEP_TX *STEP_TY)
+    k_step(const __grid_constant__ CUtensorMap mcur, const __grid_constant__ CUtensorMap mold,
+           const __grid_constant__ CUtensorMap mcoef, const StepParams<T> P) {
+  using S = Stage<T>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);
   const int n = P.n;
   const long long cs = P.cs;
+  const int tid = threadIdx.x;
+
   if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
-    const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z * (BX * BY);
+    const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z * blockDim.x;
     long long t = ((long long)blockIdx.x + gridDim.x * ((long long)blockIdx.y + gridDim.y * blockIdx.z)) *
-                      (BX * BY) +
-                  threadIdx.x + BX * threadIdx.y;
+                      blockDim.x + tid;
     for (; t < 3LL * P.n_det; t += nb) {
       const int d = (int)(t / 3), c = (int)(t - 3LL * d);
       P.trace_n[t] = (double)P.cur[c * cs + P.det_node[d]];
     }
   }
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  if (i >= n || j >= n) return;
+
+  const int tx = tid % STEP_TX, ty = tid / STEP_TX;
+  const int x0 = blockIdx.x * STEP_TX, y0 = blockIdx.y * STEP_TY;
   const int k0 = blockIdx.z * P.kz;
-  if (k0 >= n) return;
+  if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
-  const int nn2 = n * n;
-  const int ip = (i + 1 < n) ? i + 1 : n - 2, im = (i > 0) ? i - 1 : 1;
-  const int jp = (j + 1 < n) ? j + 1 : n - 2, jm = (j > 0) ? j - 1 : 1;
-  const int row = n * j;
-  const bool colfem = (i > P.a && i < P.b && j > P.a && j < P.b);
-  const bool colfree = (i >= P.f0 && i < P.f0 + P.nf && j >= P.f0 && j < P.f0 + P.nf);
-  const int fxy_now = face_count_xy(i, j, n, P.abs_now);
-  const int fxy_next = ADJ ? face_count_xy(i, j, n, P.abs_next) : 0;
-  const int fb = P.fem_n;
-  const T *__restrict__ cur = P.cur;
-  T *__restrict__ old = P.old;
+  const int nplanes = k1 - k0 + 2;  // planes k0-1 .. k1 are staged
+  const bool tile_fem = x0 <= P.b - 1 && x0 + STEP_TX - 1 >= P.a + 1 && y0 <= P.b - 1 &&
+                        y0 + STEP_TY - 1 >= P.a + 1;
 
-  T below[3], cen[3];
-  {
-    const int kb = (k0 > 0) ? k0 - 1 : 1;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      below[c] = __ldg(cur + c * cs + (long long)kb * nn2 + row + i);
-      cen[c] = __ldg(cur + c * cs + (long long)k0 * nn2 + row + i);
-    }
+  __shared__ int sh_fail;
+  if (tid == 0) {
+    sh_fail = 0;
+    for (int s = 0; s < S::RING; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+    tma_prefetch_desc(&mcur);
+    tma_prefetch_desc(&mold);
+    tma_prefetch_desc(&mcoef);
   }
+  __syncthreads();
+
+  auto issue = [&](int p) {  // thread 0: stage plane k0-1+p into slot p % S::RING
+    const int kk = k0 - 1 + p;
+    const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
+    unsigned char *st = smem + (p % S::RING) * S::BYTES;
+    const bool interior = kk >= k0 && kk < k1;
+    const bool coef = tile_fem && kk >= P.a && kk <= P.b;
+    const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::C_BYTES : 0);
+    uint64_t *b = &bar[p % S::RING];
+    mbar_expect_tx(b, bytes);
+    tma_load_4d(st + S::E_OFF, &mcur, x0 - S::HX, y0 - 1, ksrc, 0, b);
+    if (interior) tma_load_4d(st + S::O_OFF, &mold, x0, y0, kk, 0, b);
+    if (coef) tma_load_4d(st + S::C_OFF, &mcoef, x0 - S::HX, y0 - 1, kk, 0, b);
+  };
+  int issued = 0;  // thread 0: planes issued so far
+  if (tid == 0) {
+    const int first = nplanes < S::RING ? nplanes : S::RING;
+    for (int p = 0; p < first; ++p) issue(p);
+    issued = first;
+  }
+
+  const int x = x0 + tx, y = y0 + ty;
+  const bool live = x < n && y < n;
+  const int ci = (ty + 1) * S::BXW + (tx + S::HX);
+  const int dxm = (x == 0) ? 1 : -1, dxp = (x == n - 1) ? -1 : 1;
+  const int dym = (y == 0) ? S::BXW : -S::BXW, dyp = (y == n - 1) ? -S::BXW : S::BXW;
+  const bool colfem = x > P.a && x < P.b && y > P.a && y < P.b;
+  const bool colfree = x >= P.f0 && x < P.f0 + P.nf && y >= P.f0 && y < P.f0 + P.nf;
+  const long long rowoff = (long long)P.px * y + x;
+  bool failed = false;
+  int waited = 0;
+
   for (int k = k0; k < k1; ++k) {
-    const int kp = (k + 1 < n) ? k + 1 : n - 2;
-    const long long pb = (long long)k * nn2;
-    const long long me = pb + row + i;
-    T above[3], xp[3], xm[3], yp[3], ym[3], lap[3], st[3] = {T(0), T(0), T(0)}, sx[3] = {T(0), T(0), T(0)};
+    const int p = k - k0 + 1;  // plane index of k in the stage sequence
+    // fetch the free-node history / accumulators before waiting on TMA
+    const bool fre = colfree && k >= P.f0 && k < P.f0 + P.nf && live;
+    long long fi = 0;
+    T hv[3] = {T(0), T(0), T(0)};
+    double ga = 0.0, gb = 0.0;
+    if (fre) {
+      fi = (x - P.f0) + (long long)P.nf * ((y - P.f0) + (long long)P.nf * (k - P.f0));
+      if (ADJ) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T *pc = cur + c * cs + pb;
-      above[c] = __ldg(cur + c * cs + (long long)kp * nn2 + row + i);
-      xp[c] = __ldg(pc + row + ip);
-      xm[c] = __ldg(pc + row + im);
-      yp[c] = __ldg(pc + n * jp + i);
-      ym[c] = __ldg(pc + n * jm + i);
-      lap[c] = T(6) * cen[c] - (xp[c] + xm[c] + yp[c] + ym[c] + above[c] + below[c]);
-    }
-    T eps = T(1), cc, ccn = T(0);
-    const bool fem = colfem && k > P.a && k < P.b;
-    const bool fre = colfree && k >= P.f0 && k < P.f0 + P.nf;
-    if (fem) {
-      const long long bi = (i - P.a) + (long long)fb * ((j - P.a) + (long long)fb * (k - P.a));
-      const T s0 = __ldg(P.s_box + bi);
-      eps = T(1) + s0;
-      cc = __ldg(P.c_box + bi);
-      ccn = cc;
-      // offsets of the 7 pairs in the grid and in the box
-      const long long og[7] = {1, n, nn2, 1 + n, 1 + nn2, n + nn2, 1 + n + nn2};
-      const long long ob[7] = {1, fb, (long long)fb * fb, 1 + fb, 1 + (long long)fb * fb,
-                               fb + (long long)fb * fb, 1 + fb + (long long)fb * fb};
-      T v0[3], vp[7][3];
-      if (!ADJ) {
-        // w = s E at the centre and the 14 neighbours
-        T sp[7], sm[7];
-#pragma unroll
-        for (int p = 0; p < 7; ++p) {
-          sp[p] = __ldg(P.s_box + bi + ob[p]);
-          sm[p] = __ldg(P.s_box + bi - ob[p]);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T *pc = cur + c * cs;
-          v0[c] = s0 * cen[c];
-          vp[0][c] = sp[0] * xp[c] + sm[0] * xm[c];
-          vp[1][c] = sp[1] * yp[c] + sm[1] * ym[c];
-          vp[2][c] = sp[2] * above[c] + sm[2] * below[c];
-#pragma unroll
-          for (int p = 3; p < 7; ++p) vp[p][c] = sp[p] * __ldg(pc + me + og[p]) + sm[p] * __ldg(pc + me - og[p]);
-        }
-        block_apply<T>(v0, vp, st);
-      } else if (fre) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T *pc = cur + c * cs;
-          v0[c] = cen[c];
-          vp[0][c] = xp[c] + xm[c];
-          vp[1][c] = yp[c] + ym[c];
-          vp[2][c] = above[c] + below[c];
-#pragma unroll
-          for (int p = 3; p < 7; ++p) vp[p][c] = __ldg(pc + me + og[p]) + __ldg(pc + me - og[p]);
-        }
-        block_apply<T>(v0, vp, sx);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) st[c] = s0 * sx[c];
+        for (int c = 0; c < 3; ++c) hv[c] = __ldg(P.hist_r + c * P.n_free + fi);
+        ga = P.gacc_e[fi];
+        gb = P.gacc_s[fi];
       }
-    } else {
-      cc = P.cb * T(fxy_now + face_count_z(k, n, P.abs_now));
-      if (ADJ) ccn = P.cb * T(fxy_next + face_count_z(k, n, P.abs_next));
     }
-    T R[3];
+    bool ok = true;
+    while (waited <= p + 1 && waited < nplanes) {
+      if (!mbar_wait_bounded(&bar[waited % S::RING], (uint32_t)((waited / S::RING) & 1), P.spin_limit)) {
+        ok = false;
+        break;
+      }
+      ++waited;
+    }
+    if (!ok) sh_fail = 1;  // read by every thread after the barrier below
+    const T *Em = (const T *)(smem + ((p - 1) % S::RING) * S::BYTES + S::E_OFF);
+    const T *E0 = (const T *)(smem + (p % S::RING) * S::BYTES + S::E_OFF);
+    const T *Ep = (const T *)(smem + ((p + 1) % S::RING) * S::BYTES + S::E_OFF);
+    const T *O0 = (const T *)(smem + (p % S::RING) * S::BYTES + S::O_OFF);
+    const T *C0 = (const T *)(smem + (p % S::RING) * S::BYTES + S::C_OFF);
+    const T *Cm = (const T *)(smem + ((p - 1) % S::RING) * S::BYTES + S::C_OFF);
+    const T *Cp = (const T *)(smem + ((p + 1) % S::RING) * S::BYTES + S::C_OFF);
+    if (ok && live) {
+      constexpr int RE = S::ROWS * S::BXW;  // component / channel stride of a staged plane
+      T cen[3], lap[3], st[3] = {T(0), T(0), T(0)}, sx[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) R[c] = P.r2 * (lap[c] + st[c]);
-    if (!ADJ && k == n - 1 && P.src_on) {
-      if (!P.oblique) {
-        R[1] -= P.src_y;
+      for (int c = 0; c < 3; ++c) {
+        const T *e = E0 + c * RE;
+        cen[c] = e[ci];
+        lap[c] = T(6) * cen[c] - (e[ci + dxp] + e[ci + dxm] + e[ci + dyp] + e[ci + dym] + Ep[c * RE + ci] +
+                                  Em[c * RE + ci]);
+      }
+      T eps = T(1), cc, ccn = T(0);
+      const bool fem = colfem && k > P.a && k < P.b;
+      if (fem) {
+        const T s0 = C0[ci];
+        eps = T(1) + s0;
+        cc = C0[RE + ci];
+        ccn = cc;
+        constexpr int B = S::BXW;
+        T v0[3], vp[7][3];
+        if (!ADJ) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T *e0 = E0 + c * RE, *ep = Ep + c * RE, *em = Em + c * RE;
+            v0[c] = s0 * cen[c];
+            vp[0][c] = C0[ci + 1] * e0[ci + 1] + C0[ci - 1] * e0[ci - 1];
+            vp[1][c] = C0[ci + B] * e0[ci + B] + C0[ci - B] * e0[ci - B];
+            vp[2][c] = Cp[ci] * ep[ci] + Cm[ci] * em[ci];
+            vp[3][c] = C0[ci + 1 + B] * e0[ci + 1 + B] + C0[ci - 1 - B] * e0[ci - 1 - B];
+            vp[4][c] = Cp[ci + 1] * ep[ci + 1] + Cm[ci - 1] * em[ci - 1];
+            vp[5][c] = Cp[ci + B] * ep[ci + B] + Cm[ci - B] * em[ci - B];
+            vp[6][c] = Cp[ci + 1 + B] * ep[ci + 1 + B] + Cm[ci - 1 - B] * em[ci - 1 - B];
+          }
+          block_apply<T>(v0, vp, st);
+        } else if (s0 != T(0) || fre) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T *e0 = E0 + c * RE, *ep = Ep + c * RE, *em = Em + c * RE;
+            v0[c] = cen[c];
+            vp[0][c] = e0[ci + 1] + e0[ci - 1];
+            vp[1][c] = e0[ci + B] + e0[ci - B];
+            vp[2][c] = ep[ci] + em[ci];
+            vp[3][c] = e0[ci + 1 + B] + e0[ci - 1 - B];
+            vp[4][c] = ep[ci + 1] + em[ci - 1];
+            vp[5][c] = ep[ci + B] + em[ci - B];
+            vp[6][c] = ep[ci + 1 + B] + em[ci - 1 - B];
+          }
+          block_apply<T>(v0, vp, sx);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) st[c] = s0 * sx[c];
+        }
       } else {
-        const double v = P.src_scale * pulse_value(P.pulse_kind, P.freq, P.t0, P.width,
-                                                   P.t_n - P.delay[row + i]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) R[c] -= (T)(P.pol[c] * v);
+        cc = P.cb * T(face_count(x, y, k, n, P.abs_now));
+        if (ADJ) ccn = P.cb * T(face_count(x, y, k, n, P.abs_next));
       }
-    }
-    if (ADJ && k == n - 1 && P.n_det > 0) {
-      const int q0 = P.det_ptr[row + i], q1 = P.det_ptr[row + i + 1];
-      if (q1 > q0) {
-        const double wx = (i == 0 || i == n - 1) ? 0.5 : 1.0;
-        const double wy = (j == 0 || j == n - 1) ? 0.5 : 1.0;
-        const double sc = P.tau2 * P.inv_h3 / (wx * wy * 0.5);
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int q = q0; q < q1; ++q) {
-          const int d = P.det_list[q];
-          acc[0] += P.res_k[3 * d + 0];
-          acc[1] += P.res_k[3 * d + 1];
-          acc[2] += P.res_k[3 * d + 2];
+      T R[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) R[c] = P.r2 * (lap[c] + st[c]);
+      if (!ADJ && k == n - 1 && P.src_on) {
+        if (!P.oblique) {
+          R[1] -= P.src_y;
+        } else {
+          const double v = P.src_scale * pulse_value(P.pulse_kind, P.freq, P.t0, P.width,
+                                                     P.t_n - P.delay[x + n * y]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) R[c] -= (T)(P.pol[c] * v);
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) R[c] += (T)(sc * acc[c]);
       }
-    }
-    T nw[3], od[3];
-    if (!ADJ) {
+      if (ADJ && k == n - 1 && P.n_det > 0) {
+        const int q0 = P.det_ptr[x + n * y], q1 = P.det_ptr[x + n * y + 1];
+        if (q1 > q0) {
+          const double wx = (x == 0 || x == n - 1) ? 0.5 : 1.0;
+          const double wy = (y == 0 || y == n - 1) ? 0.5 : 1.0;
+          const double sc = P.tau2 * P.inv_h3 / (wx * wy * 0.5);
+          double acc[3] = {0.0, 0.0, 0.0};
+          for (int q = q0; q < q1; ++q) {
+            const int d = P.det_list[q];
+            acc[0] += P.res_k[3 * d + 0];
+            acc[1] += P.res_k[3 * d + 1];
+            acc[2] += P.res_k[3 * d + 2];
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) R[c] += (T)(sc * acc[c]);
+        }
+      }
+      const long long me = (long long)k * P.px * n + rowoff;
+      const int oi = ty * STEP_TX + tx;
+      T nw[3], od[3];
       const T inv = T(1) / (eps + cc);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        od[c] = old[c * cs + me];
-        nw[c] = cen[c] + ((eps - cc) * (cen[c] - od[c]) - R[c]) * inv;
-        old[c * cs + me] = nw[c];
+        od[c] = O0[c * (STEP_TX * STEP_TY) + oi];
+        if (!ADJ)
+          nw[c] = cen[c] + ((eps - cc) * (cen[c] - od[c]) - R[c]) * inv;
+        else  // cc: damping at step k-1, ccn: at step k+1
+          nw[c] = cen[c] + ((eps - ccn) * (cen[c] - od[c]) + (ccn - cc) * cen[c] - R[c]) * inv;
+        P.old[c * cs + me] = nw[c];
       }
       if (fre) {
-        const long long fi = (i - P.f0) + (long long)P.nf * ((j - P.f0) + (long long)P.nf * (k - P.f0));
+        if (!ADJ) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) P.hist_w[c * P.n_free + fi] = nw[c];
-      }
-    } else {
-      // cc: damping at step k-1, ccn: at step k+1
-      const T inv = T(1) / (eps + cc);
+          for (int c = 0; c < 3; ++c) P.hist_w[c * P.n_free + fi] = nw[c];
+        } else {
+          T ge = T(0), gs = T(0);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        od[c] = old[c * cs + me];
-        nw[c] = cen[c] + ((eps - ccn) * (cen[c] - od[c]) + (ccn - cc) * cen[c] - R[c]) * inv;
-        old[c * cs + me] = nw[c];
-      }
-      if (fre) {
-        const long long fi = (i - P.f0) + (long long)P.nf * ((j - P.f0) + (long long)P.nf * (k - P.f0));
-        T ge = T(0), gs = T(0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T e = __ldg(P.hist_r + c * P.n_free + fi);
-          ge += e * ((nw[c] - T(2) * cen[c] + od[c]) + P.r2 * sx[c]);
-          gs += e * (nw[c] - od[c]);
+          for (int c = 0; c < 3; ++c) {
+            ge += hv[c] * ((nw[c] - T(2) * cen[c] + od[c]) + P.r2 * sx[c]);
+            gs += hv[c] * (nw[c] - od[c]);
+          }
+          P.gacc_e[fi] = ga + (double)ge;
+          P.gacc_s[fi] = gb + (double)gs;
         }
-        P.gacc_e[fi] += (double)ge;
-        P.gacc_s[fi] += (double)gs;
       }
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      below[c] = cen[c];
-      cen[c] = above[c];
+    __syncthreads();  // every thread is done with plane k-1's slot
+    if (sh_fail) {    // uniform across the CTA: decided before the barrier
+      failed = true;
+      break;
     }
+    if (tid == 0 && p - 1 + S::RING < nplanes) {
+      issue(p - 1 + S::RING);
+      issued = p + S::RING;
+    }
+  }
+  if (failed && tid == 0) {
+    atomicOr(P.err, 4);
+    // let the copies already issued land before the CTA exits (bounded)
+    for (int q = waited; q < issued; ++q)
+      mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), P.spin_limit);
   }
 }
 
-template <typename T>
-static dim3 step_grid(const StepParams<T> &P) {
-  return dim3((P.n + BX - 1) / BX, (P.n + BY - 1) / BY, (P.n + P.kz - 1) / P.kz);
+template <typename T, bool ADJ>
+static void launch_step(const CUtensorMap &mc, const CUtensorMap &mo, const CUtensorMap &mk,
+                        const StepParams<T> &P, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_step<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<T>::SMEM);
+    attr_set = true;
+  }
+  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + STEP_TY - 1) / STEP_TY, (P.n + P.kz - 1) / P.kz);
+  k_step<T, ADJ><<<grid, STEP_TX * STEP_TY, Stage<T>::SMEM, s>>>(mc, mo, mk, P);
 }
 
 template <typename T>
-void launch_forward_step(const StepParams<T> &P, cudaStream_t s) {
-  k_step<T, false><<<step_grid(P), dim3(BX, BY), 0, s>>>(P);
+void launch_forward_step(const CUtensorMap &mc, const CUtensorMap &mo, const CUtensorMap &mk,
+                         const StepParams<T> &P, cudaStream_t s) {
+  launch_step<T, false>(mc, mo, mk, P, s);
 }
 template <typename T>
-void launch_adjoint_step(const StepParams<T> &P, cudaStream_t s) {
-  k_step<T, true><<<step_grid(P), dim3(BX, BY), 0, s>>>(P);
+void launch_adjoint_step(const CUtensorMap &mc, const CUtensorMap &mo, const CUtensorMap &mk,
+                         const StepParams<T> &P, cudaStream_t s) {
+  launch_step<T, true>(mc, mo, mk, P, s);
 }
 
-template void launch_forward_step<float>(const StepParams<float> &, cudaStream_t);
-template void launch_forward_step<double>(const StepParams<double> &, cudaStream_t);
-template void launch_adjoint_step<float>(const StepParams<float> &, cudaStream_t);
-template void launch_adjoint_step<double>(const StepParams<double> &, cudaStream_t);
-
-}  // namespace ddfd
-
-namespace ddfd {
+template void launch_forward_step<float>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                                         const StepParams<float> &, cudaStream_t);
+template void launch_forward_step<double>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                                          const StepParams<double> &, cudaStream_t);
+template void launch_adjoint_step<float>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                                         const StepParams<float> &, cudaStream_t);
+template void launch_adjoint_step<double>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                                          const StepParams<double> &, cudaStream_t);
 
 // y = h^2 M_eps^-1 K x in FP64 on every node (no damping, no source): the
 // operator whose largest eigenvalue bounds the stable time step.  One thread
-// per node; used only by the stability check.
+// per node; x, y unpadded (3 n^3); s read from the padded coefficient field.
 template <typename T>
-__global__ void k_apply_op(const double *x, double *y, int n, int a, int b, const T *s_box, int fb) {
+__global__ void k_apply_op(const double *x, double *y, int n, int px, int a, int b, const T *coef_s) {
   const long long nn = (long long)n * n * n;
   const long long nn2 = (long long)n * n;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nn;
@@ -321,18 +408,20 @@ __global__ void k_apply_op(const double *x, double *y, int n, int a, int b, cons
     }
     double eps = 1.0;
     if (i > a && i < b && j > a && j < b && k > a && k < b) {
-      const long long bi = (i - a) + (long long)fb * ((j - a) + (long long)fb * (k - a));
-      const double s0 = (double)s_box[bi];
+      auto sv = [&](int di, int dj, int dk) {
+        return (double)coef_s[(i + di) + (long long)px * ((j + dj) + (long long)n * (k + dk))];
+      };
+      const double s0 = sv(0, 0, 0);
       eps = 1.0 + s0;
-      const long long og[7] = {1, n, nn2, 1 + n, 1 + nn2, n + nn2, 1 + n + nn2};
-      const long long ob[7] = {1, fb, (long long)fb * fb, 1 + fb, 1 + (long long)fb * fb,
-                               fb + (long long)fb * fb, 1 + fb + (long long)fb * fb};
+      const int dx[7] = {1, 0, 0, 1, 1, 0, 1}, dy[7] = {0, 1, 0, 1, 0, 1, 1}, dz[7] = {0, 0, 1, 0, 1, 1, 1};
       double v0[3], vp[7][3], st[3];
       for (int c = 0; c < 3; ++c) v0[c] = s0 * x[c * nn + q];
-      for (int p = 0; p < 7; ++p)
+      for (int p = 0; p < 7; ++p) {
+        const long long og = dx[p] + n * (dy[p] + (long long)n * dz[p]);
         for (int c = 0; c < 3; ++c)
-          vp[p][c] = (double)s_box[bi + ob[p]] * x[c * nn + q + og[p]] +
-                     (double)s_box[bi - ob[p]] * x[c * nn + q - og[p]];
+          vp[p][c] = sv(dx[p], dy[p], dz[p]) * x[c * nn + q + og] +
+                     sv(-dx[p], -dy[p], -dz[p]) * x[c * nn + q - og];
+      }
       block_apply<double>(v0, vp, st);
       for (int c = 0; c < 3; ++c) out[c] += st[c];
     }
@@ -340,15 +429,15 @@ __global__ void k_apply_op(const double *x, double *y, int n, int a, int b, cons
   }
 }
 
-void launch_apply_op(const double *x, double *y, int n, int a, int b, const void *s_box, int fp32,
-                     int fem_n, cudaStream_t s) {
+void launch_apply_op(const double *x, double *y, int n, int px, int a, int b, const void *coef_s, int fp32,
+                     cudaStream_t s) {
   const long long nn = (long long)n * n * n;
   const long long nb = (nn + 255) / 256;
   const int blocks = (int)(nb < 8192 ? nb : 8192);
   if (fp32)
-    k_apply_op<float><<<blocks, 256, 0, s>>>(x, y, n, a, b, (const float *)s_box, fem_n);
+    k_apply_op<float><<<blocks, 256, 0, s>>>(x, y, n, px, a, b, (const float *)coef_s);
   else
-    k_apply_op<double><<<blocks, 256, 0, s>>>(x, y, n, a, b, (const double *)s_box, fem_n);
+    k_apply_op<double><<<blocks, 256, 0, s>>>(x, y, n, px, a, b, (const double *)coef_s);
 }
 
 }  // namespace ddfd
