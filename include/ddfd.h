@@ -99,6 +99,8 @@ typedef struct {
   int32_t cfl_check;     /* nonzero: estimate the stability bound by power iteration
                             at ddfd_set_coeffs and fail with DDFD_E_CFL above it */
   int64_t mem_budget;    /* device bytes the handle may allocate; 0 = no limit */
+  int32_t tile_kz;       /* z planes per thread block of the step kernels (tuning;
+                            0 = library default, else 2..n) */
   void *stream;          /* cudaStream_t for all work, or NULL for the default stream */
 } ddfd_config;
 

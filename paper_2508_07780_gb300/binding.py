@@ -47,7 +47,7 @@ class ddfd_config(ctypes.Structure):
         ("det_ij", POINTER(c_int32)), ("absorbing_faces", c_uint32), ("gamma_eps", c_double),
         ("gamma_sig", c_double), ("z_delta_frac", c_double), ("eps_max", c_double),
         ("sig_max", c_double), ("n_snapshots", c_int32), ("cfl_check", c_int32),
-        ("mem_budget", c_int64), ("stream", c_void_p),
+        ("mem_budget", c_int64), ("tile_kz", c_int32), ("stream", c_void_p),
     ]
 
 

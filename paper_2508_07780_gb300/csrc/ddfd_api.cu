@@ -48,15 +48,16 @@ struct ddfd_problem {
   std::vector<void *> allocs;
   int64_t bytes = 0;
   void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr};
-  void *kcoef = nullptr;      // padded full-grid (eps - 1, sigma tau / 2), 2 channels
+  void *kcoef = nullptr;      // padded full-grid (s, q1, q2), 3 channels
   void *hist = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
   double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
   double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
   int *det_node = nullptr, *det_ptr = nullptr, *det_list = nullptr, *flag = nullptr;
   int *errflag = nullptr;     // kernel-side error bits (bounded waits)
+
   // TMA descriptors: [buffer] halo-box (current level) and centre-box (old level)
-  CUtensorMap mE_halo[2], mE_ctr[2], mM_halo[2], mM_ctr[2], mK;
+  CUtensorMap mE_halo[2], mE_ctr[2], mM_halo[2], mM_ctr[2], mS, mQ;
   std::vector<double> ptab;  // [n_src][Nt] pulse value P(t_n) (normal incidence), 0 after n1
   std::vector<int> n1, oblique;
   std::vector<double> pol;   // [n_src][3]
@@ -138,6 +139,7 @@ int validate(const ddfd_config *c, std::string *m) {
   if (!(c->eps_max >= 1.0) || !(c->sig_max >= 0.0)) return *m = "bad coefficient bounds", DDFD_E_ARG;
   if (c->n_snapshots != 0) return *m = "n_snapshots > 0 (checkpointing) is not built", DDFD_E_ARG;
   if (c->mem_budget < 0) return *m = "mem_budget must be >= 0", DDFD_E_ARG;
+  if (c->tile_kz != 0 && (c->tile_kz < 2 || c->tile_kz > c->n)) return *m = "tile_kz must be 0 or in [2, n]", DDFD_E_ARG;
   if (c->src_dir)
     for (int s = 0; s < c->n_src; ++s) {
       const double *k = c->src_dir + 3 * s;
@@ -216,6 +218,7 @@ StepParams<T> base_params(const ddfd_problem *p) {
   P.kz = p->kz;
   P.cs = p->cs;
   P.err = p->errflag;
+
   P.spin_limit = 1u << 22;
   P.r2 = (T)((p->tau / p->h) * (p->tau / p->h));
   P.cb = (T)(p->tau / p->h);
@@ -269,7 +272,7 @@ int enqueue_forward(ddfd_problem *p) {
       P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
       P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
       P.hist_w = (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
-      launch_forward_step<T>(p->mE_halo[ic], p->mE_ctr[io], p->mK, P, p->stream);
+      launch_forward_step<T>(StepMaps{&p->mE_halo[ic], &p->mE_ctr[io], &p->mS, &p->mQ}, P, p->stream);
       ++p->launches;
       std::swap(ic, io);
       if (s == 0) {
@@ -314,7 +317,7 @@ int enqueue_adjoint(ddfd_problem *p) {
       P.abs_next = faces_at(p, s, k + 1);
       P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
       P.hist_r = (const T *)p->hist + ((size_t)s * (Nt + 1) + k) * 3 * p->n_free;
-      launch_adjoint_step<T>(p->mM_halo[ic], p->mM_ctr[io], p->mK, P, p->stream);
+      launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, p->stream);
       ++p->launches;
       std::swap(ic, io);
       if (s == 0) {
@@ -389,8 +392,9 @@ int cfl_check(ddfd_problem *p) {
 
 // TMA descriptors of one padded field: a 4-D tensor (x, y, z, channel) with
 // row stride px, plane stride px n, channel stride px n^2; the halo box is
-// (32 + 2 hx) x 10 x 1 x ch starting hx elements (16 bytes) left of the tile,
-// the centre box 32 x 8 x 1 x ch.  Out-of-range elements read as zero.
+// (32 + 2 hx) x (TY + 2) x 1 x ch starting hx elements (16 bytes) left of
+// the tile, the centre box 32 x TY x 1 x ch.  Out-of-range elements read as
+// zero.
 int encode_map(ddfd_problem *p, CUtensorMap *m, void *base, int channels, bool halo) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -407,8 +411,9 @@ int encode_map(ddfd_problem *p, CUtensorMap *m, void *base, int channels, bool h
   const cuuint64_t strides[3] = {(cuuint64_t)p->px * esz, (cuuint64_t)p->px * p->n * esz,
                                  (cuuint64_t)p->cs * esz};
   const cuuint32_t hx = (cuuint32_t)(16 / esz);
-  const cuuint32_t box[4] = {halo ? (cuuint32_t)STEP_TX + 2 * hx : (cuuint32_t)STEP_TX,
-                             halo ? (cuuint32_t)STEP_TY + 2 : (cuuint32_t)STEP_TY, 1, (cuuint32_t)channels};
+  const cuuint32_t ty = p->fp32 ? StepTile<float>::TY : StepTile<double>::TY;
+  const cuuint32_t box[4] = {halo ? (cuuint32_t)STEP_TX + 2 * hx : (cuuint32_t)STEP_TX, halo ? ty + 2 : ty, 1,
+                             (cuuint32_t)channels};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = encode(m, p->fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -424,7 +429,8 @@ int build_maps(ddfd_problem *p) {
     if ((st = encode_map(p, &p->mE_halo[q], p->E[q], 3, true)) || (st = encode_map(p, &p->mE_ctr[q], p->E[q], 3, false)) ||
         (st = encode_map(p, &p->mM_halo[q], p->Mu[q], 3, true)) || (st = encode_map(p, &p->mM_ctr[q], p->Mu[q], 3, false)))
       return st;
-  return encode_map(p, &p->mK, p->kcoef, 2, true);
+  if ((st = encode_map(p, &p->mS, p->kcoef, 1, true))) return st;
+  return encode_map(p, &p->mQ, (char *)p->kcoef + (size_t)p->cs * p->esz, 2, false);
 }
 
 int check_err(ddfd_problem *p) {
@@ -629,7 +635,7 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   p->fp32 = cfg->precision == DDFD_FP32;
   p->esz = p->fp32 ? 4 : 8;
   p->stream = (cudaStream_t)cfg->stream;
-  p->kz = p->n >= 128 ? 16 : 8;
+  p->kz = cfg->tile_kz ? cfg->tile_kz : (p->n >= 128 ? 16 : 8);
 
   auto bail = [&](int code) {
     g_create_err = p->err;
@@ -657,7 +663,8 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   const size_t histn = (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
   if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
       (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
-      (st = dalloc(p, 2 * (size_t)p->cs * p->esz, &p->kcoef)) || (st = dalloc_t(p, 1, &p->errflag)) ||
+      (st = dalloc(p, 3 * (size_t)p->cs * p->esz, &p->kcoef)) || (st = dalloc_t(p, 1, &p->errflag)) ||
+
       (st = dalloc(p, histn * p->esz, &p->hist)) || (st = dalloc_t(p, trn, &p->trace)) ||
       (st = dalloc_t(p, trn, &p->res)) || (st = dalloc_t(p, trn, &p->eobs_stage)) ||
       (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gacc)) || (st = dalloc_t(p, 4 * (size_t)p->n_free, &p->coef)) ||
@@ -704,8 +711,10 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
     p->err = "table upload failed";
     return bail(DDFD_E_CUDA);
   }
-  if (cudaMemsetAsync(p->kcoef, 0, 2 * (size_t)p->cs * p->esz, p->stream) ||
-      cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream) || cudaMemsetAsync(p->E[0], 0, fbytes, p->stream) ||
+  launch_coef_vacuum(p->fp32, p->cs, p->kcoef, p->stream);
+  ++p->launches;
+  if (cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream) ||
+ cudaMemsetAsync(p->E[0], 0, fbytes, p->stream) ||
       cudaMemsetAsync(p->E[1], 0, fbytes, p->stream) || cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream) ||
       cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream)) {
     p->err = "memset failed";

@@ -46,8 +46,13 @@ void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const
     k_gather_trace<double><<<nb, 256, 0, s>>>((const double *)E, cs, n_det, det_node, trace_n);
 }
 
-// s = eps - 1 (channel 0) and c = sigma tau / 2 (channel 1) at the free
-// nodes of the padded full-grid coefficient field.
+// Per free node of the padded full-grid coefficient field (FP64 arithmetic,
+// one rounding to the field type):
+//   channel 0: s  = eps - 1                  (Gauss-law weight, eq. forward_prob)
+//   channel 1: q1 = (eps - c) / (eps + c)    c = sigma tau / 2
+//   channel 2: q2 = 1 / (eps + c)
+// so that the step update reads E^{n+1} = E^n + q1 (E^n - E^{n-1}) - q2 tau^2 R.
+// Vacuum nodes hold s = 0, q1 = q2 = 1 (set once at creation).
 template <typename T>
 __global__ void k_expand(const double *coef, int nf, int f0, int n, int px, long long cs, double tau, T *out) {
   const long long n_free = (long long)nf * nf * nf;
@@ -55,9 +60,31 @@ __global__ void k_expand(const double *coef, int nf, int f0, int n, int px, long
        f += (long long)gridDim.x * blockDim.x) {
     const int li = (int)(f % nf), lj = (int)((f / nf) % nf), lk = (int)(f / ((long long)nf * nf));
     const long long off = (f0 + li) + (long long)px * ((f0 + lj) + (long long)n * (f0 + lk));
-    out[off] = (T)(coef[f] - 1.0);
-    out[cs + off] = (T)(coef[n_free + f] * tau * 0.5);
+    const double eps = coef[f], c = coef[n_free + f] * tau * 0.5;
+    out[off] = (T)(eps - 1.0);
+    out[cs + off] = (T)((eps - c) / (eps + c));
+    out[2 * cs + off] = (T)(1.0 / (eps + c));
   }
+}
+
+// Vacuum values s = 0, q1 = q2 = 1 over the whole padded field.
+template <typename T>
+__global__ void k_coef_vacuum(long long cs, T *out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cs;
+       q += (long long)gridDim.x * blockDim.x) {
+    out[q] = T(0);
+    out[cs + q] = T(1);
+    out[2 * cs + q] = T(1);
+  }
+}
+
+void launch_coef_vacuum(int fp32, long long cs, void *coef, cudaStream_t s) {
+  const long long nb = (cs + 255) / 256;
+  const int blocks = (int)(nb < 8192 ? nb : 8192);
+  if (fp32)
+    k_coef_vacuum<float><<<blocks, 256, 0, s>>>(cs, (float *)coef);
+  else
+    k_coef_vacuum<double><<<blocks, 256, 0, s>>>(cs, (double *)coef);
 }
 
 void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int n, int px,

@@ -29,11 +29,13 @@ bool build_kuhn_blocks(KuhnBlocks *out, std::string *msg);
 // Uploads the blocks to constant memory (both precisions).
 cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
 
-// Step-kernel tiling: a CTA owns a STEP_TX x STEP_TY (x, y) tile of one z
-// chunk; STEP_RING shared-memory stages hold staged planes.
+// Step-kernel tiling: a CTA of 256 threads owns a STEP_TX x TY (x, y) tile of
+// one z chunk, one node per thread and plane.
 constexpr int STEP_TX = 32;
-constexpr int STEP_TY = 8;
-constexpr int STEP_RING = 6;
+template <typename T>
+struct StepTile {
+  static constexpr int TY = 8;
+};
 
 // Geometry and per-step scalars common to the forward and adjoint steps.
 // Fields are component-major with x pitch px: offset i + px (j + n k).
@@ -80,20 +82,25 @@ struct StepParams {
   uint32_t spin_limit;   // polls per bounded wait
 };
 
+// TMA descriptors of one launch: current level (halo box), previous level
+// (centre box), s (halo box) and (q1, q2) (centre box) of the coefficients.
+struct StepMaps {
+  const CUtensorMap *cur, *old, *s, *q;
+};
+
 template <typename T>
-void launch_forward_step(const CUtensorMap &mcur, const CUtensorMap &mold, const CUtensorMap &mcoef,
-                         const StepParams<T> &P, cudaStream_t s);
+void launch_forward_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
 template <typename T>
-void launch_adjoint_step(const CUtensorMap &mcur, const CUtensorMap &mold, const CUtensorMap &mcoef,
-                         const StepParams<T> &P, cudaStream_t s);
+void launch_adjoint_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
 
 // Small kernels.
 void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const int *det_node,
                          double *trace_n, cudaStream_t s);
-// eps - 1 and sigma tau / 2 of the free nodes into the padded full-grid
-// coefficient field (channel 0 and 1); other nodes are never written (zero).
+// (s, q1, q2) of the free nodes into the padded full-grid coefficient field;
+// launch_coef_vacuum sets every node to the vacuum values (0, 1, 1) first.
 void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int n, int px,
                           long long cs, double tau, void *coef, cudaStream_t s);
+void launch_coef_vacuum(int fp32, long long cs, void *coef, cudaStream_t s);
 void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, double sig_max,
                          int *flag, cudaStream_t s);
 // residual r = tau z (trace - eobs) for n >= 1 (r[0] = 0); partial sums of

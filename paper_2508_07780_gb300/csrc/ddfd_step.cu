@@ -99,35 +99,39 @@ __device__ __forceinline__ int face_count(int i, int j, int k, int n, uint32_t a
 
 template <typename T>
 struct Stage {
-  static constexpr int HX = 16 / (int)sizeof(T);  // x halo: one 16-byte unit
+  static constexpr int TY = StepTile<T>::TY;       // tile rows
+  static constexpr int RPT = TY / 8;               // rows per thread (256 threads = 32 x 8)
+  static constexpr int HX = 16 / (int)sizeof(T);   // x halo: one 16-byte unit
   static constexpr int BXW = STEP_TX + 2 * HX;     // staged row length
-  static constexpr int ROWS = STEP_TY + 2;
-  static constexpr int E_ELEMS = 3 * ROWS * BXW;
-  static constexpr int O_ELEMS = 3 * STEP_TY * STEP_TX;
-  static constexpr int C_ELEMS = 2 * ROWS * BXW;
+  static constexpr int ROWS = TY + 2;
+  static constexpr int TXY = STEP_TX * TY;
   static constexpr int up128(int b) { return (b + 127) / 128 * 128; }
-  static constexpr int E_BYTES = E_ELEMS * (int)sizeof(T);
-  static constexpr int O_BYTES = O_ELEMS * (int)sizeof(T);
-  static constexpr int C_BYTES = C_ELEMS * (int)sizeof(T);
+  static constexpr int E_BYTES = 3 * ROWS * BXW * (int)sizeof(T);  // current level, halo
+  static constexpr int O_BYTES = 3 * TXY * (int)sizeof(T);         // previous level, centre
+  static constexpr int S_BYTES = ROWS * BXW * (int)sizeof(T);      // s = eps - 1, halo
+  static constexpr int Q_BYTES = 2 * TXY * (int)sizeof(T);         // (q1, q2), centre
   static constexpr int E_OFF = 0;
   static constexpr int O_OFF = up128(E_BYTES);
-  static constexpr int C_OFF = O_OFF + up128(O_BYTES);
-  static constexpr int BYTES = C_OFF + up128(C_BYTES);
+  static constexpr int S_OFF = O_OFF + up128(O_BYTES);
+  static constexpr int Q_OFF = S_OFF + up128(S_BYTES);
+  static constexpr int BYTES = Q_OFF + up128(Q_BYTES);
   // FP32: 6 stages (3 CTAs per SM); FP64: 4 stages (2 CTAs per SM)
-  static constexpr int RING = sizeof(T) == 4 ? STEP_RING : 4;
+  static constexpr int RING = sizeof(T) == 4 ? 6 : 4;
   static constexpr int SMEM = RING * BYTES + RING * 8 + 128;
 };
 
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(STEP_TX *STEP_TY)
+__global__ void __launch_bounds__(256)
     k_step(const __grid_constant__ CUtensorMap mcur, const __grid_constant__ CUtensorMap mold,
-           const __grid_constant__ CUtensorMap mcoef, const StepParams<T> P) {
+           const __grid_constant__ CUtensorMap ms, const __grid_constant__ CUtensorMap mq,
+           const StepParams<T> P) {
   using S = Stage<T>;
+  constexpr int RE = S::ROWS * S::BXW;  // component stride of a staged plane
+  constexpr int BW = S::BXW;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);
   const int n = P.n;
-  const long long cs = P.cs;
   const int tid = threadIdx.x;
 
   if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
@@ -136,18 +140,20 @@ __global__ void __launch_bounds__(STEP_TX *STEP_TY)
                       blockDim.x + tid;
     for (; t < 3LL * P.n_det; t += nb) {
       const int d = (int)(t / 3), c = (int)(t - 3LL * d);
-      P.trace_n[t] = (double)P.cur[c * cs + P.det_node[d]];
+      P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
     }
   }
 
-  const int tx = tid % STEP_TX, ty = tid / STEP_TX;
-  const int x0 = blockIdx.x * STEP_TX, y0 = blockIdx.y * STEP_TY;
+  const int tx = tid & 31, ty = tid >> 5;
+  // one CTA per (tile, z chunk): planes k0-1 .. k1 are staged, plane index
+  // p = kk - (k0 - 1) in slot p % RING
+  const int x0 = blockIdx.x * STEP_TX, y0 = blockIdx.y * S::TY;
   const int k0 = blockIdx.z * P.kz;
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
-  const int nplanes = k1 - k0 + 2;  // planes k0-1 .. k1 are staged
+  const int nplanes = k1 - k0 + 2;
   const bool tile_fem = x0 <= P.b - 1 && x0 + STEP_TX - 1 >= P.a + 1 && y0 <= P.b - 1 &&
-                        y0 + STEP_TY - 1 >= P.a + 1;
+                        y0 + S::TY - 1 >= P.a + 1;
 
   __shared__ int sh_fail;
   if (tid == 0) {
@@ -156,235 +162,274 @@ __global__ void __launch_bounds__(STEP_TX *STEP_TY)
     mbar_fence_init();
     tma_prefetch_desc(&mcur);
     tma_prefetch_desc(&mold);
-    tma_prefetch_desc(&mcoef);
+    tma_prefetch_desc(&ms);
+    tma_prefetch_desc(&mq);
   }
   __syncthreads();
 
-  auto issue = [&](int p) {  // thread 0: stage plane k0-1+p into slot p % S::RING
-    const int kk = k0 - 1 + p;
+  int issued = 0, islot = 0;  // thread 0: planes issued so far, slot of the next one
+  auto issue = [&]() {       // thread 0: stage plane `issued` into slot `islot`
+    const int kk = k0 - 1 + issued;
     const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
-    unsigned char *st = smem + (p % S::RING) * S::BYTES;
+    unsigned char *st = smem + islot * S::BYTES;
     const bool interior = kk >= k0 && kk < k1;
     const bool coef = tile_fem && kk >= P.a && kk <= P.b;
-    const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::C_BYTES : 0);
-    uint64_t *b = &bar[p % S::RING];
-    mbar_expect_tx(b, bytes);
-    tma_load_4d(st + S::E_OFF, &mcur, x0 - S::HX, y0 - 1, ksrc, 0, b);
-    if (interior) tma_load_4d(st + S::O_OFF, &mold, x0, y0, kk, 0, b);
-    if (coef) tma_load_4d(st + S::C_OFF, &mcoef, x0 - S::HX, y0 - 1, kk, 0, b);
+    const bool qc = coef && interior;
+    const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
+                           (qc ? S::Q_BYTES : 0);
+    uint64_t *bb = &bar[islot];
+    mbar_expect_tx(bb, bytes);
+    tma_load_4d(st + S::E_OFF, &mcur, x0 - S::HX, y0 - 1, ksrc, 0, bb);
+    if (interior) tma_load_4d(st + S::O_OFF, &mold, x0, y0, kk, 0, bb);
+    if (coef) tma_load_4d(st + S::S_OFF, &ms, x0 - S::HX, y0 - 1, kk, 0, bb);
+    if (qc) tma_load_4d(st + S::Q_OFF, &mq, x0, y0, kk, 0, bb);
+    ++issued;
+    if (++islot == S::RING) islot = 0;
   };
-  int issued = 0;  // thread 0: planes issued so far
-  if (tid == 0) {
-    const int first = nplanes < S::RING ? nplanes : S::RING;
-    for (int p = 0; p < first; ++p) issue(p);
-    issued = first;
-  }
+  if (tid == 0)
+    while (issued < nplanes && issued < S::RING) issue();
 
-  const int x = x0 + tx, y = y0 + ty;
-  const bool live = x < n && y < n;
-  const int ci = (ty + 1) * S::BXW + (tx + S::HX);
-  const int dxm = (x == 0) ? 1 : -1, dxp = (x == n - 1) ? -1 : 1;
-  const int dym = (y == 0) ? S::BXW : -S::BXW, dyp = (y == n - 1) ? -S::BXW : S::BXW;
-  const bool colfem = x > P.a && x < P.b && y > P.a && y < P.b;
-  const bool colfree = x >= P.f0 && x < P.f0 + P.nf && y >= P.f0 && y < P.f0 + P.nf;
-  const long long rowoff = (long long)P.px * y + x;
+  const long long plane = (long long)P.px * n;
+  const uint32_t cs = (uint32_t)P.cs;
   bool failed = false;
-  int waited = 0;
-
-  for (int k = k0; k < k1; ++k) {
-    const int p = k - k0 + 1;  // plane index of k in the stage sequence
-    // fetch the free-node history / accumulators before waiting on TMA
-    const bool fre = colfree && k >= P.f0 && k < P.f0 + P.nf && live;
-    long long fi = 0;
-    T hv[3] = {T(0), T(0), T(0)};
-    double ga = 0.0, gb = 0.0;
-    if (fre) {
-      fi = (x - P.f0) + (long long)P.nf * ((y - P.f0) + (long long)P.nf * (k - P.f0));
-      if (ADJ) {
+  int wq = 0, wslot = 0;   // planes waited so far, slot of the next wait
+  uint32_t wphase = 0;     // parity of the next wait
+  int sm1 = 0, s0 = 1, sp1 = 2;  // slots of planes p-1, p, p+1 (p = k - k0 + 1)
+  {
+    // per-row constants
+    const int x = x0 + tx;
+    int y[S::RPT], ci[S::RPT], oi[S::RPT], dym[S::RPT], dyp[S::RPT];
+    bool live[S::RPT], colfem[S::RPT], colfree[S::RPT], colbnd[S::RPT];
+    T *out[S::RPT];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hv[c] = __ldg(P.hist_r + c * P.n_free + fi);
-        ga = P.gacc_e[fi];
-        gb = P.gacc_s[fi];
-      }
+    for (int r = 0; r < S::RPT; ++r) {
+      const int yy = ty + 8 * r;
+      y[r] = y0 + yy;
+      ci[r] = (yy + 1) * BW + (tx + S::HX);
+      oi[r] = yy * STEP_TX + tx;
+      dym[r] = (y[r] == 0) ? BW : -BW;
+      dyp[r] = (y[r] == n - 1) ? -BW : BW;
+      live[r] = x < n && y[r] < n;
+      colfem[r] = x > P.a && x < P.b && y[r] > P.a && y[r] < P.b;
+      colfree[r] = x >= P.f0 && x < P.f0 + P.nf && y[r] >= P.f0 && y[r] < P.f0 + P.nf;
+      colbnd[r] = x == 0 || x == n - 1 || y[r] == 0 || y[r] == n - 1;
+      out[r] = P.old + (long long)k0 * plane + (long long)P.px * y[r] + x;
     }
-    bool ok = true;
-    while (waited <= p + 1 && waited < nplanes) {
-      if (!mbar_wait_bounded(&bar[waited % S::RING], (uint32_t)((waited / S::RING) & 1), P.spin_limit)) {
-        ok = false;
+    const int dxm = (x == 0) ? 1 : -1, dxp = (x == n - 1) ? -1 : 1;
+    T below[S::RPT][3], cen[S::RPT][3];
+
+    for (int k = k0; k < k1; ++k) {
+      const int p = k - k0 + 1;
+      bool ok = true;
+      while (wq <= p + 1) {
+        if (!mbar_wait_bounded(&bar[wslot], wphase, P.spin_limit)) {
+          ok = false;
+          break;
+        }
+        ++wq;
+        if (++wslot == S::RING) {
+          wslot = 0;
+          wphase ^= 1u;
+        }
+      }
+      if (!ok) sh_fail = 1;  // read by every thread after the barrier below
+      const unsigned char *bm1 = smem + sm1 * S::BYTES;
+      const unsigned char *b0 = smem + s0 * S::BYTES;
+      const unsigned char *bp1 = smem + sp1 * S::BYTES;
+      const T *Em = (const T *)(bm1 + S::E_OFF);
+      const T *E0 = (const T *)(b0 + S::E_OFF);
+      const T *Ep = (const T *)(bp1 + S::E_OFF);
+      const T *O0 = (const T *)(b0 + S::O_OFF);
+      const bool kfem = k > P.a && k < P.b;
+      const bool kfree = k >= P.f0 && k < P.f0 + P.nf;
+      const bool kbnd = k == 0 || k == n - 1;
+#pragma unroll
+      for (int r = 0; r < S::RPT; ++r) {
+        T above[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (k == k0) {
+            below[r][c] = Em[c * RE + ci[r]];
+            cen[r][c] = E0[c * RE + ci[r]];
+          }
+          above[c] = Ep[c * RE + ci[r]];
+        }
+        if (ok && live[r]) {
+          const bool fre = colfree[r] && kfree;
+          long long fi = 0;
+          if (fre) fi = (x - P.f0) + (long long)P.nf * ((y[r] - P.f0) + (long long)P.nf * (k - P.f0));
+          T od[3], R[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T *e = E0 + c * RE + ci[r];
+            od[c] = O0[c * S::TXY + oi[r]];
+            R[c] = T(6) * cen[r][c] - (e[dxp] + e[dxm] + e[dyp[r]] + e[dym[r]] + above[c] + below[r][c]);
+          }
+          // update coefficients: nw = cen + A (cen - od) + Bc cen - Cq tau^2 R
+          T A = T(1), Bc = T(0), Cq = T(1);
+          T sx[3] = {T(0), T(0), T(0)};
+          if (colfem[r] && kfem) {
+            const T *S0 = (const T *)(b0 + S::S_OFF);
+            const T *Q0 = (const T *)(b0 + S::Q_OFF);
+            const int q = ci[r];
+            const T s0v = S0[q];
+            A = Q0[oi[r]];
+            Cq = Q0[S::TXY + oi[r]];
+            T v0[3], vp[7][3], st[3];
+            if (!ADJ) {
+              const T *Sm = (const T *)(bm1 + S::S_OFF);
+              const T *Sp = (const T *)(bp1 + S::S_OFF);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const T *e0 = E0 + c * RE, *ep = Ep + c * RE, *em = Em + c * RE;
+                v0[c] = s0v * cen[r][c];
+                vp[0][c] = S0[q + 1] * e0[q + 1] + S0[q - 1] * e0[q - 1];
+                vp[1][c] = S0[q + BW] * e0[q + BW] + S0[q - BW] * e0[q - BW];
+                vp[2][c] = Sp[q] * above[c] + Sm[q] * below[r][c];
+                vp[3][c] = S0[q + 1 + BW] * e0[q + 1 + BW] + S0[q - 1 - BW] * e0[q - 1 - BW];
+                vp[4][c] = Sp[q + 1] * ep[q + 1] + Sm[q - 1] * em[q - 1];
+                vp[5][c] = Sp[q + BW] * ep[q + BW] + Sm[q - BW] * em[q - BW];
+                vp[6][c] = Sp[q + 1 + BW] * ep[q + 1 + BW] + Sm[q - 1 - BW] * em[q - 1 - BW];
+              }
+              block_apply<T>(v0, vp, st);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) R[c] += st[c];
+            } else if (s0v != T(0) || fre) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const T *e0 = E0 + c * RE, *ep = Ep + c * RE, *em = Em + c * RE;
+                v0[c] = cen[r][c];
+                vp[0][c] = e0[q + 1] + e0[q - 1];
+                vp[1][c] = e0[q + BW] + e0[q - BW];
+                vp[2][c] = above[c] + below[r][c];
+                vp[3][c] = e0[q + 1 + BW] + e0[q - 1 - BW];
+                vp[4][c] = ep[q + 1] + em[q - 1];
+                vp[5][c] = ep[q + BW] + em[q - BW];
+                vp[6][c] = ep[q + 1 + BW] + em[q - 1 - BW];
+              }
+              block_apply<T>(v0, vp, sx);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) R[c] += s0v * sx[c];
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) R[c] *= P.r2;
+          if (colbnd[r] || kbnd) {
+            // boundary node: damping of the absorbing faces, top-face source or
+            // detector residuals
+            const T cc = P.cb * T(face_count(x, y[r], k, n, P.abs_now));
+            const T ccn = ADJ ? P.cb * T(face_count(x, y[r], k, n, P.abs_next)) : cc;
+            const T inv = T(1) / (T(1) + cc);
+            A = (T(1) - ccn) * inv;
+            Bc = (ccn - cc) * inv;
+            Cq = inv;
+            if (!ADJ && k == n - 1 && P.src_on) {
+              if (!P.oblique) {
+                R[1] -= P.src_y;
+              } else {
+                const double v = P.src_scale * pulse_value(P.pulse_kind, P.freq, P.t0, P.width,
+                                                           P.t_n - P.delay[x + n * y[r]]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) R[c] -= (T)(P.pol[c] * v);
+              }
+            }
+            if (ADJ && k == n - 1 && P.n_det > 0) {
+              const int q0 = P.det_ptr[x + n * y[r]], q1 = P.det_ptr[x + n * y[r] + 1];
+              if (q1 > q0) {
+                const double wx = (x == 0 || x == n - 1) ? 0.5 : 1.0;
+                const double wy = (y[r] == 0 || y[r] == n - 1) ? 0.5 : 1.0;
+                const double sc = P.tau2 * P.inv_h3 / (wx * wy * 0.5);
+                double acc[3] = {0.0, 0.0, 0.0};
+                for (int qq = q0; qq < q1; ++qq) {
+                  const int d = P.det_list[qq];
+                  acc[0] += P.res_k[3 * d + 0];
+                  acc[1] += P.res_k[3 * d + 1];
+                  acc[2] += P.res_k[3 * d + 2];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) R[c] += (T)(sc * acc[c]);
+              }
+            }
+          }
+          T nw[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            nw[c] = cen[r][c] + (A * (cen[r][c] - od[c]) + (Bc * cen[r][c] - Cq * R[c]));
+            out[r][c * cs] = nw[c];
+          }
+          if (fre) {
+            if (!ADJ) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) P.hist_w[c * P.n_free + fi] = nw[c];
+            } else {
+              T ge = T(0), gs = T(0);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const T hv = __ldg(P.hist_r + c * P.n_free + fi);
+                ge += hv * ((nw[c] - T(2) * cen[r][c] + od[c]) + P.r2 * sx[c]);
+                gs += hv * (nw[c] - od[c]);
+              }
+              P.gacc_e[fi] += (double)ge;
+              P.gacc_s[fi] += (double)gs;
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          below[r][c] = cen[r][c];
+          cen[r][c] = above[c];
+        }
+        out[r] += plane;
+      }
+      __syncthreads();  // every thread is done with plane k-1's slot
+      if (sh_fail) {    // uniform across the CTA: decided before the barrier
+        failed = true;
         break;
       }
-      ++waited;
-    }
-    if (!ok) sh_fail = 1;  // read by every thread after the barrier below
-    const T *Em = (const T *)(smem + ((p - 1) % S::RING) * S::BYTES + S::E_OFF);
-    const T *E0 = (const T *)(smem + (p % S::RING) * S::BYTES + S::E_OFF);
-    const T *Ep = (const T *)(smem + ((p + 1) % S::RING) * S::BYTES + S::E_OFF);
-    const T *O0 = (const T *)(smem + (p % S::RING) * S::BYTES + S::O_OFF);
-    const T *C0 = (const T *)(smem + (p % S::RING) * S::BYTES + S::C_OFF);
-    const T *Cm = (const T *)(smem + ((p - 1) % S::RING) * S::BYTES + S::C_OFF);
-    const T *Cp = (const T *)(smem + ((p + 1) % S::RING) * S::BYTES + S::C_OFF);
-    if (ok && live) {
-      constexpr int RE = S::ROWS * S::BXW;  // component / channel stride of a staged plane
-      T cen[3], lap[3], st[3] = {T(0), T(0), T(0)}, sx[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T *e = E0 + c * RE;
-        cen[c] = e[ci];
-        lap[c] = T(6) * cen[c] - (e[ci + dxp] + e[ci + dxm] + e[ci + dyp] + e[ci + dym] + Ep[c * RE + ci] +
-                                  Em[c * RE + ci]);
-      }
-      T eps = T(1), cc, ccn = T(0);
-      const bool fem = colfem && k > P.a && k < P.b;
-      if (fem) {
-        const T s0 = C0[ci];
-        eps = T(1) + s0;
-        cc = C0[RE + ci];
-        ccn = cc;
-        constexpr int B = S::BXW;
-        T v0[3], vp[7][3];
-        if (!ADJ) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const T *e0 = E0 + c * RE, *ep = Ep + c * RE, *em = Em + c * RE;
-            v0[c] = s0 * cen[c];
-            vp[0][c] = C0[ci + 1] * e0[ci + 1] + C0[ci - 1] * e0[ci - 1];
-            vp[1][c] = C0[ci + B] * e0[ci + B] + C0[ci - B] * e0[ci - B];
-            vp[2][c] = Cp[ci] * ep[ci] + Cm[ci] * em[ci];
-            vp[3][c] = C0[ci + 1 + B] * e0[ci + 1 + B] + C0[ci - 1 - B] * e0[ci - 1 - B];
-            vp[4][c] = Cp[ci + 1] * ep[ci + 1] + Cm[ci - 1] * em[ci - 1];
-            vp[5][c] = Cp[ci + B] * ep[ci + B] + Cm[ci - B] * em[ci - B];
-            vp[6][c] = Cp[ci + 1 + B] * ep[ci + 1 + B] + Cm[ci - 1 - B] * em[ci - 1 - B];
-          }
-          block_apply<T>(v0, vp, st);
-        } else if (s0 != T(0) || fre) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const T *e0 = E0 + c * RE, *ep = Ep + c * RE, *em = Em + c * RE;
-            v0[c] = cen[c];
-            vp[0][c] = e0[ci + 1] + e0[ci - 1];
-            vp[1][c] = e0[ci + B] + e0[ci - B];
-            vp[2][c] = ep[ci] + em[ci];
-            vp[3][c] = e0[ci + 1 + B] + e0[ci - 1 - B];
-            vp[4][c] = ep[ci + 1] + em[ci - 1];
-            vp[5][c] = ep[ci + B] + em[ci - B];
-            vp[6][c] = ep[ci + 1 + B] + em[ci - 1 - B];
-          }
-          block_apply<T>(v0, vp, sx);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) st[c] = s0 * sx[c];
-        }
-      } else {
-        cc = P.cb * T(face_count(x, y, k, n, P.abs_now));
-        if (ADJ) ccn = P.cb * T(face_count(x, y, k, n, P.abs_next));
-      }
-      T R[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) R[c] = P.r2 * (lap[c] + st[c]);
-      if (!ADJ && k == n - 1 && P.src_on) {
-        if (!P.oblique) {
-          R[1] -= P.src_y;
-        } else {
-          const double v = P.src_scale * pulse_value(P.pulse_kind, P.freq, P.t0, P.width,
-                                                     P.t_n - P.delay[x + n * y]);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) R[c] -= (T)(P.pol[c] * v);
-        }
-      }
-      if (ADJ && k == n - 1 && P.n_det > 0) {
-        const int q0 = P.det_ptr[x + n * y], q1 = P.det_ptr[x + n * y + 1];
-        if (q1 > q0) {
-          const double wx = (x == 0 || x == n - 1) ? 0.5 : 1.0;
-          const double wy = (y == 0 || y == n - 1) ? 0.5 : 1.0;
-          const double sc = P.tau2 * P.inv_h3 / (wx * wy * 0.5);
-          double acc[3] = {0.0, 0.0, 0.0};
-          for (int q = q0; q < q1; ++q) {
-            const int d = P.det_list[q];
-            acc[0] += P.res_k[3 * d + 0];
-            acc[1] += P.res_k[3 * d + 1];
-            acc[2] += P.res_k[3 * d + 2];
-          }
-#pragma unroll
-          for (int c = 0; c < 3; ++c) R[c] += (T)(sc * acc[c]);
-        }
-      }
-      const long long me = (long long)k * P.px * n + rowoff;
-      const int oi = ty * STEP_TX + tx;
-      T nw[3], od[3];
-      const T inv = T(1) / (eps + cc);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        od[c] = O0[c * (STEP_TX * STEP_TY) + oi];
-        if (!ADJ)
-          nw[c] = cen[c] + ((eps - cc) * (cen[c] - od[c]) - R[c]) * inv;
-        else  // cc: damping at step k-1, ccn: at step k+1
-          nw[c] = cen[c] + ((eps - ccn) * (cen[c] - od[c]) + (ccn - cc) * cen[c] - R[c]) * inv;
-        P.old[c * cs + me] = nw[c];
-      }
-      if (fre) {
-        if (!ADJ) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) P.hist_w[c * P.n_free + fi] = nw[c];
-        } else {
-          T ge = T(0), gs = T(0);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            ge += hv[c] * ((nw[c] - T(2) * cen[c] + od[c]) + P.r2 * sx[c]);
-            gs += hv[c] * (nw[c] - od[c]);
-          }
-          P.gacc_e[fi] = ga + (double)ge;
-          P.gacc_s[fi] = gb + (double)gs;
-        }
-      }
-    }
-    __syncthreads();  // every thread is done with plane k-1's slot
-    if (sh_fail) {    // uniform across the CTA: decided before the barrier
-      failed = true;
-      break;
-    }
-    if (tid == 0 && p - 1 + S::RING < nplanes) {
-      issue(p - 1 + S::RING);
-      issued = p + S::RING;
+      if (tid == 0 && issued < nplanes) issue();  // refills the slot of plane p-1
+      sm1 = s0;
+      s0 = sp1;
+      sp1 = (sp1 + 1 == S::RING) ? 0 : sp1 + 1;
     }
   }
   if (failed && tid == 0) {
     atomicOr(P.err, 4);
     // let the copies already issued land before the CTA exits (bounded)
-    for (int q = waited; q < issued; ++q)
-      mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), P.spin_limit);
+    for (; wq < issued; ++wq) {
+      mbar_wait_bounded(&bar[wslot], wphase, P.spin_limit);
+      if (++wslot == S::RING) {
+        wslot = 0;
+        wphase ^= 1u;
+      }
+    }
   }
 }
 
 template <typename T, bool ADJ>
-static void launch_step(const CUtensorMap &mc, const CUtensorMap &mo, const CUtensorMap &mk,
-                        const StepParams<T> &P, cudaStream_t s) {
+static void launch_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_step<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<T>::SMEM);
     attr_set = true;
   }
-  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + STEP_TY - 1) / STEP_TY, (P.n + P.kz - 1) / P.kz);
-  k_step<T, ADJ><<<grid, STEP_TX * STEP_TY, Stage<T>::SMEM, s>>>(mc, mo, mk, P);
+  const int ty = Stage<T>::TY;
+  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, (P.n + P.kz - 1) / P.kz);
+  k_step<T, ADJ><<<grid, 256, Stage<T>::SMEM, s>>>(*m.cur, *m.old, *m.s, *m.q, P);
 }
 
 template <typename T>
-void launch_forward_step(const CUtensorMap &mc, const CUtensorMap &mo, const CUtensorMap &mk,
-                         const StepParams<T> &P, cudaStream_t s) {
-  launch_step<T, false>(mc, mo, mk, P, s);
+void launch_forward_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
+  launch_step<T, false>(m, P, s);
 }
 template <typename T>
-void launch_adjoint_step(const CUtensorMap &mc, const CUtensorMap &mo, const CUtensorMap &mk,
-                         const StepParams<T> &P, cudaStream_t s) {
-  launch_step<T, true>(mc, mo, mk, P, s);
+void launch_adjoint_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
+  launch_step<T, true>(m, P, s);
 }
 
-template void launch_forward_step<float>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                                         const StepParams<float> &, cudaStream_t);
-template void launch_forward_step<double>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                                          const StepParams<double> &, cudaStream_t);
-template void launch_adjoint_step<float>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                                         const StepParams<float> &, cudaStream_t);
-template void launch_adjoint_step<double>(const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                                          const StepParams<double> &, cudaStream_t);
+template void launch_forward_step<float>(const StepMaps &, const StepParams<float> &, cudaStream_t);
+template void launch_forward_step<double>(const StepMaps &, const StepParams<double> &, cudaStream_t);
+template void launch_adjoint_step<float>(const StepMaps &, const StepParams<float> &, cudaStream_t);
+template void launch_adjoint_step<double>(const StepMaps &, const StepParams<double> &, cudaStream_t);
 
 // y = h^2 M_eps^-1 K x in FP64 on every node (no damping, no source): the
 // operator whose largest eigenvalue bounds the stable time step.  One thread
