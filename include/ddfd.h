@@ -207,6 +207,33 @@ int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t);
 int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps);
 int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out);
 
+/* Allocation-free data misfit, without a handle.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory (a strict device-memory budget, a host framework that owns
+ * every allocation through its own arena, a real-time loop that cannot
+ * afford cudaMalloc's latency and implicit synchronisation).  Such callers
+ * cannot use ddfd_create, which allocates the field buffers.
+ *
+ * Computes J = tau/2 sum_{s, n=1..n_steps} z(t_n) sum_d |trace - eobs|^2,
+ * the misfit part of eq. tikhonov_functional as ddfd_functional computes it
+ * (same z taper, t_n = n tau, T = n_steps tau), and writes it to *J.
+ *   trace, eobs: device pointers, [n_src][n_steps + 1][n_det][3] doubles,
+ *                owned by the caller (may be NULL when n_det = 0);
+ *   J:           device pointer to one double, owned by the caller;
+ *   stream:      cudaStream_t (NULL: default stream).  The call is
+ *                asynchronous on `stream`: read *J after synchronising it.
+ * Scratch: a fixed 512 KB array in the library's device image (one FP64
+ * partial per (source, step) row); it requires n_src * (n_steps + 1) <=
+ * 65536, else DDFD_E_ARG with a message, and nothing is launched.  The call
+ * allocates and frees nothing.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call in the process
+ * shares the array and it keeps the last call's contents: calls that overlap
+ * on the GPU (other streams, other threads) race and give wrong results.
+ * Errors: DDFD_E_ARG, DDFD_E_CUDA; the message is ddfd_create_error(). */
+int ddfd_misfit_noalloc(const double *trace, const double *eobs, int32_t n_src, int32_t n_steps,
+                        int32_t n_det, double tau, double z_delta_frac, double *J, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,5 +11,6 @@ from .binding import (  # noqa: F401
     ddfd_config,
     ddfd_info,
     load_library,
+    misfit_noalloc,
     LIB_PATH,
 )

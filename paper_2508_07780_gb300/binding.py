@@ -34,7 +34,7 @@ ABI_SYMBOLS = (
     "ddfd_create_error", "ddfd_set_coeffs", "ddfd_set_coeffs_dev", "ddfd_forward",
     "ddfd_forward_dev", "ddfd_functional", "ddfd_functional_dev", "ddfd_adjoint",
     "ddfd_adjoint_dev", "ddfd_gradient", "ddfd_gradient_dev", "ddfd_get_info",
-    "ddfd_set_capture", "ddfd_get_capture", "ddfd_get_timing",
+    "ddfd_set_capture", "ddfd_get_capture", "ddfd_get_timing", "ddfd_misfit_noalloc",
 )
 
 
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).argtypes = [P, P, P]
     lib.ddfd_get_info.argtypes = [P, POINTER(ddfd_info)]
     lib.ddfd_get_timing.argtypes = [P, POINTER(ddfd_timing)]
+    lib.ddfd_misfit_noalloc.argtypes = [P, P, c_int32, c_int32, c_int32, c_double, c_double, P, P]
     lib.ddfd_set_capture.argtypes = [P, c_int32, P]
     lib.ddfd_get_capture.argtypes = [P, c_int32, c_int32, P]
     for name in ABI_SYMBOLS:
@@ -142,6 +143,21 @@ def _dev(t, count=None):
     if count is not None and t.numel() != count:
         raise ValueError(f"expected {count} values, got {t.numel()}")
     return t
+
+
+def misfit_noalloc(trace, eobs, n_src, n_steps, n_det, tau, z_delta_frac, J, stream=None):
+    """ddfd_misfit_noalloc on device tensors (float64 CUDA): writes the misfit
+    to J[0] asynchronously on `stream` (a cudaStream_t handle or None).  For
+    callers that cannot allocate device memory: no handle, no allocation."""
+    lib = load_library()
+    for t in (trace, eobs):
+        if t is not None:
+            _dev(t)
+    _dev(J, 1)
+    st = lib.ddfd_misfit_noalloc(_ptr(trace), _ptr(eobs), n_src, n_steps, n_det, tau, z_delta_frac,
+                                 _ptr(J), c_void_p(stream) if stream else None)
+    if st != DDFD_OK:
+        raise DDFDError(st, lib.ddfd_create_error().decode())
 
 
 class Problem:

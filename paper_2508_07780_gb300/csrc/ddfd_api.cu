@@ -33,6 +33,11 @@ double pulse_host(int kind, double f, double t0, double w, double t) {
 }
 }  // namespace
 
+namespace ddfd {
+// Message of the last failing handle-less call in this thread.
+void set_thread_error(const std::string &msg) { g_create_err = msg; }
+}  // namespace ddfd
+
 struct ddfd_problem {
   ddfd_config cfg{};
   std::vector<double> src_dir;
