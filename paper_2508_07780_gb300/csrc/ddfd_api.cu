@@ -75,6 +75,11 @@ struct ddfd_problem {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double fwd_ms = 0.0, adj_ms = 0.0;
   int64_t fwd_kernels = 0, adj_kernels = 0;
+  // The forward and adjoint sequences (all sources) are captured once into
+  // CUDA graphs on cap_stream and replayed on the caller's stream.
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gfwd = nullptr, gadj = nullptr;
+  int64_t gfwd_launches = 0, gadj_launches = 0;
 };
 
 namespace {
@@ -250,24 +255,25 @@ int capture_slot(const ddfd_problem *p, int step) {
   return -1;
 }
 
+// Enqueue the whole forward sequence (every source) on stream `st`; returns
+// the number of kernels enqueued in *nk.
 template <typename T>
-int enqueue_forward(ddfd_problem *p) {
+int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
   const size_t fbytes = 3 * (size_t)p->cs * sizeof(T);
   const int Nt = p->Nt;
-  float ms_total = 0.0f;
+  *nk = 0;
   for (int s = 0; s < p->n_src; ++s) {
-    CK(cudaMemsetAsync(p->E[0], 0, fbytes, p->stream));
-    CK(cudaMemsetAsync(p->E[1], 0, fbytes, p->stream));
+    CK(cudaMemsetAsync(p->E[0], 0, fbytes, sm));
+    CK(cudaMemsetAsync(p->E[1], 0, fbytes, sm));
     if (s == 0) {
       const int sl = capture_slot(p, 0);
-      if (sl >= 0) CK(cudaMemsetAsync((char *)p->capE + sl * fbytes, 0, fbytes, p->stream));
+      if (sl >= 0) CK(cudaMemsetAsync((char *)p->capE + sl * fbytes, 0, fbytes, sm));
     }
     int ic = 1, io = 0;  // buffer holding E^n, and E^{n-1}
     StepParams<T> P = base_params<T>(p);
     P.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
     P.oblique = p->oblique[s];
     for (int q = 0; q < 3; ++q) P.pol[q] = p->pol[3 * s + q];
-    CK(cudaEventRecord(p->ev[0], p->stream));
     for (int st = 0; st < Nt; ++st) {
       P.cur = (const T *)p->E[ic];
       P.old = (T *)p->E[io];
@@ -277,44 +283,35 @@ int enqueue_forward(ddfd_problem *p) {
       P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
       P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
       P.hist_w = (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
-      launch_forward_step<T>(StepMaps{&p->mE_halo[ic], &p->mE_ctr[io], &p->mS, &p->mQ}, P, p->stream);
-      ++p->launches;
+      launch_forward_step<T>(StepMaps{&p->mE_halo[ic], &p->mE_ctr[io], &p->mS, &p->mQ}, P, sm);
+      ++*nk;
       std::swap(ic, io);
       if (s == 0) {
         const int sl = capture_slot(p, st + 1);
         if (sl >= 0)
-          CK(cudaMemcpyAsync((char *)p->capE + sl * fbytes, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, p->stream));
+          CK(cudaMemcpyAsync((char *)p->capE + sl * fbytes, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
       }
     }
-    CK(cudaEventRecord(p->ev[1], p->stream));
     CK(cudaGetLastError());
     launch_gather_trace(p->E[ic], p->fp32, p->cs, p->n_det, p->det_node,
-                        p->trace + ((size_t)s * (Nt + 1) + Nt) * p->n_det * 3, p->stream);
-    if (p->n_det > 0) ++p->launches;
-    p->fwd_steps += Nt;
-    CK(cudaEventSynchronize(p->ev[1]));
-    float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
-    ms_total += ms;
+                        p->trace + ((size_t)s * (Nt + 1) + Nt) * p->n_det * 3, sm);
+    if (p->n_det > 0) ++*nk;
   }
   CK(cudaGetLastError());
-  p->fwd_ms = ms_total;
-  p->fwd_kernels = (int64_t)Nt * p->n_src;
   return DDFD_OK;
 }
 
 template <typename T>
-int enqueue_adjoint(ddfd_problem *p) {
+int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
   const size_t fbytes = 3 * (size_t)p->cs * sizeof(T);
   const int Nt = p->Nt;
-  CK(cudaMemsetAsync(p->gacc, 0, 2 * (size_t)p->n_free * sizeof(double), p->stream));
-  float ms_total = 0.0f;
+  *nk = 0;
+  CK(cudaMemsetAsync(p->gacc, 0, 2 * (size_t)p->n_free * sizeof(double), sm));
   for (int s = 0; s < p->n_src; ++s) {
-    CK(cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream));
-    CK(cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream));
+    CK(cudaMemsetAsync(p->Mu[0], 0, fbytes, sm));
+    CK(cudaMemsetAsync(p->Mu[1], 0, fbytes, sm));
     int ic = 1, io = 0;  // buffers holding mu^k and mu^{k+1}
     StepParams<T> P = base_params<T>(p);
-    CK(cudaEventRecord(p->ev[2], p->stream));
     for (int k = Nt; k >= 1; --k) {
       P.cur = (const T *)p->Mu[ic];
       P.old = (T *)p->Mu[io];
@@ -322,24 +319,67 @@ int enqueue_adjoint(ddfd_problem *p) {
       P.abs_next = faces_at(p, s, k + 1);
       P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
       P.hist_r = (const T *)p->hist + ((size_t)s * (Nt + 1) + k) * 3 * p->n_free;
-      launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, p->stream);
-      ++p->launches;
+      launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, sm);
+      ++*nk;
       std::swap(ic, io);
       if (s == 0) {
         const int sl = capture_slot(p, k - 1);
         if (sl >= 0)
-          CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, p->Mu[ic], fbytes, cudaMemcpyDeviceToDevice, p->stream));
+          CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, p->Mu[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
       }
     }
-    CK(cudaEventRecord(p->ev[3], p->stream));
     CK(cudaGetLastError());
-    CK(cudaEventSynchronize(p->ev[3]));
-    float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]));
-    ms_total += ms;
   }
-  p->adj_ms = ms_total;
-  p->adj_kernels = (int64_t)Nt * p->n_src;
+  return DDFD_OK;
+}
+
+void drop_graphs(ddfd_problem *p) {
+  if (p->gfwd) cudaGraphExecDestroy(p->gfwd);
+  if (p->gadj) cudaGraphExecDestroy(p->gadj);
+  p->gfwd = p->gadj = nullptr;
+}
+
+// Capture `adj ? adjoint : forward` into a graph (once), replay it on the
+// caller's stream between two timing events.
+int run_sequence(ddfd_problem *p, bool adj) {
+  cudaGraphExec_t *ge = adj ? &p->gadj : &p->gfwd;
+  int64_t *gl = adj ? &p->gadj_launches : &p->gfwd_launches;
+  if (!*ge) {
+    CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+    int64_t nk = 0;
+    int st;
+    if (adj)
+      st = p->fp32 ? enqueue_adjoint<float>(p, p->cap_stream, &nk) : enqueue_adjoint<double>(p, p->cap_stream, &nk);
+    else
+      st = p->fp32 ? enqueue_forward<float>(p, p->cap_stream, &nk) : enqueue_forward<double>(p, p->cap_stream, &nk);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &g);
+    if (st) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    CK(ec);
+    const cudaError_t ei = cudaGraphInstantiate(ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    *gl = nk;
+  }
+  cudaEvent_t e0 = p->ev[adj ? 2 : 0], e1 = p->ev[adj ? 3 : 1];
+  CK(cudaEventRecord(e0, p->stream));
+  CK(cudaGraphLaunch(*ge, p->stream));
+  CK(cudaEventRecord(e1, p->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  p->launches += *gl;
+  if (adj) {
+    p->adj_ms = ms;
+    p->adj_kernels = (int64_t)p->Nt * p->n_src;
+  } else {
+    p->fwd_ms = ms;
+    p->fwd_kernels = (int64_t)p->Nt * p->n_src;
+    p->fwd_steps += (int64_t)p->Nt * p->n_src;
+  }
   return DDFD_OK;
 }
 
@@ -487,7 +527,7 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
 }
 
 int forward_impl(ddfd_problem *p, double *trace_out, cudaMemcpyKind kind) {
-  int st = p->fp32 ? enqueue_forward<float>(p) : enqueue_forward<double>(p);
+  int st = run_sequence(p, false);
   if (st) return st;
   if ((st = check_err(p))) return st;
   const long long cnt = (long long)p->n_src * (p->Nt + 1) * p->n_det * 3;
@@ -541,7 +581,7 @@ int adjoint_impl(ddfd_problem *p, const double *eobs, bool host) {
   }
   launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
   ++p->launches;
-  int st = p->fp32 ? enqueue_adjoint<float>(p) : enqueue_adjoint<double>(p);
+  int st = run_sequence(p, true);
   if (st) return st;
   if ((st = check_err(p))) return st;
   const int s2 = sync_check(p);
@@ -652,6 +692,11 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
       p->err = "cudaEventCreate failed";
       return bail(DDFD_E_CUDA);
     }
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      prepare_step_kernels() != cudaSuccess) {
+    p->err = "stream creation or kernel attribute setup failed";
+    return bail(DDFD_E_CUDA);
+  }
   KuhnBlocks kb;
   if (!build_kuhn_blocks(&kb, &m)) {
     p->err = m;
@@ -748,6 +793,8 @@ void ddfd_destroy(ddfd_problem *p) {
   for (void *v : p->allocs) cudaFree(v);
   for (int q = 0; q < 4; ++q)
     if (p->ev[q]) cudaEventDestroy(p->ev[q]);
+  drop_graphs(p);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
 
@@ -859,6 +906,7 @@ int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps) {
       return st;
   }
   p->cap_steps.assign(steps, steps + count);
+  drop_graphs(p);  // the captured sequences copy fields at the capture steps
   return DDFD_OK;
 }
 

@@ -88,6 +88,10 @@ struct StepMaps {
   const CUtensorMap *cur, *old, *s, *q;
 };
 
+// Sets the dynamic shared-memory limit of every step-kernel instance (once,
+// before any launch or capture).
+cudaError_t prepare_step_kernels();
+
 template <typename T>
 void launch_forward_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
 template <typename T>

@@ -405,13 +405,22 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+cudaError_t prepare_step_kernels() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_step<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Stage<float>::SMEM)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_step<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Stage<float>::SMEM)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_step<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Stage<double>::SMEM)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_step<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Stage<double>::SMEM)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
 template <typename T, bool ADJ>
 static void launch_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_step<T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<T>::SMEM);
-    attr_set = true;
-  }
   const int ty = Stage<T>::TY;
   const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, (P.n + P.kz - 1) / P.kz);
   k_step<T, ADJ><<<grid, 256, Stage<T>::SMEM, s>>>(*m.cur, *m.old, *m.s, *m.q, P);
