@@ -191,6 +191,44 @@ def run_reference(args, w, rank):
     print(json.dumps(line), flush=True)
 
 
+def fp64_plain(w, dev, stream):
+    """One timed pass (after one warm-up) of the same workload with FP64 fields."""
+    import torch
+    from paper_2508_07780_gb300 import Problem
+    w64 = w.with_(precision="fp64")
+    eps, sig = w64.model()
+    e_lay, s_lay = w64.model(inclusions=False)
+    p = Problem(n=w64.n, fem_n=w64.fem_n, n_steps=w64.n_steps, cfl=w64.cfl, precision="fp64",
+                src_dir=w64.directions(), det_ij=w64.detectors(), z_delta_frac=w64.z_delta_frac,
+                stream=stream.cuda_stream)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    p.set_coeffs(e_lay, s_lay)
+    eobs = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
+    p.forward_dev(eobs)
+    eps_d, sig_d = T(eps), T(sig)
+    ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
+    gs = torch.empty_like(ge)
+
+    def step():
+        p.set_coeffs_dev(eps_d, sig_d)
+        p.forward_dev(None)
+        p.functional_dev(eobs)
+        p.adjoint_dev(eobs)
+        p.gradient_dev(ge, gs)
+
+    step()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    p.close()
+    return w64.updates / (ms / 1e3), ms
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -320,6 +358,13 @@ def run_ours(args, w, rank, world, local_rank):
             "roofline": roof,
             "gpu_launches": int(launches),
             "clocks": clocks}
+    if world == 1 and w.precision == "fp32" and not args.no_fp64:
+        # the plain FP64 path on the same workload, for the FP32 speedup
+        v64, ms64 = fp64_plain(w, dev, stream)
+        line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": 1, "warmup": 1,
+                              "fp32_speedup": value / v64,
+                              "accuracy": "FP32 vs FP64 on this workload: trace 2.4e-6, J 1.9e-6, "
+                                          "g 1.1e-5 relative L2 (tests/test_gpu_fullsize.py)"}
     if world == 1 and not args.no_cpu_baseline:
         v, wall, cores = oracle_sample(w, 2)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -338,6 +383,7 @@ def main():
     ap.add_argument("--workload", default="c2_fp32_201")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison pass")
     args = ap.parse_args()
     w = workload(args.workload)
     if args.precision:

@@ -94,8 +94,11 @@ typedef struct {
                             d = frac * T; 0 disables it */
   double eps_max, sig_max; /* coefficient bounds checked by ddfd_set_coeffs */
   int32_t n_snapshots;   /* 0: keep E on the free nodes for every step in device memory;
-                            > 0: binomial checkpointing with this many full-state
-                            snapshots, the adjoint replays forward segments */
+                            1..n_steps: checkpointing -- the forward keeps the state
+                            (E^n, E^{n-1}) at the starts of n_snapshots equal segments
+                            and the adjoint replays each segment's forward steps from its
+                            snapshot into a one-segment history (one extra forward sweep;
+                            results are bitwise those of the full history) */
   int32_t cfl_check;     /* nonzero: estimate the stability bound by power iteration
                             at ddfd_set_coeffs and fail with DDFD_E_CFL above it */
   int64_t mem_budget;    /* device bytes the handle may allocate; 0 = no limit */
@@ -189,10 +192,11 @@ typedef struct {
 } ddfd_info;
 int ddfd_get_info(const ddfd_problem *p, ddfd_info *info);
 
-/* Device time of the last forward / adjoint step loops, measured with CUDA
- * events recorded on the handle's stream around the back-to-back step
- * kernels (all sources), and the number of step kernels in each loop.  The
- * average step-kernel duration is loop_ms / steps.  Zero before a run. */
+/* Device time of the last forward / adjoint sequences, measured with CUDA
+ * events recorded on the handle's stream around each (all sources, with the
+ * forward replays of checkpointing in the adjoint sequence), and the number
+ * of step kernels each launched.  loop_ms / kernels is the average step-kernel
+ * time including the small per-source set-up.  Zero before a run. */
 typedef struct {
   double forward_loop_ms, adjoint_loop_ms;
   int64_t forward_step_kernels, adjoint_step_kernels;

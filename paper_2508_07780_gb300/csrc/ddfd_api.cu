@@ -54,7 +54,11 @@ struct ddfd_problem {
   int64_t bytes = 0;
   void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr};
   void *kcoef = nullptr;      // padded full-grid (s, q1, q2), 3 channels
-  void *hist = nullptr;
+  void *hist = nullptr;       // E on the free nodes: every step, or one replayed segment
+  // checkpointing (n_snapshots > 0): state snapshots (E^n, E^{n-1}) at the
+  // starts of segments of seg steps; the adjoint replays each segment
+  int nsnap = 0, seg = 0;
+  void *snap = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
   double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
   double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
@@ -147,7 +151,7 @@ int validate(const ddfd_config *c, std::string *m) {
   if (c->gamma_eps < 0 || c->gamma_sig < 0) return *m = "gammas must be >= 0", DDFD_E_ARG;
   if (!(c->z_delta_frac >= 0.0 && c->z_delta_frac < 1.0)) return *m = "z_delta_frac must be in [0,1)", DDFD_E_ARG;
   if (!(c->eps_max >= 1.0) || !(c->sig_max >= 0.0)) return *m = "bad coefficient bounds", DDFD_E_ARG;
-  if (c->n_snapshots != 0) return *m = "n_snapshots > 0 (checkpointing) is not built", DDFD_E_ARG;
+  if (c->n_snapshots < 0 || c->n_snapshots > c->n_steps) return *m = "n_snapshots must be in [0, n_steps]", DDFD_E_ARG;
   if (c->mem_budget < 0) return *m = "mem_budget must be >= 0", DDFD_E_ARG;
   if (c->tile_kz != 0 && (c->tile_kz < 2 || c->tile_kz > c->n)) return *m = "tile_kz must be 0 or in [2, n]", DDFD_E_ARG;
   if (c->src_dir)
@@ -275,6 +279,11 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
     P.oblique = p->oblique[s];
     for (int q = 0; q < 3; ++q) P.pol[q] = p->pol[3 * s + q];
     for (int st = 0; st < Nt; ++st) {
+      if (p->nsnap && st % p->seg == 0) {  // snapshot the state (E^st, E^{st-1})
+        char *sn = (char *)p->snap + ((size_t)s * p->nsnap + st / p->seg) * 2 * fbytes;
+        CK(cudaMemcpyAsync(sn, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
+        CK(cudaMemcpyAsync(sn + fbytes, p->E[io], fbytes, cudaMemcpyDeviceToDevice, sm));
+      }
       P.cur = (const T *)p->E[ic];
       P.old = (T *)p->E[io];
       P.abs_now = faces_at(p, s, st);
@@ -282,7 +291,7 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
       P.t_n = st * p->tau;
       P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
       P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
-      P.hist_w = (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
+      P.hist_w = p->nsnap ? nullptr : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
       launch_forward_step<T>(StepMaps{&p->mE_halo[ic], &p->mE_ctr[io], &p->mS, &p->mQ}, P, sm);
       ++*nk;
       std::swap(ic, io);
@@ -312,20 +321,56 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
     CK(cudaMemsetAsync(p->Mu[1], 0, fbytes, sm));
     int ic = 1, io = 0;  // buffers holding mu^k and mu^{k+1}
     StepParams<T> P = base_params<T>(p);
-    for (int k = Nt; k >= 1; --k) {
-      P.cur = (const T *)p->Mu[ic];
-      P.old = (T *)p->Mu[io];
-      P.abs_now = faces_at(p, s, k - 1);
-      P.abs_next = faces_at(p, s, k + 1);
-      P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
-      P.hist_r = (const T *)p->hist + ((size_t)s * (Nt + 1) + k) * 3 * p->n_free;
-      launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, sm);
-      ++*nk;
-      std::swap(ic, io);
-      if (s == 0) {
-        const int sl = capture_slot(p, k - 1);
-        if (sl >= 0)
-          CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, p->Mu[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
+    // segments [n0, n1): all of [0, Nt) at once when the whole history is
+    // kept, else the checkpoint segments from the last to the first
+    const int nseg = p->nsnap ? (Nt + p->seg - 1) / p->seg : 1;
+    for (int j = nseg - 1; j >= 0; --j) {
+      const int n0 = p->nsnap ? j * p->seg : 0;
+      const int n1 = p->nsnap ? std::min(n0 + p->seg, Nt) : Nt;
+      const T *hbase;  // E^k of this segment at hbase + (k - n0) * 3 n_free
+      if (p->nsnap) {
+        // restore the snapshot of step n0 and replay the segment's forward
+        // steps, keeping E on the free nodes for the adjoint steps below
+        const char *sn = (const char *)p->snap + ((size_t)s * p->nsnap + j) * 2 * fbytes;
+        CK(cudaMemcpyAsync(p->E[1], sn, fbytes, cudaMemcpyDeviceToDevice, sm));
+        CK(cudaMemcpyAsync(p->E[0], sn + fbytes, fbytes, cudaMemcpyDeviceToDevice, sm));
+        int fc = 1, fo = 0;
+        StepParams<T> F = base_params<T>(p);
+        F.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
+        F.oblique = p->oblique[s];
+        for (int q = 0; q < 3; ++q) F.pol[q] = p->pol[3 * s + q];
+        for (int st = n0; st < n1; ++st) {
+          F.cur = (const T *)p->E[fc];
+          F.old = (T *)p->E[fo];
+          F.abs_now = faces_at(p, s, st);
+          F.src_on = st <= p->n1[s] ? 1 : 0;
+          F.t_n = st * p->tau;
+          F.src_y = (T)(F.src_scale * p->ptab[(size_t)s * Nt + st]);
+          F.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;  // same values again
+          F.hist_w = (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free;
+          launch_forward_step<T>(StepMaps{&p->mE_halo[fc], &p->mE_ctr[fo], &p->mS, &p->mQ}, F, sm);
+          ++*nk;
+          std::swap(fc, fo);
+        }
+        hbase = (const T *)p->hist;
+      } else {
+        hbase = (const T *)p->hist + (size_t)s * (Nt + 1) * 3 * p->n_free;
+      }
+      for (int k = n1; k >= n0 + 1; --k) {
+        P.cur = (const T *)p->Mu[ic];
+        P.old = (T *)p->Mu[io];
+        P.abs_now = faces_at(p, s, k - 1);
+        P.abs_next = faces_at(p, s, k + 1);
+        P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
+        P.hist_r = hbase + (size_t)(k - n0) * 3 * p->n_free;
+        launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, sm);
+        ++*nk;
+        std::swap(ic, io);
+        if (s == 0) {
+          const int sl = capture_slot(p, k - 1);
+          if (sl >= 0)
+            CK(cudaMemcpyAsync((char *)p->capMu + sl * fbytes, p->Mu[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
+        }
       }
     }
     CK(cudaGetLastError());
@@ -374,7 +419,8 @@ int run_sequence(ddfd_problem *p, bool adj) {
   p->launches += *gl;
   if (adj) {
     p->adj_ms = ms;
-    p->adj_kernels = (int64_t)p->Nt * p->n_src;
+    p->adj_kernels = (int64_t)p->Nt * p->n_src * (p->nsnap ? 2 : 1);
+    if (p->nsnap) p->fwd_steps += (int64_t)p->Nt * p->n_src;  // replayed forward steps
   } else {
     p->fwd_ms = ms;
     p->fwd_kernels = (int64_t)p->Nt * p->n_src;
@@ -710,7 +756,12 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   setup_sources(p, &delay_host);
   const size_t fbytes = 3 * (size_t)p->cs * p->esz;
   const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
-  const size_t histn = (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
+  if (cfg->n_snapshots > 0) {
+    p->seg = (p->Nt + cfg->n_snapshots - 1) / cfg->n_snapshots;
+    p->nsnap = (p->Nt + p->seg - 1) / p->seg;
+  }
+  const size_t histn = p->nsnap ? (size_t)(p->seg + 1) * 3 * p->n_free
+                                : (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
   if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
       (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
       (st = dalloc(p, 3 * (size_t)p->cs * p->esz, &p->kcoef)) || (st = dalloc_t(p, 1, &p->errflag)) ||
@@ -725,6 +776,7 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
       (st = dalloc_t(p, (size_t)p->n * p->n + 1, &p->det_ptr)) ||
       (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_list)))
     return bail(st);
+  if (p->nsnap && (st = dalloc(p, (size_t)p->n_src * p->nsnap * 2 * fbytes, &p->snap))) return bail(st);
   bool any_oblique = false;
   for (int s = 0; s < p->n_src; ++s) any_oblique |= p->oblique[s] != 0;
   if (any_oblique && (st = dalloc_t(p, delay_host.size(), &p->delay))) return bail(st);

@@ -73,7 +73,7 @@ struct StepParams {
   double inv_h3;         // 1 / h^3
   double tau2;           // tau^2
   // history of E on the free nodes
-  T *hist_w;             // forward: hist[n+1] ([3][n_free])
+  T *hist_w;             // forward: hist[n+1] ([3][n_free]); null: not kept
   const T *hist_r;       // adjoint: hist[k]
   long long n_free;
   double *gacc_e;        // adjoint: gradient accumulators (FP64)

@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(256)
           }
           if (fre) {
             if (!ADJ) {
+            if (P.hist_w)
 #pragma unroll
               for (int c = 0; c < 3; ++c) P.hist_w[c * P.n_free + fi] = nw[c];
             } else {
