@@ -59,6 +59,12 @@ struct ddfd_problem {
   // starts of segments of seg steps; the adjoint replays each segment
   int nsnap = 0, seg = 0;
   void *snap = nullptr;
+  // element-by-element FEM rows (fem_kind = DDFD_FEM_EBE): explicit mesh
+  int ebe_rows = 0;
+  int *ebe_row_node = nullptr, *ebe_row_ptr = nullptr, *ebe_inc_tet = nullptr, *ebe_inc_local = nullptr;
+  int *ebe_tet_node = nullptr;
+  void *ebe_tet_grad = nullptr, *ebe_out_r = nullptr, *ebe_out_q = nullptr;
+  double *ebe_scale = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
   double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
   double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
@@ -137,7 +143,7 @@ int validate(const ddfd_config *c, std::string *m) {
   if (c->n_steps < 1) return *m = "n_steps must be >= 1", DDFD_E_ARG;
   if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) return *m = "cfl must be positive", DDFD_E_ARG;
   if (c->precision != DDFD_FP64 && c->precision != DDFD_FP32) return *m = "bad precision", DDFD_E_ARG;
-  if (c->fem_kind != DDFD_FEM_STENCIL) return *m = "fem_kind: only DDFD_FEM_STENCIL is built", DDFD_E_ARG;
+  if (c->fem_kind != DDFD_FEM_STENCIL && c->fem_kind != DDFD_FEM_EBE) return *m = "bad fem_kind", DDFD_E_ARG;
   if (c->n_src < 1) return *m = "n_src must be >= 1", DDFD_E_ARG;
   if (c->source_kind != DDFD_SRC_GAUSS && c->source_kind != DDFD_SRC_SINE) return *m = "bad source_kind", DDFD_E_ARG;
   if (!(c->freq > 0.0) || (c->source_kind == DDFD_SRC_GAUSS && !(c->width > 0.0)))
@@ -232,6 +238,9 @@ StepParams<T> base_params(const ddfd_problem *p) {
   P.kz = p->kz;
   P.cs = p->cs;
   P.err = p->errflag;
+  P.ebe_r = (const T *)p->ebe_out_r;
+  P.ebe_q = (const T *)p->ebe_out_q;
+  P.ebe_rows = p->ebe_rows;
 
   P.spin_limit = 1u << 22;
   P.r2 = (T)((p->tau / p->h) * (p->tau / p->h));
@@ -257,6 +266,28 @@ int capture_slot(const ddfd_problem *p, int step) {
   for (size_t q = 0; q < p->cap_steps.size(); ++q)
     if (p->cap_steps[q] == step) return (int)q;
   return -1;
+}
+
+// The element-by-element rows of the current level (fem_kind = DDFD_FEM_EBE).
+template <typename T>
+void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, int64_t *nk) {
+  if (!p->ebe_rows) return;
+  EbeParams<T> E;
+  E.n_rows = p->ebe_rows;
+  E.row_node = p->ebe_row_node;
+  E.row_ptr = p->ebe_row_ptr;
+  E.inc_tet = p->ebe_inc_tet;
+  E.inc_local = p->ebe_inc_local;
+  E.tet_node = p->ebe_tet_node;
+  E.tet_grad = (const T *)p->ebe_tet_grad;
+  E.scale = p->ebe_scale;
+  E.field = (const T *)field;
+  E.s = (const T *)p->kcoef;
+  E.cs = p->cs;
+  E.out_r = (T *)p->ebe_out_r;
+  E.out_q = (T *)p->ebe_out_q;
+  launch_ebe<T>(E, adj, sm);
+  ++*nk;
 }
 
 // Enqueue the whole forward sequence (every source) on stream `st`; returns
@@ -292,6 +323,7 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
       P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
       P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
       P.hist_w = p->nsnap ? nullptr : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
+      enqueue_ebe<T>(p, p->E[ic], false, sm, nk);
       launch_forward_step<T>(StepMaps{&p->mE_halo[ic], &p->mE_ctr[io], &p->mS, &p->mQ}, P, sm);
       ++*nk;
       std::swap(ic, io);
@@ -348,6 +380,7 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
           F.src_y = (T)(F.src_scale * p->ptab[(size_t)s * Nt + st]);
           F.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;  // same values again
           F.hist_w = (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free;
+          enqueue_ebe<T>(p, p->E[fc], false, sm, nk);
           launch_forward_step<T>(StepMaps{&p->mE_halo[fc], &p->mE_ctr[fo], &p->mS, &p->mQ}, F, sm);
           ++*nk;
           std::swap(fc, fo);
@@ -363,6 +396,7 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
         P.abs_next = faces_at(p, s, k + 1);
         P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
         P.hist_r = hbase + (size_t)(k - n0) * 3 * p->n_free;
+        enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk);
         launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, sm);
         ++*nk;
         std::swap(ic, io);
@@ -511,6 +545,109 @@ int encode_map(ddfd_problem *p, CUtensorMap *m, void *base, int channels, bool h
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(p, DDFD_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return DDFD_OK;
+}
+
+// Explicit P1 mesh of the FEM cube for the element-by-element path: the six
+// Kuhn tetrahedra of every cube of [a, b]^3 as a tet list with per-tet
+// sqrt|K| g (from the inverse of [1 x] in FP64), the incidences of the nodes
+// strictly inside the cube (the rows the FEM updates) and their lumped masses.
+int build_ebe(ddfd_problem *p) {
+  const int a = p->a, b = p->b, n = p->n;
+  const int fm = b - a - 1;  // rows per axis
+  const long long rows = (long long)fm * fm * fm;
+  const long long cubes = (long long)(b - a) * (b - a) * (b - a);
+  const long long ntet = 6 * cubes;
+  if (ntet > (1LL << 31) / 4) return fail(p, DDFD_E_ARG, "FEM mesh too large for the element path");
+  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  std::vector<int> tnode((size_t)ntet * 4);
+  std::vector<double> tgrad((size_t)ntet * 12);
+  std::vector<int> rptr((size_t)rows + 1, 0);
+  std::vector<double> mass((size_t)rows, 0.0);
+  auto off = [&](int i, int j, int k) { return (int)(i + (long long)p->px * (j + (long long)n * k)); };
+  auto rowof = [&](int i, int j, int k) -> long long {
+    if (i <= a || i >= b || j <= a || j >= b || k <= a || k >= b) return -1;
+    return (i - a - 1) + (long long)fm * ((j - a - 1) + (long long)fm * (k - a - 1));
+  };
+  long long t = 0;
+  for (int k = a; k < b; ++k)
+    for (int j = a; j < b; ++j)
+      for (int i = a; i < b; ++i)
+        for (const auto &pm : perms) {
+          int v[4][3] = {{i, j, k}};
+          for (int q = 0; q < 3; ++q) {
+            for (int d = 0; d < 3; ++d) v[q + 1][d] = v[q][d];
+            v[q + 1][pm[q]] += 1;
+          }
+          double A[4][4], C[4][4];
+          for (int q = 0; q < 4; ++q) {
+            A[q][0] = 1.0;
+            for (int d = 0; d < 3; ++d) A[q][d + 1] = v[q][d] * p->h;
+          }
+          if (!invert4(A, C)) return fail(p, DDFD_E_ARG, "degenerate tetrahedron in the FEM mesh");
+          double e1[3], e2[3], e3[3];
+          for (int d = 0; d < 3; ++d) {
+            e1[d] = A[1][d + 1] - A[0][d + 1];
+            e2[d] = A[2][d + 1] - A[0][d + 1];
+            e3[d] = A[3][d + 1] - A[0][d + 1];
+          }
+          const double vol = std::fabs(e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                                       e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+          const double sv = std::sqrt(vol);
+          for (int q = 0; q < 4; ++q) {
+            tnode[t * 4 + q] = off(v[q][0], v[q][1], v[q][2]);
+            for (int d = 0; d < 3; ++d) tgrad[t * 12 + q * 3 + d] = sv * C[d + 1][q];
+            const long long r = rowof(v[q][0], v[q][1], v[q][2]);
+            if (r >= 0) {
+              rptr[r + 1]++;
+              mass[r] += vol / 4.0;
+            }
+          }
+          ++t;
+        }
+  for (long long r = 0; r < rows; ++r) rptr[r + 1] += rptr[r];
+  const long long ninc = rptr[rows];
+  std::vector<int> itet((size_t)ninc), iloc((size_t)ninc), fillp(rptr.begin(), rptr.end() - 1), rnode((size_t)rows);
+  std::vector<double> scale((size_t)rows);
+  for (t = 0; t < ntet; ++t)
+    for (int q = 0; q < 4; ++q) {
+      const int o = tnode[t * 4 + q];
+      const int i = (int)(o % p->px), j = (int)((o / p->px) % n), k = (int)(o / ((long long)p->px * n));
+      const long long r = rowof(i, j, k);
+      if (r >= 0) {
+        itet[fillp[r]] = (int)t;
+        iloc[fillp[r]++] = q;
+      }
+    }
+  for (int k = a + 1; k < b; ++k)
+    for (int j = a + 1; j < b; ++j)
+      for (int i = a + 1; i < b; ++i) {
+        const long long r = rowof(i, j, k);
+        rnode[r] = off(i, j, k);
+        scale[r] = p->h * p->h / mass[r];
+      }
+  int st;
+  const size_t es = p->esz;
+  if ((st = dalloc_t(p, (size_t)rows, &p->ebe_row_node)) || (st = dalloc_t(p, (size_t)rows + 1, &p->ebe_row_ptr)) ||
+      (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_tet)) || (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_local)) ||
+      (st = dalloc_t(p, (size_t)ntet * 4, &p->ebe_tet_node)) || (st = dalloc(p, (size_t)ntet * 12 * es, &p->ebe_tet_grad)) ||
+      (st = dalloc_t(p, (size_t)rows, &p->ebe_scale)) || (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_r)) ||
+      (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_q)))
+    return st;
+  std::vector<float> tgf;
+  const void *gsrc = tgrad.data();
+  if (p->fp32) {
+    tgf.assign(tgrad.begin(), tgrad.end());
+    gsrc = tgf.data();
+  }
+  CK(cudaMemcpy(p->ebe_row_node, rnode.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_row_ptr, rptr.data(), (rows + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_inc_tet, itet.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_inc_local, iloc.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_tet_node, tnode.data(), ntet * 4 * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_tet_grad, gsrc, ntet * 12 * es, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_scale, scale.data(), rows * sizeof(double), cudaMemcpyHostToDevice));
+  p->ebe_rows = (int)rows;
   return DDFD_OK;
 }
 
@@ -827,6 +964,7 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
     return bail(DDFD_E_CUDA);
   }
   if ((st = build_maps(p))) return bail(st);
+  if (cfg->fem_kind == DDFD_FEM_EBE && (st = build_ebe(p))) return bail(st);
   // vacuum coefficients
   std::vector<double> one((size_t)p->n_free, 1.0), zero((size_t)p->n_free, 0.0);
   const bool chk = p->cfg.cfl_check != 0;

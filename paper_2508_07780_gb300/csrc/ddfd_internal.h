@@ -26,6 +26,9 @@ struct KuhnBlocks {
 // returns false (with a message) if the FE rows do not match the FD rows.
 bool build_kuhn_blocks(KuhnBlocks *out, std::string *msg);
 
+// Inverse of a 4x4 matrix (Gauss-Jordan, partial pivoting); false if singular.
+bool invert4(const double A[4][4], double X[4][4]);
+
 // Uploads the blocks to constant memory (both precisions).
 cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
 
@@ -78,6 +81,13 @@ struct StepParams {
   long long n_free;
   double *gacc_e;        // adjoint: gradient accumulators (FP64)
   double *gacc_s;
+  // element-by-element FEM rows (fem_kind = DDFD_FEM_EBE): when ebe_r is set,
+  // nodes strictly inside the FEM cube take R = h^2 M^-1 (K E) (and, in the
+  // adjoint, q = h^2 M^-1 (D^T D mu)) from these arrays, row index
+  // (x-a-1) + (fem_n-2) ((y-a-1) + (fem_n-2) (k-a-1)), instead of the stencil
+  const T *ebe_r;
+  const T *ebe_q;
+  int ebe_rows;
   int *err;              // bit 4: a bounded mbarrier wait gave up
   uint32_t spin_limit;   // polls per bounded wait
 };
@@ -96,6 +106,26 @@ template <typename T>
 void launch_forward_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
 template <typename T>
 void launch_adjoint_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
+
+// Element-by-element FEM apply over an explicit tetrahedral mesh.
+template <typename T>
+struct EbeParams {
+  int n_rows;               // FEM-updated nodes
+  const int *row_node;      // padded offset of each row's node
+  const int *row_ptr;       // incidences of row r: [row_ptr[r], row_ptr[r+1])
+  const int *inc_tet;       // incident tet
+  const int *inc_local;     // the row's vertex index (0..3) in that tet
+  const int *tet_node;      // [T][4] padded offsets
+  const T *tet_grad;        // [T][4][3] sqrt|K| times the P1 gradients
+  const double *scale;      // h^2 / m of each row (lumped P1 mass)
+  const T *field;           // E^n (forward) or mu^k (adjoint), padded, 3 components
+  const T *s;               // eps - 1, padded (coefficient channel 0)
+  long long cs;             // component stride
+  T *out_r;                 // [3][n_rows] h^2 M^-1 (K E) or (K^T mu)
+  T *out_q;                 // [3][n_rows] adjoint: h^2 M^-1 (D^T D mu)
+};
+template <typename T>
+void launch_ebe(const EbeParams<T> &P, bool adj, cudaStream_t s);
 
 // Small kernels.
 void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const int *det_node,

@@ -17,7 +17,7 @@
 
 namespace ddfd {
 
-static bool invert4(const double A[4][4], double X[4][4]) {
+bool invert4(const double A[4][4], double X[4][4]) {
   double M[4][8];
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? A[r][c] : (c - 4 == r ? 1.0 : 0.0);

@@ -268,7 +268,19 @@ __global__ void __launch_bounds__(256)
           // update coefficients: nw = cen + A (cen - od) + Bc cen - Cq tau^2 R
           T A = T(1), Bc = T(0), Cq = T(1);
           T sx[3] = {T(0), T(0), T(0)};
-          if (colfem[r] && kfem) {
+          if (colfem[r] && kfem && P.ebe_r) {
+            // element-by-element rows computed by k_ebe for this step
+            const T *Q0 = (const T *)(b0 + S::Q_OFF);
+            A = Q0[oi[r]];
+            Cq = Q0[S::TXY + oi[r]];
+            const int fm = P.b - P.a - 1;
+            const long long row = (x - P.a - 1) + (long long)fm * ((y[r] - P.a - 1) + (long long)fm * (k - P.a - 1));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              R[c] = P.ebe_r[c * P.ebe_rows + row];
+              if (ADJ) sx[c] = P.ebe_q[c * P.ebe_rows + row];
+            }
+          } else if (colfem[r] && kfem) {
             const T *S0 = (const T *)(b0 + S::S_OFF);
             const T *Q0 = (const T *)(b0 + S::Q_OFF);
             const int q = ci[r];

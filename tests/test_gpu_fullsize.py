@@ -136,3 +136,28 @@ def test_gradient_matches_central_differences_at_full_size(eobs_201):
             assert abs(g[i] - fd) <= 1e-5 * scale, (which, i, g[i], fd)
             assert abs(g32[i] - fd) <= 1e-3 * scale, (which, i, g32[i], fd)
     p64.close()
+
+
+def test_element_by_element_matches_stencil_at_full_size(eobs_201):
+    """The two FEM implementations (block stencil, element gather) on the
+    201^3 workload in FP32."""
+    out = {}
+    for kind in (0, 1):
+        p = gpu_problem(W, "fp32", fem_kind=kind)
+        eps, sig = W.model()
+        p.set_coeffs(eps, sig)
+        tr = p.forward()
+        J = p.functional(eobs_201)
+        p.adjoint(eobs_201)
+        ge, gs = p.gradient()
+        out[kind] = (tr, J, ge, gs, p.get_timing())
+        p.close()
+    a, b = out[0], out[1]
+    print("EBE vs stencil at 201^3:", rel_l2(b[0], a[0]), abs(b[1] - a[1]) / abs(a[1]),
+          rel_l2(b[2], a[2]), rel_l2(b[3], a[3]),
+          "step ms fwd %.4f/%.4f adj %.4f/%.4f" % (a[4].forward_loop_ms / a[4].forward_step_kernels,
+                                                  b[4].forward_loop_ms / b[4].forward_step_kernels,
+                                                  a[4].adjoint_loop_ms / a[4].adjoint_step_kernels,
+                                                  b[4].adjoint_loop_ms / b[4].adjoint_step_kernels))
+    assert rel_l2(b[0], a[0]) <= 1e-5 and abs(b[1] - a[1]) <= 1e-5 * abs(a[1])
+    assert rel_l2(b[2], a[2]) <= 1e-4 and rel_l2(b[3], a[3]) <= 1e-4

@@ -217,3 +217,25 @@ def test_device_entry_points_match_host_ones():
     assert np.array_equal(ge.cpu().numpy(), host["g_eps"])
     assert np.array_equal(gs.cpu().numpy(), host["g_sig"])
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["tiny", "small_oblique_sine", "c1_fp64_41", "min_fem"])
+def test_element_by_element_parity_with_oracle(name, prec):
+    """fem_kind = DDFD_FEM_EBE: FEM rows gathered element by element over the
+    explicit tetrahedra instead of the block stencil; same bars."""
+    w, opt = CASES[name]
+    ref = oracle_case(name)
+    ke, km = capture_steps(w.n_steps)
+    kw, src_kw = gpu_kw(opt)
+    out = run_gpu(w, ref["eobs"], precision=prec, keep_e=ke, keep_mu=km, src_kw=src_kw,
+                  fem_kind=1, **kw)
+    tol = TOL[prec]
+    assert rel_l2(out["trace"], ref["trace"]) <= tol["E"]
+    assert abs(out["J"] - ref["J"]) <= tol["J"] * abs(ref["J"])
+    assert rel_l2(out["g_eps"], ref["g_eps"]) <= tol["g"]
+    assert rel_l2(out["g_sig"], ref["g_sig"]) <= tol["g"]
+    for s in ke:
+        assert rel_l2(out["E"][s], ref["E"][s]) <= tol["E"]
+    for s in km:
+        assert rel_l2(out["mu"][s], ref["mu"][s]) <= tol["mu"]
