@@ -245,6 +245,7 @@ StepParams<T> base_params(const ddfd_problem *p) {
   P.spin_limit = 1u << 22;
   P.r2 = (T)((p->tau / p->h) * (p->tau / p->h));
   P.cb = (T)(p->tau / p->h);
+  for (int f = 0; f < 4; ++f) P.inv_tab[f] = (T)(1.0 / (1.0 + f * (p->tau / p->h)));
   P.src_scale = 2.0 * p->tau * p->tau / p->h;
   P.pulse_kind = p->cfg.source_kind;
   P.freq = p->cfg.freq;
@@ -885,8 +886,8 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
     p->err = m;
     return bail(DDFD_E_ARG);
   }
-  if ((ce = upload_kuhn_blocks(kb, p->stream)) != cudaSuccess) {
-    p->err = std::string("constant upload: ") + cudaGetErrorString(ce);
+  if ((ce = check_kuhn_blocks(kb, p->stream)) != cudaSuccess) {
+    p->err = "the Kuhn blocks assembled from the tetrahedra differ from the compiled-in table";
     return bail(DDFD_E_CUDA);
   }
   std::vector<double> delay_host;

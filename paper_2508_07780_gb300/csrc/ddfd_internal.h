@@ -29,8 +29,9 @@ bool build_kuhn_blocks(KuhnBlocks *out, std::string *msg);
 // Inverse of a 4x4 matrix (Gauss-Jordan, partial pivoting); false if singular.
 bool invert4(const double A[4][4], double X[4][4]);
 
-// Uploads the blocks to constant memory (both precisions).
-cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
+// Checks the assembled blocks against the table compiled into the step
+// kernels (cudaErrorInvalidValue if they differ).
+cudaError_t check_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
 
 // Step-kernel tiling: a CTA of 256 threads owns a STEP_TX x TY (x, y) tile of
 // one z chunk, one node per thread and plane.
@@ -54,6 +55,7 @@ struct StepParams {
   T *old;                // written: E^{n+1} (forward) or mu^{k-1} (adjoint)
   T r2;                  // (tau/h)^2
   T cb;                  // tau/h: damping of one absorbing face, divided form
+  T inv_tab[4];          // 1 / (1 + f tau/h) for f = 0..3 absorbing faces at a node
   uint32_t abs_now;      // forward: absorbing faces at step n; adjoint: at step k-1
   uint32_t abs_next;     // adjoint: absorbing faces at step k+1
   // top-face source (forward only)

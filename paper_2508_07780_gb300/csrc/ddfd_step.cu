@@ -32,34 +32,40 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "ddfd_internal.h"
 #include "ddfd_tma.h"
 
 namespace ddfd {
 
-__constant__ double c_Bd[72];
-__constant__ float c_Bf[72];
+// The Kuhn P1 div-div blocks of an interior node in integer form: (D^T D)_{i,i+o}
+// = (h/6) kb(o, .), B_{-o} = B_o = B_o^T, offsets 0, (1,0,0), (0,1,0), (0,0,1),
+// (1,1,0), (1,0,1), (0,1,1), (1,1,1).  Compiled in so that zero and unit
+// weights cost nothing; ddfd_create checks them against the blocks it
+// assembles from the 24 Kuhn tetrahedra (csrc/ddfd_kuhn.cpp) and refuses to
+// run if they differ.
+__host__ __device__ constexpr int kb(int o, int e) {
+  constexpr int t[8][9] = {
+      {12, -4, -4, -4, 12, -4, -4, -4, 12},  // 0
+      {-6, 2, 2, 2, 0, -1, 2, -1, 0},        // (1,0,0)
+      {0, 2, -1, 2, -6, 2, -1, 2, 0},        // (0,1,0)
+      {0, -1, 2, -1, 0, 2, 2, 2, -6},        // (0,0,1)
+      {0, -2, 1, -2, 0, 1, 1, 1, 0},         // (1,1,0)
+      {0, 1, -2, 1, 0, 1, -2, 1, 0},         // (1,0,1)
+      {0, 1, 1, 1, 0, -2, 1, -2, 0},         // (0,1,1)
+      {0, -1, -1, -1, 0, -1, -1, -1, 0}};    // (1,1,1)
+  return t[o][e];
+}
 
-template <typename T>
-__device__ __forceinline__ T Bk(int i);
-template <>
-__device__ __forceinline__ double Bk<double>(int i) { return c_Bd[i]; }
-template <>
-__device__ __forceinline__ float Bk<float>(int i) { return c_Bf[i]; }
+static int kb_int(int o, int e) { return kb(o, e); }
 
-cudaError_t upload_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s) {
-  double d[72];
-  float f[72];
+cudaError_t check_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t) {
   for (int o = 0; o < 8; ++o)
-    for (int e = 0; e < 9; ++e) {
-      d[o * 9 + e] = kb.B[o][e];
-      f[o * 9 + e] = (float)kb.B[o][e];
-    }
-  cudaError_t err = cudaMemcpyToSymbolAsync(c_Bd, d, sizeof(d), 0, cudaMemcpyHostToDevice, s);
-  if (err != cudaSuccess) return err;
-  err = cudaMemcpyToSymbolAsync(c_Bf, f, sizeof(f), 0, cudaMemcpyHostToDevice, s);
-  if (err != cudaSuccess) return err;
-  return cudaStreamSynchronize(s);
+    for (int e = 0; e < 9; ++e)
+      if (std::fabs(kb.B[o][e] * 6.0 - kb_int(o, e)) > 1e-12)
+        return cudaErrorInvalidValue;
+  return cudaSuccess;
 }
 
 __device__ __forceinline__ double pulse_value(int kind, double f, double t0, double w, double t) {
@@ -71,18 +77,27 @@ __device__ __forceinline__ double pulse_value(int kind, double f, double t0, dou
   return (t > 0.0 && t < 1.0 / f) ? sin(2.0 * 3.141592653589793 * f * t) : 0.0;
 }
 
-// sum_o B_o v_{i+o} for one node, with B_{-o} = B_o; v given as the centre
-// value and the 7 (+o, -o) neighbour pairs already summed.
+// sum_o B_o v_{i+o} for one node (B = kb / 6), with B_{-o} = B_o; v given as
+// the centre value and the 7 (+o, -o) neighbour pairs already summed.
 template <typename T>
 __device__ __forceinline__ void block_apply(const T v0[3], const T vp[7][3], T out[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    T acc = Bk<T>(c * 3 + 0) * v0[0] + Bk<T>(c * 3 + 1) * v0[1] + Bk<T>(c * 3 + 2) * v0[2];
+    T acc = T(kb(0, c * 3 + 0)) * v0[0] + T(kb(0, c * 3 + 1)) * v0[1] + T(kb(0, c * 3 + 2)) * v0[2];
 #pragma unroll
-    for (int p = 0; p < 7; ++p)
-      acc += Bk<T>((p + 1) * 9 + c * 3 + 0) * vp[p][0] + Bk<T>((p + 1) * 9 + c * 3 + 1) * vp[p][1] +
-             Bk<T>((p + 1) * 9 + c * 3 + 2) * vp[p][2];
-    out[c] = acc;
+    for (int p = 0; p < 7; ++p) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int w = kb(p + 1, c * 3 + d);
+        if (w == 1)
+          acc += vp[p][d];
+        else if (w == -1)
+          acc -= vp[p][d];
+        else if (w != 0)
+          acc += T(w) * vp[p][d];
+      }
+    }
+    out[c] = acc * T(1.0 / 6.0);
   }
 }
 
@@ -117,11 +132,16 @@ struct Stage {
   static constexpr int BYTES = Q_OFF + up128(Q_BYTES);
   // FP32: 6 stages (3 CTAs per SM); FP64: 4 stages (2 CTAs per SM)
   static constexpr int RING = sizeof(T) == 4 ? 6 : 4;
-  static constexpr int SMEM = RING * BYTES + RING * 8 + 128;
+  static constexpr int SMEM = RING * BYTES + 2 * RING * 8 + 128;
 };
 
+// Warp roles: warps 0..7 compute (one node per thread and plane), warp 8
+// stages planes.
+constexpr int STEP_CONSUMERS = 256;
+constexpr int STEP_THREADS = STEP_CONSUMERS + 32;
+
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
     k_step(const __grid_constant__ CUtensorMap mcur, const __grid_constant__ CUtensorMap mold,
            const __grid_constant__ CUtensorMap ms, const __grid_constant__ CUtensorMap mq,
            const StepParams<T> P) {
@@ -130,7 +150,8 @@ __global__ void __launch_bounds__(256)
   constexpr int BW = S::BXW;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);
+  uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);  // "full": plane landed
+  uint64_t *emp = bar + S::RING;                             // "empty": consumers released it
   const int n = P.n;
   const int tid = threadIdx.x;
 
@@ -155,10 +176,11 @@ __global__ void __launch_bounds__(256)
   const bool tile_fem = x0 <= P.b - 1 && x0 + STEP_TX - 1 >= P.a + 1 && y0 <= P.b - 1 &&
                         y0 + S::TY - 1 >= P.a + 1;
 
-  __shared__ int sh_fail;
   if (tid == 0) {
-    sh_fail = 0;
-    for (int s = 0; s < S::RING; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < S::RING; ++s) {
+      mbar_init(&bar[s], 1);
+      mbar_init(&emp[s], STEP_CONSUMERS / 32);
+    }
     mbar_fence_init();
     tma_prefetch_desc(&mcur);
     tma_prefetch_desc(&mold);
@@ -167,31 +189,46 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
 
-  int issued = 0, islot = 0;  // thread 0: planes issued so far, slot of the next one
-  auto issue = [&]() {       // thread 0: stage plane `issued` into slot `islot`
-    const int kk = k0 - 1 + issued;
-    const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
-    unsigned char *st = smem + islot * S::BYTES;
-    const bool interior = kk >= k0 && kk < k1;
-    const bool coef = tile_fem && kk >= P.a && kk <= P.b;
-    const bool qc = coef && interior;
-    const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
-                           (qc ? S::Q_BYTES : 0);
-    uint64_t *bb = &bar[islot];
-    mbar_expect_tx(bb, bytes);
-    tma_load_4d(st + S::E_OFF, &mcur, x0 - S::HX, y0 - 1, ksrc, 0, bb);
-    if (interior) tma_load_4d(st + S::O_OFF, &mold, x0, y0, kk, 0, bb);
-    if (coef) tma_load_4d(st + S::S_OFF, &ms, x0 - S::HX, y0 - 1, kk, 0, bb);
-    if (qc) tma_load_4d(st + S::Q_OFF, &mq, x0, y0, kk, 0, bb);
-    ++issued;
-    if (++islot == S::RING) islot = 0;
-  };
-  if (tid == 0)
-    while (issued < nplanes && issued < S::RING) issue();
+  if (tid >= STEP_CONSUMERS) {
+    // Producer warp: lane 0 stages plane p (k0-1+p) into slot p % RING once the
+    // consumers have released the slot's previous plane (p - RING).
+    if (tid != STEP_CONSUMERS) return;
+    int p = 0;
+    bool ok = true;
+    for (; p < nplanes; ++p) {
+      const int slot = p % S::RING;
+      // plane p reuses the slot of plane p - RING, whose release is completion
+      // number p/RING - 1 of that slot's empty barrier
+      if (p >= S::RING && !mbar_wait_bounded(&emp[slot], (uint32_t)((p / S::RING - 1) & 1), P.spin_limit)) {
+        ok = false;
+        break;
+      }
+      const int kk = k0 - 1 + p;
+      const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
+      unsigned char *st = smem + slot * S::BYTES;
+      const bool interior = kk >= k0 && kk < k1;
+      const bool coef = tile_fem && kk >= P.a && kk <= P.b;
+      const bool qc = coef && interior;
+      const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
+                             (qc ? S::Q_BYTES : 0);
+      uint64_t *bb = &bar[slot];
+      mbar_expect_tx(bb, bytes);
+      tma_load_4d(st + S::E_OFF, &mcur, x0 - S::HX, y0 - 1, ksrc, 0, bb);
+      if (interior) tma_load_4d(st + S::O_OFF, &mold, x0, y0, kk, 0, bb);
+      if (coef) tma_load_4d(st + S::S_OFF, &ms, x0 - S::HX, y0 - 1, kk, 0, bb);
+      if (qc) tma_load_4d(st + S::Q_OFF, &mq, x0, y0, kk, 0, bb);
+    }
+    if (!ok) atomicOr(P.err, 4);
+    // every issued plane must land before the CTA can retire (bounded)
+    const int first = p > S::RING ? p - S::RING : 0;
+    for (int q = first; q < p; ++q)
+      mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), P.spin_limit);
+    return;
+  }
 
   const long long plane = (long long)P.px * n;
   const uint32_t cs = (uint32_t)P.cs;
-  bool failed = false;
+  const uint32_t sides = (P.abs_now | P.abs_next) & (DDFD_ABS_X0 | DDFD_ABS_X1 | DDFD_ABS_Y0 | DDFD_ABS_Y1);
   int wq = 0, wslot = 0;   // planes waited so far, slot of the next wait
   uint32_t wphase = 0;     // parity of the next wait
   int sm1 = 0, s0 = 1, sp1 = 2;  // slots of planes p-1, p, p+1 (p = k - k0 + 1)
@@ -212,7 +249,9 @@ __global__ void __launch_bounds__(256)
       live[r] = x < n && y[r] < n;
       colfem[r] = x > P.a && x < P.b && y[r] > P.a && y[r] < P.b;
       colfree[r] = x >= P.f0 && x < P.f0 + P.nf && y[r] >= P.f0 && y[r] < P.f0 + P.nf;
-      colbnd[r] = x == 0 || x == n - 1 || y[r] == 0 || y[r] == n - 1;
+      // side columns need the boundary path only where a side face absorbs
+      colbnd[r] = (x == 0 && (sides & DDFD_ABS_X0)) || (x == n - 1 && (sides & DDFD_ABS_X1)) ||
+                  (y[r] == 0 && (sides & DDFD_ABS_Y0)) || (y[r] == n - 1 && (sides & DDFD_ABS_Y1));
       out[r] = P.old + (long long)k0 * plane + (long long)P.px * y[r] + x;
     }
     const int dxm = (x == 0) ? 1 : -1, dxp = (x == n - 1) ? -1 : 1;
@@ -232,7 +271,10 @@ __global__ void __launch_bounds__(256)
           wphase ^= 1u;
         }
       }
-      if (!ok) sh_fail = 1;  // read by every thread after the barrier below
+      if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform, so __syncwarp below stays safe
+        if ((tid & 31) == 0) atomicOr(P.err, 4);
+        break;  // the producer times out on the slots we no longer release
+      }
       const unsigned char *bm1 = smem + sm1 * S::BYTES;
       const unsigned char *b0 = smem + s0 * S::BYTES;
       const unsigned char *bp1 = smem + sp1 * S::BYTES;
@@ -242,7 +284,9 @@ __global__ void __launch_bounds__(256)
       const T *O0 = (const T *)(b0 + S::O_OFF);
       const bool kfem = k > P.a && k < P.b;
       const bool kfree = k >= P.f0 && k < P.f0 + P.nf;
-      const bool kbnd = k == 0 || k == n - 1;
+      // bottom plane: absorbing or plain Neumann; top plane: source, absorbing
+      // face or detector residuals
+      const bool kbnd = (k == 0 && ((P.abs_now | P.abs_next) & DDFD_ABS_BOTTOM)) || k == n - 1;
 #pragma unroll
       for (int r = 0; r < S::RPT; ++r) {
         T above[3];
@@ -254,7 +298,7 @@ __global__ void __launch_bounds__(256)
           }
           above[c] = Ep[c * RE + ci[r]];
         }
-        if (ok && live[r]) {
+        if (live[r]) {
           const bool fre = colfree[r] && kfree;
           long long fi = 0;
           if (fre) fi = (x - P.f0) + (long long)P.nf * ((y[r] - P.f0) + (long long)P.nf * (k - P.f0));
@@ -329,9 +373,10 @@ __global__ void __launch_bounds__(256)
           if (colbnd[r] || kbnd) {
             // boundary node: damping of the absorbing faces, top-face source or
             // detector residuals
-            const T cc = P.cb * T(face_count(x, y[r], k, n, P.abs_now));
+            const int fn = face_count(x, y[r], k, n, P.abs_now);
+            const T cc = P.cb * T(fn);
             const T ccn = ADJ ? P.cb * T(face_count(x, y[r], k, n, P.abs_next)) : cc;
-            const T inv = T(1) / (T(1) + cc);
+            const T inv = P.inv_tab[fn];  // 1 / (1 + cc)
             A = (T(1) - ccn) * inv;
             Bc = (ccn - cc) * inv;
             Cq = inv;
@@ -394,26 +439,12 @@ __global__ void __launch_bounds__(256)
         }
         out[r] += plane;
       }
-      __syncthreads();  // every thread is done with plane k-1's slot
-      if (sh_fail) {    // uniform across the CTA: decided before the barrier
-        failed = true;
-        break;
-      }
-      if (tid == 0 && issued < nplanes) issue();  // refills the slot of plane p-1
+      // release plane p-1 (its slot) to the producer: one arrival per warp
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&emp[sm1]);
       sm1 = s0;
       s0 = sp1;
       sp1 = (sp1 + 1 == S::RING) ? 0 : sp1 + 1;
-    }
-  }
-  if (failed && tid == 0) {
-    atomicOr(P.err, 4);
-    // let the copies already issued land before the CTA exits (bounded)
-    for (; wq < issued; ++wq) {
-      mbar_wait_bounded(&bar[wslot], wphase, P.spin_limit);
-      if (++wslot == S::RING) {
-        wslot = 0;
-        wphase ^= 1u;
-      }
     }
   }
 }
@@ -436,7 +467,7 @@ template <typename T, bool ADJ>
 static void launch_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
   const int ty = Stage<T>::TY;
   const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, (P.n + P.kz - 1) / P.kz);
-  k_step<T, ADJ><<<grid, 256, Stage<T>::SMEM, s>>>(*m.cur, *m.old, *m.s, *m.q, P);
+  k_step<T, ADJ><<<grid, STEP_THREADS, Stage<T>::SMEM, s>>>(*m.cur, *m.old, *m.s, *m.q, P);
 }
 
 template <typename T>
