@@ -13,6 +13,7 @@ from .models import (  # noqa: F401
     detector_grid,
     hemisphere_directions,
     layered_inclusion_model,
+    shard_directions,
     workload,
     WORKLOADS,
 )

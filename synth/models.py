@@ -139,6 +139,16 @@ def hemisphere_directions(n_src: int, seed: int) -> np.ndarray:
     return out
 
 
+def shard_directions(n_src: int, seed: int = 5) -> np.ndarray:
+    """n_src incidence directions for source sharding: normal incidence first,
+    then n_src - 1 drawn on the lower hemisphere."""
+    d = np.zeros((n_src, 3))
+    d[0, 2] = -1.0
+    if n_src > 1:
+        d[1:] = hemisphere_directions(n_src - 1, seed)
+    return d
+
+
 @dataclass(frozen=True)
 class Workload:
     """One problem description, as plain numbers and seeds."""
