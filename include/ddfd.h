@@ -50,6 +50,7 @@ extern "C" {
 #endif
 
 typedef struct ddfd_problem ddfd_problem; /* opaque; owns all its device memory */
+typedef struct ddfd_batch ddfd_batch;     /* opaque; a set of problems stepped together */
 
 typedef enum {
   DDFD_OK = 0,
@@ -210,6 +211,72 @@ int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t);
  * as 3 * n^3 doubles (component-major, node order) to host memory. */
 int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps);
 int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out);
+
+/* Tile autotuner for the step kernels of one handle.  Times `steps` forward
+ * and `steps` adjoint step kernels (CUDA events on the handle's stream) for
+ * each candidate z depth of the thread-block tile (32 x 8 x kz nodes; kz in
+ * 4, 6, 8, 12, 16, 24, 32, up to n) and keeps the fastest; *tile_kz_out (may
+ * be NULL) receives it.  The trial steps overwrite the fields, so forward
+ * and adjoint state are invalidated (run ddfd_forward again).  1 <= steps
+ * <= n_steps.  The paper has no counterpart (a GPU tuning aid). */
+int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out);
+
+/* Batched heterogeneous problems.  count (1..256) problems with the same n,
+ * n_steps, cfl and precision and the stencil FEM apply, each with its own
+ * FEM cube size fem_n, detectors, absorbing faces, regularisation,
+ * n_snapshots and one incident plane wave (n_src = 1, src_dir may differ;
+ * several waves on one model are several members with the same
+ * coefficients).  The members' fields are stacked in one allocation and
+ * every time step of the whole batch is one kernel launch per group of 16
+ * members, the whole forward (adjoint) sequence one CUDA graph.  Members
+ * that checkpoint (n_snapshots > 0) must share the segment length
+ * ceil(n_steps / n_snapshots).  Stream: cfgs[0].stream for all work.
+ * The paper solves its measurements one by one; batching is a GPU
+ * throughput device and changes no result: a member's trace, J and
+ * gradient are bitwise those of the same problem run alone.
+ * Errors: DDFD_E_ARG (mismatched members), DDFD_E_OOM, DDFD_E_CUDA; the
+ * message is ddfd_create_error(). */
+int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out);
+void ddfd_destroy_batch(ddfd_batch *b);  /* NULL allowed; destroys the members too */
+const char *ddfd_batch_last_error(const ddfd_batch *b);
+
+/* Member i as a problem handle, owned by the batch (ddfd_destroy ignores
+ * it).  Every single-problem call works on it: ddfd_set_coeffs,
+ * ddfd_functional, ddfd_gradient after a batch run, and also ddfd_forward /
+ * ddfd_adjoint, which run that member alone. */
+int ddfd_batch_member(ddfd_batch *b, int32_t i, ddfd_problem **out);
+
+/* Forward solve of every member in the batched launches.  trace_out may be
+ * NULL; else trace_out[i] (may be NULL) receives member i's trace (host,
+ * layout of ddfd_forward).  Afterwards every member is in the forward state. */
+int ddfd_batch_forward(ddfd_batch *b, double *const *trace_out);
+/* Same; trace_out[i] are device pointers. */
+int ddfd_batch_forward_dev(ddfd_batch *b, double *const *trace_out);
+
+/* Adjoint solve of every member in the batched launches; eobs[i] is member
+ * i's observed trace (host, layout of ddfd_adjoint).  Requires every member
+ * in the forward state (DDFD_E_STATE).  Afterwards ddfd_gradient(member)
+ * returns each member's gradient. */
+int ddfd_batch_adjoint(ddfd_batch *b, const double *const *eobs);
+/* Same; eobs[i] are device pointers. */
+int ddfd_batch_adjoint_dev(ddfd_batch *b, const double *const *eobs);
+
+/* The tile autotuner of ddfd_autotune, timing the batched launches; it
+ * invalidates every member's forward and adjoint state. */
+int ddfd_batch_autotune(ddfd_batch *b, int32_t steps, int32_t *tile_kz_out);
+
+/* Bookkeeping of a batch: timing of the last batched forward / adjoint
+ * sequences (device time, CUDA events on the batch stream; step kernels
+ * counts one per batched launch), kernels launched, device bytes of the
+ * batch and its members, and the tile depth in use. */
+typedef struct {
+  int32_t count, tile_kz;
+  double forward_loop_ms, adjoint_loop_ms;
+  int64_t forward_step_kernels, adjoint_step_kernels;
+  int64_t kernel_launches;
+  int64_t device_bytes;
+} ddfd_batch_info;
+int ddfd_batch_get_info(const ddfd_batch *b, ddfd_batch_info *info);
 
 /* Allocation-free data misfit, without a handle.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

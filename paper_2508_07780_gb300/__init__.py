@@ -7,6 +7,7 @@ include/ddfd.h.  This package holds the ctypes binding and the build script.
 from .binding import (  # noqa: F401
     ABI_SYMBOLS,
     DDFDError,
+    Batch,
     Problem,
     ddfd_config,
     ddfd_info,

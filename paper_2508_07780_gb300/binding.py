@@ -35,6 +35,9 @@ ABI_SYMBOLS = (
     "ddfd_forward_dev", "ddfd_functional", "ddfd_functional_dev", "ddfd_adjoint",
     "ddfd_adjoint_dev", "ddfd_gradient", "ddfd_gradient_dev", "ddfd_get_info",
     "ddfd_set_capture", "ddfd_get_capture", "ddfd_get_timing", "ddfd_misfit_noalloc",
+    "ddfd_autotune", "ddfd_create_batch", "ddfd_destroy_batch", "ddfd_batch_last_error",
+    "ddfd_batch_member", "ddfd_batch_forward", "ddfd_batch_forward_dev", "ddfd_batch_adjoint",
+    "ddfd_batch_adjoint_dev", "ddfd_batch_autotune", "ddfd_batch_get_info",
 )
 
 
@@ -64,6 +67,15 @@ class ddfd_timing(ctypes.Structure):
     _fields_ = [
         ("forward_loop_ms", c_double), ("adjoint_loop_ms", c_double),
         ("forward_step_kernels", c_int64), ("adjoint_step_kernels", c_int64),
+    ]
+
+
+class ddfd_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("count", c_int32), ("tile_kz", c_int32),
+        ("forward_loop_ms", c_double), ("adjoint_loop_ms", c_double),
+        ("forward_step_kernels", c_int64), ("adjoint_step_kernels", c_int64),
+        ("kernel_launches", c_int64), ("device_bytes", c_int64),
     ]
 
 
@@ -111,9 +123,21 @@ def load_library(path: str = LIB_PATH):
     lib.ddfd_misfit_noalloc.argtypes = [P, P, c_int32, c_int32, c_int32, c_double, c_double, P, P]
     lib.ddfd_set_capture.argtypes = [P, c_int32, P]
     lib.ddfd_get_capture.argtypes = [P, c_int32, c_int32, P]
+    lib.ddfd_autotune.argtypes = [P, c_int32, POINTER(c_int32)]
+    lib.ddfd_create_batch.argtypes = [POINTER(ddfd_config), c_int32, POINTER(c_void_p)]
+    lib.ddfd_destroy_batch.argtypes = [P]
+    lib.ddfd_destroy_batch.restype = None
+    lib.ddfd_batch_last_error.argtypes = [P]
+    lib.ddfd_batch_last_error.restype = c_char_p
+    lib.ddfd_batch_member.argtypes = [P, c_int32, POINTER(c_void_p)]
+    for name in ("ddfd_batch_forward", "ddfd_batch_forward_dev", "ddfd_batch_adjoint",
+                 "ddfd_batch_adjoint_dev"):
+        getattr(lib, name).argtypes = [P, P]
+    lib.ddfd_batch_autotune.argtypes = [P, c_int32, POINTER(c_int32)]
+    lib.ddfd_batch_get_info.argtypes = [P, POINTER(ddfd_batch_info)]
     for name in ABI_SYMBOLS:
         if name not in ("ddfd_config_default", "ddfd_destroy", "ddfd_last_error",
-                        "ddfd_create_error"):
+                        "ddfd_create_error", "ddfd_destroy_batch", "ddfd_batch_last_error"):
             getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -160,6 +184,33 @@ def misfit_noalloc(trace, eobs, n_src, n_steps, n_det, tau, z_delta_frac, J, str
         raise DDFDError(st, lib.ddfd_create_error().decode())
 
 
+def make_config(lib, kw, keep):
+    """ddfd_config from keyword arguments (config field names; src_dir and
+    det_ij as arrays, precision as "fp32"/"fp64" or the enum, stream as an
+    integer handle).  Arrays the struct points to are appended to keep."""
+    cfg = ddfd_config()
+    lib.ddfd_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if k == "src_dir":
+            if v is not None:
+                arr = _host(v, np.float64).reshape(-1, 3)
+                keep.append(arr)
+                cfg.src_dir = arr.ctypes.data_as(POINTER(c_double))
+                cfg.n_src = arr.shape[0]
+        elif k == "det_ij":
+            arr = _host(v, np.int32).reshape(-1, 2)
+            keep.append(arr)
+            cfg.det_ij = arr.ctypes.data_as(POINTER(c_int32))
+            cfg.n_det = arr.shape[0]
+        elif k == "stream":
+            cfg.stream = c_void_p(v)
+        elif k == "precision" and isinstance(v, str):
+            cfg.precision = DDFD_FP32 if v == "fp32" else DDFD_FP64
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
 class Problem:
     """One ddfd handle.  Keyword arguments are ddfd_config fields; src_dir and
     det_ij are arrays ([n_src][3] floats, [n_det][2] ints)."""
@@ -167,34 +218,33 @@ class Problem:
     def __init__(self, **kw):
         lib = load_library()
         self._lib = lib
-        cfg = ddfd_config()
-        lib.ddfd_config_default(ctypes.byref(cfg))
         self._keep = []
-        for k, v in kw.items():
-            if k == "src_dir":
-                if v is not None:
-                    arr = _host(v, np.float64).reshape(-1, 3)
-                    self._keep.append(arr)
-                    cfg.src_dir = arr.ctypes.data_as(POINTER(c_double))
-                    cfg.n_src = arr.shape[0]
-            elif k == "det_ij":
-                arr = _host(v, np.int32).reshape(-1, 2)
-                self._keep.append(arr)
-                cfg.det_ij = arr.ctypes.data_as(POINTER(c_int32))
-                cfg.n_det = arr.shape[0]
-            elif k == "stream":
-                cfg.stream = c_void_p(v)
-            elif k == "precision" and isinstance(v, str):
-                cfg.precision = DDFD_FP32 if v == "fp32" else DDFD_FP64
-            else:
-                setattr(cfg, k, v)
+        cfg = make_config(lib, kw, self._keep)
         self.cfg = cfg
         h = c_void_p()
         st = lib.ddfd_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != DDFD_OK:
             raise DDFDError(st, lib.ddfd_create_error().decode())
         self._h = h
+        self._owned = True
         self.info = self.get_info()
+
+    @classmethod
+    def _member(cls, lib, handle, batch):
+        """A batch member: a handle the batch owns (close() does nothing)."""
+        self = cls.__new__(cls)
+        self._lib = lib
+        self._keep = []
+        self._h = handle
+        self._owned = False
+        self._batch = batch
+        self.info = self.get_info()
+        return self
+
+    def autotune(self, steps=8):
+        kz = c_int32()
+        self._check(self._lib.ddfd_autotune(self._h, steps, ctypes.byref(kz)))
+        return kz.value
 
     # -- helpers -------------------------------------------------------------
     def _check(self, st):
@@ -203,7 +253,8 @@ class Problem:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.ddfd_destroy(self._h)
+            if self._owned:
+                self._lib.ddfd_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -302,3 +353,95 @@ class Problem:
         out = np.empty(3 * n ** 3)
         self._check(self._lib.ddfd_get_capture(self._h, kind, idx, _ptr(out)))
         return out.reshape(3, n ** 3)
+
+
+class Batch:
+    """ddfd_batch: problems with the same grid, step count and precision,
+    stepped together (one launch per time step for up to 16 members).
+    ``configs`` is a list of keyword dicts as for ``Problem``; ``members``
+    are Problem views of the batch's handles (set_coeffs, functional and
+    gradient per member)."""
+
+    def __init__(self, configs):
+        lib = load_library()
+        self._lib = lib
+        self._keep = []
+        arr = (ddfd_config * len(configs))()
+        for i, kw in enumerate(configs):
+            arr[i] = make_config(lib, kw, self._keep)
+        h = c_void_p()
+        st = lib.ddfd_create_batch(arr, len(configs), ctypes.byref(h))
+        if st != DDFD_OK:
+            raise DDFDError(st, lib.ddfd_create_error().decode())
+        self._h = h
+        self.members = []
+        for i in range(len(configs)):
+            m = c_void_p()
+            self._check(lib.ddfd_batch_member(h, i, ctypes.byref(m)))
+            self.members.append(Problem._member(lib, m, self))
+
+    def _check(self, st):
+        if st != DDFD_OK:
+            raise DDFDError(st, self._lib.ddfd_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None
+            self._lib.ddfd_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __len__(self):
+        return len(self.members)
+
+    def get_info(self):
+        inf = ddfd_batch_info()
+        self._check(self._lib.ddfd_batch_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def autotune(self, steps=8):
+        kz = c_int32()
+        self._check(self._lib.ddfd_batch_autotune(self._h, steps, ctypes.byref(kz)))
+        return kz.value
+
+    def forward(self, want_trace=True):
+        """Batched forward; returns the members' traces (host) or None."""
+        outs = [np.empty(m.trace_shape) for m in self.members] if want_trace else None
+        ptrs = (c_void_p * len(self.members))(*[o.ctypes.data for o in outs]) if outs else None
+        self._check(self._lib.ddfd_batch_forward(self._h, ptrs))
+        return outs
+
+    def adjoint(self, eobs):
+        es = [_host(e, np.float64, int(np.prod(m.trace_shape))) for e, m in zip(eobs, self.members)]
+        ptrs = (c_void_p * len(es))(*[e.ctypes.data for e in es])
+        self._check(self._lib.ddfd_batch_adjoint(self._h, ptrs))
+
+    def forward_dev(self, trace_out=None):
+        """trace_out: None or one float64 CUDA tensor (or None) per member."""
+        ptrs = None
+        if trace_out is not None:
+            for t, m in zip(trace_out, self.members):
+                if t is not None:
+                    _dev(t, int(np.prod(m.trace_shape)))
+            ptrs = (c_void_p * len(trace_out))(*[t.data_ptr() if t is not None else None
+                                                 for t in trace_out])
+        self._check(self._lib.ddfd_batch_forward_dev(self._h, ptrs))
+        return trace_out
+
+    def adjoint_dev(self, eobs):
+        for e, m in zip(eobs, self.members):
+            _dev(e, int(np.prod(m.trace_shape)))
+        ptrs = (c_void_p * len(eobs))(*[e.data_ptr() for e in eobs])
+        self._check(self._lib.ddfd_batch_adjoint_dev(self._h, ptrs))

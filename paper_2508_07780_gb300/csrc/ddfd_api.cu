@@ -90,9 +90,15 @@ struct ddfd_problem {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gfwd = nullptr, gadj = nullptr;
   int64_t gfwd_launches = 0, gadj_launches = 0;
+  // batch member: E, Mu and the coefficient field are slot `slot` of the
+  // batch's stacked slabs (not owned); the batch destroys its members
+  ddfd_batch *batch = nullptr;
+  int slot = 0;
 };
 
 namespace {
+
+void destroy_problem(ddfd_problem *p);
 
 int fail(ddfd_problem *p, int code, const std::string &m) {
   p->err = m;
@@ -263,6 +269,53 @@ StepParams<T> base_params(const ddfd_problem *p) {
   return P;
 }
 
+template <typename T>
+void set_source(StepParams<T> &P, const ddfd_problem *p, int s) {
+  P.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
+  P.oblique = p->oblique[s];
+  for (int q = 0; q < 3; ++q) P.pol[q] = p->pol[3 * s + q];
+}
+
+// Per-step scalars of forward step st (E^st -> E^{st+1}) of source s.
+template <typename T>
+void set_forward_step(StepParams<T> &P, const ddfd_problem *p, int s, int st, const void *cur, void *old,
+                      T *hist_w) {
+  P.cur = (const T *)cur;
+  P.old = (T *)old;
+  P.abs_now = faces_at(p, s, st);
+  P.src_on = st <= p->n1[s] ? 1 : 0;
+  P.t_n = st * p->tau;
+  P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * p->Nt + st]);
+  P.trace_n = p->trace + ((size_t)s * (p->Nt + 1) + st) * p->n_det * 3;
+  P.hist_w = hist_w;
+}
+
+// Per-step scalars of adjoint step k (mu^k -> mu^{k-1}) of source s.
+template <typename T>
+void set_adjoint_step(StepParams<T> &P, const ddfd_problem *p, int s, int k, const void *cur, void *old,
+                      const T *hist_r) {
+  P.cur = (const T *)cur;
+  P.old = (T *)old;
+  P.abs_now = faces_at(p, s, k - 1);
+  P.abs_next = faces_at(p, s, k + 1);
+  P.res_k = p->res + ((size_t)s * (p->Nt + 1) + k) * p->n_det * 3;
+  P.hist_r = hist_r;
+}
+
+template <typename T>
+StepLaunch<T, 1> single_launch(const StepParams<T> &P, const CUtensorMap &cur, const CUtensorMap &old,
+                               const ddfd_problem *p) {
+  StepLaunch<T, 1> L;
+  L.cur = cur;
+  L.old = old;
+  L.s = p->mS;
+  L.q = p->mQ;
+  L.nprob = 1;
+  L.zchunks = (p->n + P.kz - 1) / P.kz;
+  L.p[0] = P;
+  return L;
+}
+
 int capture_slot(const ddfd_problem *p, int step) {
   for (size_t q = 0; q < p->cap_steps.size(); ++q)
     if (p->cap_steps[q] == step) return (int)q;
@@ -307,25 +360,17 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
     }
     int ic = 1, io = 0;  // buffer holding E^n, and E^{n-1}
     StepParams<T> P = base_params<T>(p);
-    P.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
-    P.oblique = p->oblique[s];
-    for (int q = 0; q < 3; ++q) P.pol[q] = p->pol[3 * s + q];
+    set_source(P, p, s);
     for (int st = 0; st < Nt; ++st) {
       if (p->nsnap && st % p->seg == 0) {  // snapshot the state (E^st, E^{st-1})
         char *sn = (char *)p->snap + ((size_t)s * p->nsnap + st / p->seg) * 2 * fbytes;
         CK(cudaMemcpyAsync(sn, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
         CK(cudaMemcpyAsync(sn + fbytes, p->E[io], fbytes, cudaMemcpyDeviceToDevice, sm));
       }
-      P.cur = (const T *)p->E[ic];
-      P.old = (T *)p->E[io];
-      P.abs_now = faces_at(p, s, st);
-      P.src_on = st <= p->n1[s] ? 1 : 0;
-      P.t_n = st * p->tau;
-      P.src_y = (T)(P.src_scale * p->ptab[(size_t)s * Nt + st]);
-      P.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;
-      P.hist_w = p->nsnap ? nullptr : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free;
+      set_forward_step(P, p, s, st, p->E[ic], p->E[io],
+                       p->nsnap ? nullptr : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free);
       enqueue_ebe<T>(p, p->E[ic], false, sm, nk);
-      launch_forward_step<T>(StepMaps{&p->mE_halo[ic], &p->mE_ctr[io], &p->mS, &p->mQ}, P, sm);
+      launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
       ++*nk;
       std::swap(ic, io);
       if (s == 0) {
@@ -369,20 +414,12 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
         CK(cudaMemcpyAsync(p->E[0], sn + fbytes, fbytes, cudaMemcpyDeviceToDevice, sm));
         int fc = 1, fo = 0;
         StepParams<T> F = base_params<T>(p);
-        F.delay = p->delay ? p->delay + (size_t)s * p->n * p->n : nullptr;
-        F.oblique = p->oblique[s];
-        for (int q = 0; q < 3; ++q) F.pol[q] = p->pol[3 * s + q];
+        set_source(F, p, s);
         for (int st = n0; st < n1; ++st) {
-          F.cur = (const T *)p->E[fc];
-          F.old = (T *)p->E[fo];
-          F.abs_now = faces_at(p, s, st);
-          F.src_on = st <= p->n1[s] ? 1 : 0;
-          F.t_n = st * p->tau;
-          F.src_y = (T)(F.src_scale * p->ptab[(size_t)s * Nt + st]);
-          F.trace_n = p->trace + ((size_t)s * (Nt + 1) + st) * p->n_det * 3;  // same values again
-          F.hist_w = (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free;
+          // (the trace is written again with the same values)
+          set_forward_step(F, p, s, st, p->E[fc], p->E[fo], (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free);
           enqueue_ebe<T>(p, p->E[fc], false, sm, nk);
-          launch_forward_step<T>(StepMaps{&p->mE_halo[fc], &p->mE_ctr[fo], &p->mS, &p->mQ}, F, sm);
+          launch_forward_step(single_launch(F, p->mE_halo[fc], p->mE_ctr[fo], p), sm);
           ++*nk;
           std::swap(fc, fo);
         }
@@ -391,14 +428,9 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
         hbase = (const T *)p->hist + (size_t)s * (Nt + 1) * 3 * p->n_free;
       }
       for (int k = n1; k >= n0 + 1; --k) {
-        P.cur = (const T *)p->Mu[ic];
-        P.old = (T *)p->Mu[io];
-        P.abs_now = faces_at(p, s, k - 1);
-        P.abs_next = faces_at(p, s, k + 1);
-        P.res_k = p->res + ((size_t)s * (Nt + 1) + k) * p->n_det * 3;
-        P.hist_r = hbase + (size_t)(k - n0) * 3 * p->n_free;
+        set_adjoint_step(P, p, s, k, p->Mu[ic], p->Mu[io], hbase + (size_t)(k - n0) * 3 * p->n_free);
         enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk);
-        launch_adjoint_step<T>(StepMaps{&p->mM_halo[ic], &p->mM_ctr[io], &p->mS, &p->mQ}, P, sm);
+        launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
         ++*nk;
         std::swap(ic, io);
         if (s == 0) {
@@ -521,7 +553,8 @@ int cfl_check(ddfd_problem *p) {
 // (32 + 2 hx) x (TY + 2) x 1 x ch starting hx elements (16 bytes) left of
 // the tile, the centre box 32 x TY x 1 x ch.  Out-of-range elements read as
 // zero.
-int encode_map(ddfd_problem *p, CUtensorMap *m, void *base, int channels, bool halo) {
+int encode_map(std::string *err, CUtensorMap *m, void *base, int n, int px, int fp32, int channels,
+               int box_channels, bool halo) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -529,24 +562,43 @@ int encode_map(ddfd_problem *p, CUtensorMap *m, void *base, int channels, bool h
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
             cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
-      return fail(p, DDFD_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+      return *err = "cuTensorMapEncodeTiled is not available from the driver", DDFD_E_CUDA;
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  const cuuint64_t esz = p->esz;
-  const cuuint64_t dims[4] = {(cuuint64_t)p->n, (cuuint64_t)p->n, (cuuint64_t)p->n, (cuuint64_t)channels};
-  const cuuint64_t strides[3] = {(cuuint64_t)p->px * esz, (cuuint64_t)p->px * p->n * esz,
-                                 (cuuint64_t)p->cs * esz};
+  const cuuint64_t esz = fp32 ? 4 : 8;
+  const cuuint64_t cs = (cuuint64_t)px * n * n;
+  const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)channels};
+  const cuuint64_t strides[3] = {(cuuint64_t)px * esz, (cuuint64_t)px * n * esz, cs * esz};
   const cuuint32_t hx = (cuuint32_t)(16 / esz);
-  const cuuint32_t ty = p->fp32 ? StepTile<float>::TY : StepTile<double>::TY;
+  const cuuint32_t ty = fp32 ? StepTile<float>::TY : StepTile<double>::TY;
   const cuuint32_t box[4] = {halo ? (cuuint32_t)STEP_TX + 2 * hx : (cuuint32_t)STEP_TX, halo ? ty + 2 : ty, 1,
-                             (cuuint32_t)channels};
+                             (cuuint32_t)box_channels};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = encode(m, p->fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+  const CUresult r = encode(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(p, DDFD_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  if (r != CUDA_SUCCESS) return *err = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r), DDFD_E_CUDA;
   return DDFD_OK;
+}
+
+// The six descriptors of `problems` stacked problems: fields E[q], Mu[q]
+// (3 channels each per problem) and the coefficients (s, q1, q2).
+struct FieldMaps {
+  CUtensorMap E_halo[2], E_ctr[2], M_halo[2], M_ctr[2], S, Q;
+};
+int encode_field_maps(std::string *err, FieldMaps *fm, void *const E[2], void *const Mu[2], void *coef, int n,
+                      int px, int fp32, int problems) {
+  const int ch = 3 * problems;
+  int st;
+  for (int q = 0; q < 2; ++q)
+    if ((st = encode_map(err, &fm->E_halo[q], E[q], n, px, fp32, ch, 3, true)) ||
+        (st = encode_map(err, &fm->E_ctr[q], E[q], n, px, fp32, ch, 3, false)) ||
+        (st = encode_map(err, &fm->M_halo[q], Mu[q], n, px, fp32, ch, 3, true)) ||
+        (st = encode_map(err, &fm->M_ctr[q], Mu[q], n, px, fp32, ch, 3, false)))
+      return st;
+  if ((st = encode_map(err, &fm->S, coef, n, px, fp32, ch, 1, true))) return st;
+  return encode_map(err, &fm->Q, coef, n, px, fp32, ch, 2, false);
 }
 
 // Explicit P1 mesh of the FEM cube for the element-by-element path: the six
@@ -653,13 +705,18 @@ int build_ebe(ddfd_problem *p) {
 }
 
 int build_maps(ddfd_problem *p) {
-  int st;
-  for (int q = 0; q < 2; ++q)
-    if ((st = encode_map(p, &p->mE_halo[q], p->E[q], 3, true)) || (st = encode_map(p, &p->mE_ctr[q], p->E[q], 3, false)) ||
-        (st = encode_map(p, &p->mM_halo[q], p->Mu[q], 3, true)) || (st = encode_map(p, &p->mM_ctr[q], p->Mu[q], 3, false)))
-      return st;
-  if ((st = encode_map(p, &p->mS, p->kcoef, 1, true))) return st;
-  return encode_map(p, &p->mQ, (char *)p->kcoef + (size_t)p->cs * p->esz, 2, false);
+  FieldMaps fm;
+  const int st = encode_field_maps(&p->err, &fm, p->E, p->Mu, p->kcoef, p->n, p->px, p->fp32, 1);
+  if (st) return st;
+  for (int q = 0; q < 2; ++q) {
+    p->mE_halo[q] = fm.E_halo[q];
+    p->mE_ctr[q] = fm.E_ctr[q];
+    p->mM_halo[q] = fm.M_halo[q];
+    p->mM_ctr[q] = fm.M_ctr[q];
+  }
+  p->mS = fm.S;
+  p->mQ = fm.Q;
+  return DDFD_OK;
 }
 
 int check_err(ddfd_problem *p) {
@@ -821,7 +878,28 @@ void ddfd_config_default(ddfd_config *c) {
 
 const char *ddfd_create_error(void) { return g_create_err.c_str(); }
 
-int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
+}  // extern "C"
+
+namespace {
+// Stacked field storage of a batch member: slot of E[0], E[1], Mu[0], Mu[1]
+// and the coefficient field.
+struct MemberSlot {
+  void *E[2], *Mu[2], *kcoef;
+  ddfd_batch *batch;
+  int slot;
+};
+
+int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **out);
+}  // namespace
+
+extern "C" {
+
+int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) { return create_impl(cfg, nullptr, out); }
+
+}  // extern "C"
+
+namespace {
+int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **out) {
   g_create_err.clear();
   if (!cfg || !out) {
     g_create_err = "NULL argument";
@@ -868,7 +946,7 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
 
   auto bail = [&](int code) {
     g_create_err = p->err;
-    ddfd_destroy(p);
+    destroy_problem(p);
     return code;
   };
   for (int q = 0; q < 4; ++q)
@@ -900,10 +978,20 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   }
   const size_t histn = p->nsnap ? (size_t)(p->seg + 1) * 3 * p->n_free
                                 : (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
-  if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
-      (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
-      (st = dalloc(p, 3 * (size_t)p->cs * p->esz, &p->kcoef)) || (st = dalloc_t(p, 1, &p->errflag)) ||
-
+  if (ext) {
+    for (int q = 0; q < 2; ++q) {
+      p->E[q] = ext->E[q];
+      p->Mu[q] = ext->Mu[q];
+    }
+    p->kcoef = ext->kcoef;
+    p->batch = ext->batch;
+    p->slot = ext->slot;
+  } else if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
+             (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
+             (st = dalloc(p, 3 * (size_t)p->cs * p->esz, &p->kcoef))) {
+    return bail(st);
+  }
+  if ((st = dalloc_t(p, 1, &p->errflag)) ||
       (st = dalloc(p, histn * p->esz, &p->hist)) || (st = dalloc_t(p, trn, &p->trace)) ||
       (st = dalloc_t(p, trn, &p->res)) || (st = dalloc_t(p, trn, &p->eobs_stage)) ||
       (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gacc)) || (st = dalloc_t(p, 4 * (size_t)p->n_free, &p->coef)) ||
@@ -976,9 +1064,19 @@ int ddfd_create(const ddfd_config *cfg, ddfd_problem **out) {
   *out = p;
   return DDFD_OK;
 }
+}  // namespace
+
+extern "C" {
 
 void ddfd_destroy(ddfd_problem *p) {
-  if (!p) return;
+  if (!p || p->batch) return;  // batch members go with their batch
+  destroy_problem(p);
+}
+
+}  // extern "C"
+
+namespace {
+void destroy_problem(ddfd_problem *p) {
   if (p->stream) cudaStreamSynchronize(p->stream);
   else cudaDeviceSynchronize();
   for (void *v : p->allocs) cudaFree(v);
@@ -988,6 +1086,9 @@ void ddfd_destroy(ddfd_problem *p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
+}  // namespace
+
+extern "C" {
 
 const char *ddfd_last_error(const ddfd_problem *p) { return p ? p->err.c_str() : "NULL handle"; }
 
@@ -1122,6 +1223,619 @@ int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out) {
     for (long long kj = 0; kj < (long long)n * n; ++kj)
       for (int i = 0; i < n; ++i)
         out[(size_t)c * p->nn + kj * n + i] = tmp[(size_t)c * p->cs + kj * p->px + i];
+  return DDFD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Tile autotuner and batched problems
+// ---------------------------------------------------------------------------
+
+struct ddfd_batch {
+  std::vector<ddfd_problem *> m;
+  std::string err;
+  int n = 0, Nt = 0, px = 0, fp32 = 0, kz = 16, seg = 0;
+  long long cs = 0;
+  size_t esz = 8;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr}, *kcoef = nullptr;
+  std::vector<void *> allocs;
+  int64_t bytes = 0, launches = 0;
+  FieldMaps maps;
+  int *errflag = nullptr;
+  cudaGraphExec_t gfwd = nullptr, gadj = nullptr;
+  int64_t gfwd_launches = 0, gadj_launches = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double fwd_ms = 0.0, adj_ms = 0.0;
+  int64_t fwd_kernels = 0, adj_kernels = 0;
+};
+
+namespace {
+
+int bfail(ddfd_batch *b, int code, const std::string &m) {
+  b->err = m;
+  return code;
+}
+
+#define BCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return bfail(b, DDFD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+  } while (0)
+
+const int kTileKz[] = {4, 6, 8, 12, 16, 24, 32};
+
+// Runs trial(kz, &ms) for every candidate z depth (after one untimed warm-up
+// trial) and returns the fastest in *best.
+template <typename Trial>
+int autotune_kz(int n, Trial trial, int *best) {
+  int st;
+  float ms = 0.0f;
+  if ((st = trial(kTileKz[0] <= n ? kTileKz[0] : n, &ms))) return st;
+  float best_ms = 3.4e38f;
+  *best = 0;
+  for (int kz : kTileKz) {
+    if (kz > n) break;
+    if ((st = trial(kz, &ms))) return st;
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = kz;
+    }
+  }
+  return DDFD_OK;
+}
+
+// E^n on the free nodes for trial step st (any valid slot of the history).
+long long trial_hist_index(const ddfd_problem *p, int st) {
+  return p->nsnap ? (long long)(st % p->seg) + 1 : (long long)st + 1;
+}
+
+template <typename T>
+int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
+  const size_t fbytes = 3 * (size_t)p->cs * sizeof(T);
+  const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
+  cudaStream_t sm = p->stream;
+  p->kz = kz;
+  for (int q = 0; q < 2; ++q) {
+    CK(cudaMemsetAsync(p->E[q], 0, fbytes, sm));
+    CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, sm));
+  }
+  if (trn) CK(cudaMemsetAsync(p->res, 0, trn * sizeof(double), sm));
+  CK(cudaEventRecord(p->ev[0], sm));
+  int64_t nk = 0;
+  StepParams<T> P = base_params<T>(p);
+  set_source(P, p, 0);
+  int ic = 1, io = 0;
+  for (int st = 0; st < steps; ++st) {
+    set_forward_step(P, p, 0, st, p->E[ic], p->E[io], (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
+    enqueue_ebe<T>(p, p->E[ic], false, sm, &nk);
+    launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
+    std::swap(ic, io);
+  }
+  ic = 1, io = 0;
+  for (int k = steps; k >= 1; --k) {
+    set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free);
+    enqueue_ebe<T>(p, p->Mu[ic], true, sm, &nk);
+    launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
+    std::swap(ic, io);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(p->ev[1], sm));
+  CK(cudaEventSynchronize(p->ev[1]));
+  CK(cudaEventElapsedTime(ms, p->ev[0], p->ev[1]));
+  p->launches += 2 * steps + nk;
+  return DDFD_OK;
+}
+
+// One batched step launch per group of BATCH_MAX members; fill(P, p) sets the
+// per-step scalars of member p.
+template <typename T, typename Fill>
+void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const CUtensorMap &cur,
+                   const CUtensorMap &old, Fill fill, cudaStream_t sm, int64_t *nk) {
+  for (size_t g0 = 0; g0 < idx.size(); g0 += BATCH_MAX) {
+    StepLaunch<T, BATCH_MAX> L;
+    std::memset(&L, 0, sizeof(L));
+    L.cur = cur;
+    L.old = old;
+    L.s = b->maps.S;
+    L.q = b->maps.Q;
+    L.nprob = (int)std::min<size_t>(BATCH_MAX, idx.size() - g0);
+    L.zchunks = (b->n + b->kz - 1) / b->kz;
+    for (int g = 0; g < L.nprob; ++g) {
+      ddfd_problem *p = b->m[idx[g0 + g]];
+      StepParams<T> P = base_params<T>(p);
+      set_source(P, p, 0);
+      P.kz = b->kz;
+      P.chan = 3 * p->slot;
+      P.err = b->errflag;
+      fill(P, p);
+      L.p[g] = P;
+    }
+    if (adj)
+      launch_adjoint_step(L, sm);
+    else
+      launch_forward_step(L, sm);
+    ++*nk;
+  }
+}
+
+std::vector<int> all_members(const ddfd_batch *b) {
+  std::vector<int> v(b->m.size());
+  for (size_t i = 0; i < v.size(); ++i) v[i] = (int)i;
+  return v;
+}
+
+template <typename T>
+int enqueue_batch_forward(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
+  const size_t fbytes = 3 * (size_t)b->cs * sizeof(T);
+  const size_t slab = fbytes * b->m.size();
+  const int Nt = b->Nt;
+  *nk = 0;
+  BCK(cudaMemsetAsync(b->E[0], 0, slab, sm));
+  BCK(cudaMemsetAsync(b->E[1], 0, slab, sm));
+  const std::vector<int> all = all_members(b);
+  int ic = 1, io = 0;
+  for (int st = 0; st < Nt; ++st) {
+    for (ddfd_problem *p : b->m)
+      if (p->nsnap && st % p->seg == 0) {
+        char *sn = (char *)p->snap + (size_t)(st / p->seg) * 2 * fbytes;
+        BCK(cudaMemcpyAsync(sn, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
+        BCK(cudaMemcpyAsync(sn + fbytes, p->E[io], fbytes, cudaMemcpyDeviceToDevice, sm));
+      }
+    launch_groups<T>(
+        b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io],
+        [&](StepParams<T> &P, ddfd_problem *p) {
+          set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
+                           p->nsnap ? nullptr : (T *)p->hist + (size_t)(st + 1) * 3 * p->n_free);
+        },
+        sm, nk);
+    std::swap(ic, io);
+  }
+  BCK(cudaGetLastError());
+  for (ddfd_problem *p : b->m) {
+    launch_gather_trace(p->E[ic], p->fp32, p->cs, p->n_det, p->det_node, p->trace + (size_t)Nt * p->n_det * 3, sm);
+    if (p->n_det > 0) ++*nk;
+  }
+  BCK(cudaGetLastError());
+  return DDFD_OK;
+}
+
+template <typename T>
+int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
+  const size_t fbytes = 3 * (size_t)b->cs * sizeof(T);
+  const size_t slab = fbytes * b->m.size();
+  const int Nt = b->Nt;
+  *nk = 0;
+  for (ddfd_problem *p : b->m) BCK(cudaMemsetAsync(p->gacc, 0, 2 * (size_t)p->n_free * sizeof(double), sm));
+  BCK(cudaMemsetAsync(b->Mu[0], 0, slab, sm));
+  BCK(cudaMemsetAsync(b->Mu[1], 0, slab, sm));
+  const std::vector<int> all = all_members(b);
+  std::vector<int> ck;  // checkpointing members: replayed segment by segment
+  for (size_t i = 0; i < b->m.size(); ++i)
+    if (b->m[i]->nsnap) ck.push_back((int)i);
+  const int seg = b->seg;
+  const int nseg = seg ? (Nt + seg - 1) / seg : 1;
+  int ic = 1, io = 0;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int n0 = seg ? j * seg : 0;
+    const int n1 = seg ? std::min(n0 + seg, Nt) : Nt;
+    if (!ck.empty()) {
+      for (int i : ck) {
+        ddfd_problem *p = b->m[i];
+        const char *sn = (const char *)p->snap + (size_t)j * 2 * fbytes;
+        BCK(cudaMemcpyAsync(p->E[1], sn, fbytes, cudaMemcpyDeviceToDevice, sm));
+        BCK(cudaMemcpyAsync(p->E[0], sn + fbytes, fbytes, cudaMemcpyDeviceToDevice, sm));
+      }
+      int fc = 1, fo = 0;
+      for (int st = n0; st < n1; ++st) {
+        launch_groups<T>(
+            b, false, ck, b->maps.E_halo[fc], b->maps.E_ctr[fo],
+            [&](StepParams<T> &P, ddfd_problem *p) {
+              set_forward_step(P, p, 0, st, p->E[fc], p->E[fo], (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free);
+            },
+            sm, nk);
+        std::swap(fc, fo);
+      }
+    }
+    for (int k = n1; k >= n0 + 1; --k) {
+      launch_groups<T>(
+          b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io],
+          [&](StepParams<T> &P, ddfd_problem *p) {
+            const long long hk = p->nsnap ? k - n0 : k;
+            set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free);
+          },
+          sm, nk);
+      std::swap(ic, io);
+    }
+  }
+  BCK(cudaGetLastError());
+  return DDFD_OK;
+}
+
+void drop_batch_graphs(ddfd_batch *b) {
+  if (b->gfwd) cudaGraphExecDestroy(b->gfwd);
+  if (b->gadj) cudaGraphExecDestroy(b->gadj);
+  b->gfwd = b->gadj = nullptr;
+}
+
+int run_batch_sequence(ddfd_batch *b, bool adj) {
+  cudaGraphExec_t *ge = adj ? &b->gadj : &b->gfwd;
+  int64_t *gl = adj ? &b->gadj_launches : &b->gfwd_launches;
+  if (!*ge) {
+    BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
+    int64_t nk = 0;
+    int st;
+    if (adj)
+      st = b->fp32 ? enqueue_batch_adjoint<float>(b, b->cap_stream, &nk)
+                   : enqueue_batch_adjoint<double>(b, b->cap_stream, &nk);
+    else
+      st = b->fp32 ? enqueue_batch_forward<float>(b, b->cap_stream, &nk)
+                   : enqueue_batch_forward<double>(b, b->cap_stream, &nk);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &g);
+    if (st) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    BCK(ec);
+    const cudaError_t ei = cudaGraphInstantiate(ge, g, 0);
+    cudaGraphDestroy(g);
+    BCK(ei);
+    *gl = nk;
+  }
+  cudaEvent_t e0 = b->ev[adj ? 2 : 0], e1 = b->ev[adj ? 3 : 1];
+  BCK(cudaEventRecord(e0, b->stream));
+  BCK(cudaGraphLaunch(*ge, b->stream));
+  BCK(cudaEventRecord(e1, b->stream));
+  BCK(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  BCK(cudaEventElapsedTime(&ms, e0, e1));
+  b->launches += *gl;
+  const int64_t groups = ((int64_t)b->m.size() + BATCH_MAX - 1) / BATCH_MAX;
+  if (adj) {
+    b->adj_ms = ms;
+    int64_t ckg = 0;
+    for (ddfd_problem *p : b->m) ckg += p->nsnap ? 1 : 0;
+    ckg = (ckg + BATCH_MAX - 1) / BATCH_MAX;
+    b->adj_kernels = (int64_t)b->Nt * (groups + ckg);
+    for (ddfd_problem *p : b->m)
+      if (p->nsnap) p->fwd_steps += b->Nt;
+  } else {
+    b->fwd_ms = ms;
+    b->fwd_kernels = (int64_t)b->Nt * groups;
+    for (ddfd_problem *p : b->m) p->fwd_steps += b->Nt;
+  }
+  return DDFD_OK;
+}
+
+int batch_check_err(ddfd_batch *b) {
+  int e = 0;
+  BCK(cudaMemcpyAsync(&e, b->errflag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (e) {
+    BCK(cudaMemsetAsync(b->errflag, 0, sizeof(int), b->stream));
+    return bfail(b, DDFD_E_TIMEOUT, "a step kernel gave up a bounded wait on its TMA pipeline");
+  }
+  return DDFD_OK;
+}
+
+template <typename T>
+int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
+  const size_t fbytes = 3 * (size_t)b->cs * sizeof(T);
+  const size_t slab = fbytes * b->m.size();
+  cudaStream_t sm = b->stream;
+  b->kz = kz;
+  for (int q = 0; q < 2; ++q) {
+    BCK(cudaMemsetAsync(b->E[q], 0, slab, sm));
+    BCK(cudaMemsetAsync(b->Mu[q], 0, slab, sm));
+  }
+  for (ddfd_problem *p : b->m) {
+    const size_t trn = (size_t)(p->Nt + 1) * p->n_det * 3;
+    if (trn) BCK(cudaMemsetAsync(p->res, 0, trn * sizeof(double), sm));
+  }
+  const std::vector<int> all = all_members(b);
+  int64_t nk = 0;
+  BCK(cudaEventRecord(b->ev[0], sm));
+  int ic = 1, io = 0;
+  for (int st = 0; st < steps; ++st) {
+    launch_groups<T>(
+        b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io],
+        [&](StepParams<T> &P, ddfd_problem *p) {
+          set_forward_step(P, p, 0, st, p->E[ic], p->E[io], (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
+        },
+        sm, &nk);
+    std::swap(ic, io);
+  }
+  ic = 1, io = 0;
+  for (int k = steps; k >= 1; --k) {
+    launch_groups<T>(
+        b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io],
+        [&](StepParams<T> &P, ddfd_problem *p) {
+          set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io],
+                           (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free);
+        },
+        sm, &nk);
+    std::swap(ic, io);
+  }
+  BCK(cudaGetLastError());
+  BCK(cudaEventRecord(b->ev[1], sm));
+  BCK(cudaEventSynchronize(b->ev[1]));
+  BCK(cudaEventElapsedTime(ms, b->ev[0], b->ev[1]));
+  b->launches += nk;
+  return DDFD_OK;
+}
+
+int batch_forward_impl(ddfd_batch *b, double *const *trace_out, cudaMemcpyKind kind) {
+  int st = run_batch_sequence(b, false);
+  if (st) return st;
+  if ((st = batch_check_err(b))) return st;
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    ddfd_problem *p = b->m[i];
+    const long long cnt = (long long)(p->Nt + 1) * p->n_det * 3;
+    BCK(cudaMemsetAsync(p->flag, 0, sizeof(int), b->stream));
+    if (cnt > 0) {
+      launch_nonfinite(p->trace, cnt, p->flag, b->stream);
+      ++b->launches;
+    }
+    int flag = 0;
+    BCK(cudaMemcpyAsync(&flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    p->state = ST_FORWARD;
+    if (flag) return bfail(b, DDFD_E_NONFINITE, "non-finite value in the forward trace of member " + std::to_string(i));
+    if (trace_out && trace_out[i] && cnt > 0)
+      BCK(cudaMemcpyAsync(trace_out[i], p->trace, cnt * sizeof(double), kind, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  return DDFD_OK;
+}
+
+int batch_adjoint_impl(ddfd_batch *b, const double *const *eobs, bool host) {
+  for (size_t i = 0; i < b->m.size(); ++i)
+    if (b->m[i]->state < ST_FORWARD)
+      return bfail(b, DDFD_E_STATE, "member " + std::to_string(i) + " has no forward run");
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    ddfd_problem *p = b->m[i];
+    const long long cnt = (long long)(p->Nt + 1) * p->n_det * 3;
+    if (cnt > 0 && (!eobs || !eobs[i])) return bfail(b, DDFD_E_ARG, "eobs of member " + std::to_string(i) + " is missing");
+    const double *e = cnt > 0 ? eobs[i] : nullptr;
+    if (host && cnt > 0) {
+      BCK(cudaMemcpyAsync(p->eobs_stage, e, cnt * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+      e = p->eobs_stage;
+    }
+    launch_residual(p->trace, e, p->z, p->Nt, p->n_det, 1, p->tau, p->res, p->part, p->n_part, b->stream);
+    ++b->launches;
+  }
+  int st = run_batch_sequence(b, true);
+  if (st) return st;
+  if ((st = batch_check_err(b))) return st;
+  BCK(cudaStreamSynchronize(b->stream));
+  for (ddfd_problem *p : b->m) p->state = ST_ADJOINT;
+  return DDFD_OK;
+}
+
+void destroy_batch(ddfd_batch *b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  for (ddfd_problem *p : b->m) destroy_problem(p);
+  for (void *v : b->allocs) cudaFree(v);
+  for (int q = 0; q < 4; ++q)
+    if (b->ev[q]) cudaEventDestroy(b->ev[q]);
+  drop_batch_graphs(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  if (steps < 1 || steps > p->Nt) return fail(p, DDFD_E_ARG, "steps must be in [1, n_steps]");
+  int best = 0;
+  int st = autotune_kz(
+      p->n,
+      [&](int kz, float *ms) { return p->fp32 ? single_trial<float>(p, steps, kz, ms) : single_trial<double>(p, steps, kz, ms); },
+      &best);
+  if (!st && (st = check_err(p))) best = 0;
+  p->kz = best ? best : p->kz;
+  p->state = ST_READY;
+  drop_graphs(p);
+  const size_t fbytes = 3 * (size_t)p->cs * p->esz;
+  for (int q = 0; q < 2; ++q) {
+    CK(cudaMemsetAsync(p->E[q], 0, fbytes, p->stream));
+    CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, p->stream));
+  }
+  if (st) return st;
+  if (tile_kz_out) *tile_kz_out = p->kz;
+  return sync_check(p);
+}
+
+int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) {
+  g_create_err.clear();
+  if (!cfgs || !out || count < 1 || count > 256) {
+    g_create_err = "need 1..256 configurations and an output pointer";
+    return DDFD_E_ARG;
+  }
+  int seg = 0;
+  for (int i = 0; i < count; ++i) {
+    const ddfd_config &c = cfgs[i];
+    std::string m;
+    int st = validate(&c, &m);
+    if (st) {
+      g_create_err = "member " + std::to_string(i) + ": " + m;
+      return st;
+    }
+    if (c.n != cfgs[0].n || c.n_steps != cfgs[0].n_steps || c.cfl != cfgs[0].cfl ||
+        c.precision != cfgs[0].precision) {
+      g_create_err = "member " + std::to_string(i) + ": n, n_steps, cfl and precision must match member 0";
+      return DDFD_E_ARG;
+    }
+    if (c.n_src != 1 || c.fem_kind != DDFD_FEM_STENCIL) {
+      g_create_err = "member " + std::to_string(i) + ": batch members take one source and the stencil FEM apply";
+      return DDFD_E_ARG;
+    }
+    if (c.n_snapshots > 0) {
+      const int sg = (c.n_steps + c.n_snapshots - 1) / c.n_snapshots;
+      if (seg && sg != seg) {
+        g_create_err = "member " + std::to_string(i) + ": checkpointing members must share the segment length";
+        return DDFD_E_ARG;
+      }
+      seg = sg;
+    }
+  }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    g_create_err = std::string("no usable CUDA device: ") + cudaGetErrorString(ce);
+    return DDFD_E_CUDA;
+  }
+  ddfd_batch *b = new ddfd_batch();
+  b->n = cfgs[0].n;
+  b->Nt = cfgs[0].n_steps;
+  b->px = (b->n + 7) / 8 * 8;
+  b->cs = (long long)b->px * b->n * b->n;
+  b->fp32 = cfgs[0].precision == DDFD_FP32;
+  b->esz = b->fp32 ? 4 : 8;
+  b->seg = seg;
+  b->stream = (cudaStream_t)cfgs[0].stream;
+  b->kz = cfgs[0].tile_kz ? cfgs[0].tile_kz : (b->n >= 128 ? 16 : 8);
+  auto bail = [&](int code, const std::string &m) {
+    g_create_err = m;
+    destroy_batch(b);
+    return code;
+  };
+  for (int q = 0; q < 4; ++q)
+    if (cudaEventCreate(&b->ev[q]) != cudaSuccess) return bail(DDFD_E_CUDA, "cudaEventCreate failed");
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(DDFD_E_CUDA, "stream creation failed");
+  const size_t slab = 3 * (size_t)b->cs * b->esz * count;
+  void **bufs[5] = {&b->E[0], &b->E[1], &b->Mu[0], &b->Mu[1], &b->kcoef};
+  for (void **v : bufs) {
+    if (cudaMalloc(v, slab) != cudaSuccess) {
+      cudaGetLastError();
+      *v = nullptr;
+      return bail(DDFD_E_OOM, "cudaMalloc of a " + std::to_string(slab) + "-byte field slab failed");
+    }
+    b->allocs.push_back(*v);
+    b->bytes += (int64_t)slab;
+  }
+  if (cudaMalloc((void **)&b->errflag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(DDFD_E_OOM, "cudaMalloc of the error flag failed");
+  }
+  b->allocs.push_back(b->errflag);
+  if (cudaMemset(b->errflag, 0, sizeof(int)) != cudaSuccess) return bail(DDFD_E_CUDA, "memset failed");
+  std::string m;
+  if (encode_field_maps(&m, &b->maps, b->E, b->Mu, b->kcoef, b->n, b->px, b->fp32, count))
+    return bail(DDFD_E_CUDA, m);
+  const size_t fb = 3 * (size_t)b->cs * b->esz;
+  for (int i = 0; i < count; ++i) {
+    ddfd_config c = cfgs[i];
+    c.stream = cfgs[0].stream;
+    c.tile_kz = b->kz;
+    MemberSlot ms;
+    for (int q = 0; q < 2; ++q) {
+      ms.E[q] = (char *)b->E[q] + i * fb;
+      ms.Mu[q] = (char *)b->Mu[q] + i * fb;
+    }
+    ms.kcoef = (char *)b->kcoef + i * fb;
+    ms.batch = b;
+    ms.slot = i;
+    ddfd_problem *p = nullptr;
+    const int st = create_impl(&c, &ms, &p);
+    if (st) return bail(st, "member " + std::to_string(i) + ": " + g_create_err);
+    b->m.push_back(p);
+  }
+  *out = b;
+  return DDFD_OK;
+}
+
+void ddfd_destroy_batch(ddfd_batch *b) {
+  if (b) destroy_batch(b);
+}
+
+const char *ddfd_batch_last_error(const ddfd_batch *b) { return b ? b->err.c_str() : "NULL handle"; }
+
+int ddfd_batch_member(ddfd_batch *b, int32_t i, ddfd_problem **out) {
+  if (!b || !out) return DDFD_E_ARG;
+  b->err.clear();
+  if (i < 0 || i >= (int)b->m.size()) return bfail(b, DDFD_E_ARG, "member index out of range");
+  *out = b->m[i];
+  return DDFD_OK;
+}
+
+int ddfd_batch_forward(ddfd_batch *b, double *const *trace_out) {
+  if (!b) return DDFD_E_ARG;
+  b->err.clear();
+  return batch_forward_impl(b, trace_out, cudaMemcpyDeviceToHost);
+}
+
+int ddfd_batch_forward_dev(ddfd_batch *b, double *const *trace_out) {
+  if (!b) return DDFD_E_ARG;
+  b->err.clear();
+  return batch_forward_impl(b, trace_out, cudaMemcpyDeviceToDevice);
+}
+
+int ddfd_batch_adjoint(ddfd_batch *b, const double *const *eobs) {
+  if (!b) return DDFD_E_ARG;
+  b->err.clear();
+  return batch_adjoint_impl(b, eobs, true);
+}
+
+int ddfd_batch_adjoint_dev(ddfd_batch *b, const double *const *eobs) {
+  if (!b) return DDFD_E_ARG;
+  b->err.clear();
+  return batch_adjoint_impl(b, eobs, false);
+}
+
+int ddfd_batch_autotune(ddfd_batch *b, int32_t steps, int32_t *tile_kz_out) {
+  if (!b) return DDFD_E_ARG;
+  b->err.clear();
+  if (steps < 1 || steps > b->Nt) return bfail(b, DDFD_E_ARG, "steps must be in [1, n_steps]");
+  int best = 0;
+  int st = autotune_kz(
+      b->n,
+      [&](int kz, float *ms) { return b->fp32 ? batch_trial<float>(b, steps, kz, ms) : batch_trial<double>(b, steps, kz, ms); },
+      &best);
+  if (!st && (st = batch_check_err(b))) best = 0;
+  b->kz = best ? best : b->kz;
+  drop_batch_graphs(b);
+  for (ddfd_problem *p : b->m) {
+    p->kz = b->kz;
+    p->state = ST_READY;
+    drop_graphs(p);
+  }
+  const size_t slab = 3 * (size_t)b->cs * b->esz * b->m.size();
+  for (int q = 0; q < 2; ++q) {
+    BCK(cudaMemsetAsync(b->E[q], 0, slab, b->stream));
+    BCK(cudaMemsetAsync(b->Mu[q], 0, slab, b->stream));
+  }
+  if (st) return st;
+  if (tile_kz_out) *tile_kz_out = b->kz;
+  BCK(cudaStreamSynchronize(b->stream));
+  return DDFD_OK;
+}
+
+int ddfd_batch_get_info(const ddfd_batch *b, ddfd_batch_info *info) {
+  if (!b || !info) return DDFD_E_ARG;
+  info->count = (int32_t)b->m.size();
+  info->tile_kz = b->kz;
+  info->forward_loop_ms = b->fwd_ms;
+  info->adjoint_loop_ms = b->adj_ms;
+  info->forward_step_kernels = b->fwd_kernels;
+  info->adjoint_step_kernels = b->adj_kernels;
+  int64_t l = b->launches, bytes = b->bytes;
+  for (const ddfd_problem *p : b->m) {
+    l += p->launches;
+    bytes += p->bytes;
+  }
+  info->kernel_launches = l;
+  info->device_bytes = bytes;
   return DDFD_OK;
 }
 

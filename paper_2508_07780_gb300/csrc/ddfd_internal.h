@@ -92,22 +92,32 @@ struct StepParams {
   int ebe_rows;
   int *err;              // bit 4: a bounded mbarrier wait gave up
   uint32_t spin_limit;   // polls per bounded wait
+  int chan;              // first channel of this problem in the launch's tensor maps:
+                         // fields at chan..chan+2, coefficients (s, q1, q2) likewise
 };
 
-// TMA descriptors of one launch: current level (halo box), previous level
-// (centre box), s (halo box) and (q1, q2) (centre box) of the coefficients.
-struct StepMaps {
-  const CUtensorMap *cur, *old, *s, *q;
+// One step launch over NB_MAX problems at most, all with the same grid size
+// and z chunking: the TMA descriptors span the stacked fields (channel axis
+// 3 x problems) of the current level (halo box), the previous level (centre
+// box), s (halo box, one channel) and (q1, q2) (centre box, two channels);
+// CTA z index = z chunk + zchunks x problem.
+constexpr int BATCH_MAX = 16;
+template <typename T, int NB>
+struct StepLaunch {
+  CUtensorMap cur, old, s, q;
+  int nprob;
+  int zchunks;
+  StepParams<T> p[NB];
 };
 
 // Sets the dynamic shared-memory limit of every step-kernel instance (once,
 // before any launch or capture).
 cudaError_t prepare_step_kernels();
 
-template <typename T>
-void launch_forward_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
-template <typename T>
-void launch_adjoint_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s);
+template <typename T, int NB>
+void launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s);
+template <typename T, int NB>
+void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s);
 
 // Element-by-element FEM apply over an explicit tetrahedral mesh.
 template <typename T>

@@ -140,12 +140,15 @@ struct Stage {
 constexpr int STEP_CONSUMERS = 256;
 constexpr int STEP_THREADS = STEP_CONSUMERS + 32;
 
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, int NB>
 __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
-    k_step(const __grid_constant__ CUtensorMap mcur, const __grid_constant__ CUtensorMap mold,
-           const __grid_constant__ CUtensorMap ms, const __grid_constant__ CUtensorMap mq,
-           const StepParams<T> P) {
+    k_step(const __grid_constant__ StepLaunch<T, NB> L) {
   using S = Stage<T>;
+  // problem of this CTA (uniform) and its z chunk
+  const int prob = NB == 1 ? 0 : (int)blockIdx.z / L.zchunks;
+  const int zc = NB == 1 ? (int)blockIdx.z : (int)blockIdx.z - prob * L.zchunks;
+  const int zchunks = NB == 1 ? (int)gridDim.z : L.zchunks;
+  const StepParams<T> &P = L.p[prob];
   constexpr int RE = S::ROWS * S::BXW;  // component stride of a staged plane
   constexpr int BW = S::BXW;
   extern __shared__ unsigned char smem_raw[];
@@ -156,8 +159,8 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   const int tid = threadIdx.x;
 
   if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
-    const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z * blockDim.x;
-    long long t = ((long long)blockIdx.x + gridDim.x * ((long long)blockIdx.y + gridDim.y * blockIdx.z)) *
+    const long long nb = (long long)gridDim.x * gridDim.y * zchunks * blockDim.x;
+    long long t = ((long long)blockIdx.x + gridDim.x * ((long long)blockIdx.y + gridDim.y * zc)) *
                       blockDim.x + tid;
     for (; t < 3LL * P.n_det; t += nb) {
       const int d = (int)(t / 3), c = (int)(t - 3LL * d);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   // one CTA per (tile, z chunk): planes k0-1 .. k1 are staged, plane index
   // p = kk - (k0 - 1) in slot p % RING
   const int x0 = blockIdx.x * STEP_TX, y0 = blockIdx.y * S::TY;
-  const int k0 = blockIdx.z * P.kz;
+  const int k0 = zc * P.kz;
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
   const int nplanes = k1 - k0 + 2;
@@ -182,10 +185,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
       mbar_init(&emp[s], STEP_CONSUMERS / 32);
     }
     mbar_fence_init();
-    tma_prefetch_desc(&mcur);
-    tma_prefetch_desc(&mold);
-    tma_prefetch_desc(&ms);
-    tma_prefetch_desc(&mq);
+    tma_prefetch_desc(&L.cur);
+    tma_prefetch_desc(&L.old);
+    tma_prefetch_desc(&L.s);
+    tma_prefetch_desc(&L.q);
   }
   __syncthreads();
 
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
     if (tid != STEP_CONSUMERS) return;
     int p = 0;
     bool ok = true;
+    const int ch = P.chan;
     for (; p < nplanes; ++p) {
       const int slot = p % S::RING;
       // plane p reuses the slot of plane p - RING, whose release is completion
@@ -213,10 +217,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
                              (qc ? S::Q_BYTES : 0);
       uint64_t *bb = &bar[slot];
       mbar_expect_tx(bb, bytes);
-      tma_load_4d(st + S::E_OFF, &mcur, x0 - S::HX, y0 - 1, ksrc, 0, bb);
-      if (interior) tma_load_4d(st + S::O_OFF, &mold, x0, y0, kk, 0, bb);
-      if (coef) tma_load_4d(st + S::S_OFF, &ms, x0 - S::HX, y0 - 1, kk, 0, bb);
-      if (qc) tma_load_4d(st + S::Q_OFF, &mq, x0, y0, kk, 0, bb);
+      tma_load_4d(st + S::E_OFF, &L.cur, x0 - S::HX, y0 - 1, ksrc, ch, bb);
+      if (interior) tma_load_4d(st + S::O_OFF, &L.old, x0, y0, kk, ch, bb);
+      if (coef) tma_load_4d(st + S::S_OFF, &L.s, x0 - S::HX, y0 - 1, kk, ch, bb);
+      if (qc) tma_load_4d(st + S::Q_OFF, &L.q, x0, y0, kk, ch + 1, bb);
     }
     if (!ok) atomicOr(P.err, 4);
     // every issued plane must land before the CTA can retire (bounded)
@@ -449,40 +453,48 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   }
 }
 
+template <typename T, bool ADJ, int NB>
+static cudaError_t set_smem() {
+  return cudaFuncSetAttribute(k_step<T, ADJ, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<T>::SMEM);
+}
+
 cudaError_t prepare_step_kernels() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_step<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Stage<float>::SMEM)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_step<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Stage<float>::SMEM)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_step<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Stage<double>::SMEM)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_step<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Stage<double>::SMEM)) != cudaSuccess)
+  if ((e = set_smem<float, false, 1>()) != cudaSuccess || (e = set_smem<float, true, 1>()) != cudaSuccess ||
+      (e = set_smem<double, false, 1>()) != cudaSuccess || (e = set_smem<double, true, 1>()) != cudaSuccess ||
+      (e = set_smem<float, false, BATCH_MAX>()) != cudaSuccess ||
+      (e = set_smem<float, true, BATCH_MAX>()) != cudaSuccess ||
+      (e = set_smem<double, false, BATCH_MAX>()) != cudaSuccess ||
+      (e = set_smem<double, true, BATCH_MAX>()) != cudaSuccess)
     return e;
   return cudaSuccess;
 }
 
-template <typename T, bool ADJ>
-static void launch_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
+template <typename T, bool ADJ, int NB>
+static void launch_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
   const int ty = Stage<T>::TY;
-  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, (P.n + P.kz - 1) / P.kz);
-  k_step<T, ADJ><<<grid, STEP_THREADS, Stage<T>::SMEM, s>>>(*m.cur, *m.old, *m.s, *m.q, P);
+  const StepParams<T> &P = L.p[0];
+  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
+  k_step<T, ADJ, NB><<<grid, STEP_THREADS, Stage<T>::SMEM, s>>>(L);
 }
 
-template <typename T>
-void launch_forward_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
-  launch_step<T, false>(m, P, s);
+template <typename T, int NB>
+void launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
+  launch_step<T, false, NB>(L, s);
 }
-template <typename T>
-void launch_adjoint_step(const StepMaps &m, const StepParams<T> &P, cudaStream_t s) {
-  launch_step<T, true>(m, P, s);
+template <typename T, int NB>
+void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
+  launch_step<T, true, NB>(L, s);
 }
 
-template void launch_forward_step<float>(const StepMaps &, const StepParams<float> &, cudaStream_t);
-template void launch_forward_step<double>(const StepMaps &, const StepParams<double> &, cudaStream_t);
-template void launch_adjoint_step<float>(const StepMaps &, const StepParams<float> &, cudaStream_t);
-template void launch_adjoint_step<double>(const StepMaps &, const StepParams<double> &, cudaStream_t);
+#define DDFD_STEP_INST(T, NB)                                                      \
+  template void launch_forward_step<T, NB>(const StepLaunch<T, NB> &, cudaStream_t); \
+  template void launch_adjoint_step<T, NB>(const StepLaunch<T, NB> &, cudaStream_t);
+DDFD_STEP_INST(float, 1)
+DDFD_STEP_INST(double, 1)
+DDFD_STEP_INST(float, BATCH_MAX)
+DDFD_STEP_INST(double, BATCH_MAX)
+#undef DDFD_STEP_INST
 
 // y = h^2 M_eps^-1 K x in FP64 on every node (no damping, no source): the
 // operator whose largest eigenvalue bounds the stable time step.  One thread

@@ -16,4 +16,5 @@ from .models import (  # noqa: F401
     shard_directions,
     workload,
     WORKLOADS,
+    batched_problems,
 )

@@ -64,3 +64,22 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(DDFDError) as e:
         Problem(n=13, fem_n=9, n_steps=4)
     assert e.value.code == -4
+
+
+@pytest.mark.parametrize("cfgs,what", [
+    ([dict(n=21, fem_n=11, n_steps=3), dict(n=25, fem_n=11, n_steps=3)], "must match member 0"),
+    ([dict(n=21, fem_n=11, n_steps=3), dict(n=21, fem_n=11, n_steps=4)], "must match member 0"),
+    ([dict(n=21, fem_n=11, n_steps=3, precision="fp32"), dict(n=21, fem_n=11, n_steps=3)],
+     "must match member 0"),
+    ([dict(n=21, fem_n=11, n_steps=3, src_dir=[[0, 0, -1.0], [0, 0.1, -1.0]])], "one source"),
+    ([dict(n=21, fem_n=11, n_steps=3, fem_kind=1)], "stencil FEM"),
+    ([dict(n=21, fem_n=11, n_steps=30, n_snapshots=3), dict(n=21, fem_n=9, n_steps=30, n_snapshots=5)],
+     "segment length"),
+    ([dict(n=21, fem_n=11, n_steps=3), dict(n=21, fem_n=30, n_steps=3)], "member 1: fem_n"),
+    ([], "1..256"),
+])
+def test_create_batch_rejects_mismatched_members(lib, cfgs, what):
+    from paper_2508_07780_gb300 import Batch, DDFDError
+    with pytest.raises(DDFDError) as e:
+        Batch(cfgs)
+    assert e.value.code == -1 and what in str(e.value), str(e.value)
