@@ -11,7 +11,10 @@ inputs; `e2e` is the same through the host-pointer entry points with the
 host<->device copies inside the timed region; `roofline` is the dominant
 step kernel's algorithmic bytes over its CUDA-event duration against the
 measured HBM copy bandwidth; `cpu_baseline` times the FP64 CPU oracle on a
-bounded sample of the same workload.
+bounded sample of the same workload; `fp64_plain` is one pass of the plain
+FP64 GPU path on the same workload; `batched` is the batched FP32 workload
+(16 problems of mixed FEM cube size on a 161^3 grid, one launch per time
+step) with its own throughput and roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -229,6 +232,92 @@ def fp64_plain(w, dev, stream):
     return w64.updates / (ms / 1e3), ms
 
 
+def batched_bytes(ws):
+    """Algorithmic bytes of one batched forward launch: the per-problem bytes
+    of algorithmic_bytes summed over the members."""
+    return sum(algorithmic_bytes(w)[0] for w in ws)
+
+
+def run_batched(args, dev, stream):
+    """The batched FP32 workload: 16 problems on a 161^3 grid, FEM cubes
+    61/81/101/121 (problem b mod 4), one hemisphere-drawn incidence
+    direction each, 1600 steps, 1024 detectors, stepped together (one launch
+    per time step, graph-captured), tile depth from the autotuner.  Members
+    with the 61^3 and 81^3 cubes keep the E history; the 101^3 and 121^3
+    ones checkpoint (32 snapshots) and are replayed in batched launches of
+    their own, so that the batch fits in about 85 GB."""
+    import torch
+    from paper_2508_07780_gb300 import Batch
+    from synth import batched_problems
+    probs = batched_problems()
+    cfgs = [dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp32",
+                 src_dir=d[None, :], det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
+                 n_snapshots=32 if w.fem_n > 81 else 0, stream=stream.cuda_stream)
+            for w, d in probs]
+    b = Batch(cfgs)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    for (w, _), m in zip(probs, b.members):
+        m.set_coeffs(*w.model(inclusions=False))
+    eobs = [torch.empty(m.trace_shape, dtype=torch.float64, device=dev) for m in b.members]
+    b.forward_dev(eobs)
+    coefs = [tuple(T(a) for a in w.model()) for w, _ in probs]
+    grads = [(torch.empty(m.n_free, dtype=torch.float64, device=dev),
+              torch.empty(m.n_free, dtype=torch.float64, device=dev)) for m in b.members]
+    kz = b.autotune(steps=8)
+
+    def step():
+        for m, (e, s) in zip(b.members, coefs):
+            m.set_coeffs_dev(e, s)
+        b.forward_dev(None)
+        J = sum(m.functional_dev(e) for m, e in zip(b.members, eobs))
+        b.adjoint_dev(eobs)
+        for m, (ge, gs) in zip(b.members, grads):
+            m.gradient_dev(ge, gs)
+        return J
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    l0 = b.get_info().kernel_launches
+    fwd_ms = adj_ms = 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        inf = b.get_info()
+        fwd_ms += inf.forward_loop_ms
+        adj_ms += inf.adjoint_loop_ms
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    inf = b.get_info()
+    launches = inf.kernel_launches - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ws = [w for w, _ in probs]
+    updates = sum(w.updates for w in ws)
+    nb = batched_bytes(ws)
+    fwd_avg = fwd_ms / (args.steps * inf.forward_step_kernels)
+    peak, peak_kind = measured_peak()
+    achieved = nb / (fwd_avg / 1e3) / 1e9
+    out = {"workload": (f"batched FP32: 16 problems, {ws[0].n}^3 grid, FEM cubes 61/81/101/121 "
+                        f"(problem b mod 4), {ws[0].n_steps} steps, one hemisphere-drawn plane wave "
+                        f"each, 1024 detectors, seeds 300..315"),
+           "value": updates / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+           "warmup": args.warmup, "tile_kz": kz, "gpu_launches": int(launches),
+           "device_bytes": int(inf.device_bytes),
+           "memory_plan": "61^3/81^3 members keep the E history, 101^3/121^3 members checkpoint "
+                          "(32 snapshots, replayed in batched launches; replays are not counted "
+                          "as updates)",
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "k_step<float,forward,16> (one launch = one step of all 16)",
+                        "algorithmic_bytes_per_launch": nb, "avg_launch_ms": fwd_avg,
+                        "adjoint_loop_ms_per_step": adj_ms / args.steps,
+                        "peak_kind": f"{peak_kind} (HBM copy, MEASURED_PEAKS.json hbm_gbs)"}}
+    b.close()
+    return out
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -384,6 +473,8 @@ def run_ours(args, w, rank, world, local_rank):
                               "fp32_speedup": value / v64,
                               "accuracy": "FP32 vs FP64 on this workload: trace 2.4e-6, J 1.9e-6, "
                                           "g 1.1e-5 relative L2 (tests/test_gpu_fullsize.py)"}
+    if world == 1 and not args.no_batched:
+        line["batched"] = run_batched(args, dev, stream)
     if world == 1 and not args.no_cpu_baseline:
         v, wall, cores = oracle_sample(w, 2)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -403,6 +494,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison pass")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 16-problem workload")
     args = ap.parse_args()
     w = workload(args.workload)
     if args.precision:
