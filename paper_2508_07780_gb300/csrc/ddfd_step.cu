@@ -151,8 +151,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   const StepParams<T> &P = L.p[prob];
   constexpr int RE = S::ROWS * S::BXW;  // component stride of a staged plane
   constexpr int BW = S::BXW;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  // 128-byte aligned stage base, computed in the shared window so that the
+  // compiler keeps every stage access a shared-memory access
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);  // "full": plane landed
   uint64_t *emp = bar + S::RING;                             // "empty": consumers released it
   const int n = P.n;
