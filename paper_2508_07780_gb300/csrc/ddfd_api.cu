@@ -66,6 +66,7 @@ struct ddfd_problem {
   void *ebe_tet_grad = nullptr, *ebe_out_r = nullptr, *ebe_out_q = nullptr;
   double *ebe_scale = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
+  float *gpart = nullptr;     // FP32: per free node (g_eps, g_sig) sums of the current step block
   double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
   double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
   int *det_node = nullptr, *det_ptr = nullptr, *det_list = nullptr, *flag = nullptr;
@@ -266,7 +267,15 @@ StepParams<T> base_params(const ddfd_problem *p) {
   P.n_free = p->n_free;
   P.gacc_e = p->gacc;
   P.gacc_s = p->gacc + p->n_free;
+  P.gpart = p->gpart;
   return P;
+}
+
+// Where adjoint step k sits in its block of GRAD_BLOCK steps (blocks end at
+// k = 1, GRAD_BLOCK + 1, ...); k_first is the first step of the sequence.
+int grad_mode(int k, int k_first) {
+  const int phase = (k - 1) % GRAD_BLOCK;
+  return ((k == k_first || phase == GRAD_BLOCK - 1) ? GM_FIRST : 0) | (phase == 0 ? GM_FOLD : 0);
 }
 
 template <typename T>
@@ -293,7 +302,8 @@ void set_forward_step(StepParams<T> &P, const ddfd_problem *p, int s, int st, co
 // Per-step scalars of adjoint step k (mu^k -> mu^{k-1}) of source s.
 template <typename T>
 void set_adjoint_step(StepParams<T> &P, const ddfd_problem *p, int s, int k, const void *cur, void *old,
-                      const T *hist_r) {
+                      const T *hist_r, int k_first) {
+  P.gmode = grad_mode(k, k_first);
   P.cur = (const T *)cur;
   P.old = (T *)old;
   P.abs_now = faces_at(p, s, k - 1);
@@ -428,7 +438,7 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
         hbase = (const T *)p->hist + (size_t)s * (Nt + 1) * 3 * p->n_free;
       }
       for (int k = n1; k >= n0 + 1; --k) {
-        set_adjoint_step(P, p, s, k, p->Mu[ic], p->Mu[io], hbase + (size_t)(k - n0) * 3 * p->n_free);
+        set_adjoint_step(P, p, s, k, p->Mu[ic], p->Mu[io], hbase + (size_t)(k - n0) * 3 * p->n_free, Nt);
         enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk);
         launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
         ++*nk;
@@ -1000,7 +1010,8 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
       (st = dalloc_t(p, 2 * (size_t)p->n_part, &p->part)) || (st = dalloc_t(p, 4, &p->scal)) ||
       (st = dalloc_t(p, 1, &p->flag)) || (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_node)) ||
       (st = dalloc_t(p, (size_t)p->n * p->n + 1, &p->det_ptr)) ||
-      (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_list)))
+      (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_list)) ||
+      (p->fp32 && (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gpart))))
     return bail(st);
   if (p->nsnap && (st = dalloc(p, (size_t)p->n_src * p->nsnap * 2 * fbytes, &p->snap))) return bail(st);
   bool any_oblique = false;
@@ -1316,7 +1327,8 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
   }
   ic = 1, io = 0;
   for (int k = steps; k >= 1; --k) {
-    set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free);
+    set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free,
+                     steps);
     enqueue_ebe<T>(p, p->Mu[ic], true, sm, &nk);
     launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
     std::swap(ic, io);
@@ -1444,7 +1456,7 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
           b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io],
           [&](StepParams<T> &P, ddfd_problem *p) {
             const long long hk = p->nsnap ? k - n0 : k;
-            set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free);
+            set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free, Nt);
           },
           sm, nk);
       std::swap(ic, io);
@@ -1554,7 +1566,7 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
         b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io],
         [&](StepParams<T> &P, ddfd_problem *p) {
           set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io],
-                           (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free);
+                           (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free, steps);
         },
         sm, &nk);
     std::swap(ic, io);

@@ -33,13 +33,24 @@ bool invert4(const double A[4][4], double X[4][4]);
 // kernels (cudaErrorInvalidValue if they differ).
 cudaError_t check_kuhn_blocks(const KuhnBlocks &kb, cudaStream_t s);
 
-// Step-kernel tiling: a CTA of 256 threads owns a STEP_TX x TY (x, y) tile of
-// one z chunk, one node per thread and plane.
+// Step-kernel tiling: a CTA of 256 computing threads owns a STEP_TX x TY
+// (x, y) tile of one z chunk: FP64 one node per thread (TY = 8), FP32 two
+// x-adjacent nodes per thread (TY = 16).
 constexpr int STEP_TX = 32;
 template <typename T>
 struct StepTile {
   static constexpr int TY = 8;
 };
+template <>
+struct StepTile<float> {
+  static constexpr int TY = 16;
+};
+
+// FP32 gradient accumulation: the adjoint steps of each block of GRAD_BLOCK
+// consecutive time steps are summed in FP32 (per free node) and the block sum
+// is added to the FP64 accumulators; gmode tells a launch where it sits.
+constexpr int GRAD_BLOCK = 16;
+enum { GM_FIRST = 1, GM_FOLD = 2 };
 
 // Geometry and per-step scalars common to the forward and adjoint steps.
 // Fields are component-major with x pitch px: offset i + px (j + n k).
@@ -94,6 +105,9 @@ struct StepParams {
   uint32_t spin_limit;   // polls per bounded wait
   int chan;              // first channel of this problem in the launch's tensor maps:
                          // fields at chan..chan+2, coefficients (s, q1, q2) likewise
+  float *gpart;          // FP32 adjoint: (g_eps, g_sig) block sums per free node
+  int gmode;             // FP32 adjoint: GM_FIRST (block starts: no partial to read),
+                         // GM_FOLD (block ends: add to the FP64 accumulators)
 };
 
 // One step launch over NB_MAX problems at most, all with the same grid size

@@ -114,6 +114,7 @@ __device__ __forceinline__ int face_count(int i, int j, int k, int n, uint32_t a
 
 template <typename T>
 struct Stage {
+  static constexpr int TX = STEP_TX;
   static constexpr int TY = StepTile<T>::TY;       // tile rows
   static constexpr int RPT = TY / 8;               // rows per thread (256 threads = 32 x 8)
   static constexpr int HX = 16 / (int)sizeof(T);   // x halo: one 16-byte unit
@@ -135,10 +136,79 @@ struct Stage {
   static constexpr int SMEM = RING * BYTES + 2 * RING * 8 + 128;
 };
 
-// Warp roles: warps 0..7 compute (one node per thread and plane), warp 8
-// stages planes.
+// FP32 stage: 32 x 16 tile, each computing thread owns two x-adjacent nodes
+// (so every staged row is read as float2 pairs); 5 stages, 2 CTAs per SM.
+constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+struct PairStage {
+  static constexpr int TX = STEP_TX;
+  static constexpr int TY = StepTile<float>::TY;
+  static constexpr int HX = 4;                     // x halo: one 16-byte unit
+  static constexpr int BXW = TX + 2 * HX;          // staged row length (40)
+  static constexpr int ROWS = TY + 2;
+  static constexpr int RE = ROWS * BXW;            // component stride of a staged plane
+  static constexpr int TXY = TX * TY;
+  static constexpr int E_BYTES = 3 * RE * 4;
+  static constexpr int O_BYTES = 3 * TXY * 4;
+  static constexpr int S_BYTES = RE * 4;
+  static constexpr int Q_BYTES = 2 * TXY * 4;
+  static constexpr int E_OFF = 0;
+  static constexpr int O_OFF = round128(E_BYTES);
+  static constexpr int S_OFF = O_OFF + round128(O_BYTES);
+  static constexpr int Q_OFF = S_OFF + round128(S_BYTES);
+  static constexpr int BYTES = Q_OFF + round128(Q_BYTES);
+  static constexpr int RING = 5;
+  static constexpr int SMEM = RING * BYTES + 2 * RING * 8 + 128;
+};
+
+// Warp roles: warps 0..7 compute, warp 8 stages planes.
 constexpr int STEP_CONSUMERS = 256;
 constexpr int STEP_THREADS = STEP_CONSUMERS + 32;
+
+// Producer (one thread): stages plane p = kk - (k0 - 1) of the chunk into
+// slot p % RING once the consumers have released the slot's previous plane
+// (p - RING): the current level (halo box; mirrored ghost planes at kk = -1
+// and kk = n), the previous level (centre box, computed planes only) and, on
+// tiles touching the FEM cube, s (halo box, planes a..b) and (q1, q2)
+// (centre box, computed planes a..b).  Every wait is bounded; on give-up it
+// sets error bit 4 and still waits (bounded) for its issued copies.
+template <class S>
+__device__ __forceinline__ void produce_planes(const CUtensorMap *mcur, const CUtensorMap *mold,
+                                               const CUtensorMap *ms, const CUtensorMap *mq,
+                                               unsigned char *smem, uint64_t *bar, uint64_t *emp, int x0,
+                                               int y0, int k0, int k1, int n, bool tile_fem, int a, int b,
+                                               int ch, uint32_t spin, int *err) {
+  const int nplanes = k1 - k0 + 2;
+  int p = 0;
+  bool ok = true;
+  for (; p < nplanes; ++p) {
+    const int slot = p % S::RING;
+    // plane p reuses the slot of plane p - RING, whose release is completion
+    // number p/RING - 1 of that slot's empty barrier
+    if (p >= S::RING && !mbar_wait_bounded(&emp[slot], (uint32_t)((p / S::RING - 1) & 1), spin)) {
+      ok = false;
+      break;
+    }
+    const int kk = k0 - 1 + p;
+    const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
+    unsigned char *st = smem + slot * S::BYTES;
+    const bool interior = kk >= k0 && kk < k1;
+    const bool coef = tile_fem && kk >= a && kk <= b;
+    const bool qc = coef && interior;
+    const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
+                           (qc ? S::Q_BYTES : 0);
+    uint64_t *bb = &bar[slot];
+    mbar_expect_tx(bb, bytes);
+    tma_load_4d(st + S::E_OFF, mcur, x0 - S::HX, y0 - 1, ksrc, ch, bb);
+    if (interior) tma_load_4d(st + S::O_OFF, mold, x0, y0, kk, ch, bb);
+    if (coef) tma_load_4d(st + S::S_OFF, ms, x0 - S::HX, y0 - 1, kk, ch, bb);
+    if (qc) tma_load_4d(st + S::Q_OFF, mq, x0, y0, kk, ch + 1, bb);
+  }
+  if (!ok) atomicOr(err, 4);
+  // every issued plane must land before the CTA can retire (bounded)
+  const int first = p > S::RING ? p - S::RING : 0;
+  for (int q = first; q < p; ++q)
+    mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), spin);
+}
 
 template <typename T, bool ADJ, int NB>
 __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
@@ -177,7 +247,6 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   const int k0 = zc * P.kz;
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
-  const int nplanes = k1 - k0 + 2;
   const bool tile_fem = x0 <= P.b - 1 && x0 + STEP_TX - 1 >= P.a + 1 && y0 <= P.b - 1 &&
                         y0 + S::TY - 1 >= P.a + 1;
 
@@ -195,40 +264,9 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   __syncthreads();
 
   if (tid >= STEP_CONSUMERS) {
-    // Producer warp: lane 0 stages plane p (k0-1+p) into slot p % RING once the
-    // consumers have released the slot's previous plane (p - RING).
-    if (tid != STEP_CONSUMERS) return;
-    int p = 0;
-    bool ok = true;
-    const int ch = P.chan;
-    for (; p < nplanes; ++p) {
-      const int slot = p % S::RING;
-      // plane p reuses the slot of plane p - RING, whose release is completion
-      // number p/RING - 1 of that slot's empty barrier
-      if (p >= S::RING && !mbar_wait_bounded(&emp[slot], (uint32_t)((p / S::RING - 1) & 1), P.spin_limit)) {
-        ok = false;
-        break;
-      }
-      const int kk = k0 - 1 + p;
-      const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
-      unsigned char *st = smem + slot * S::BYTES;
-      const bool interior = kk >= k0 && kk < k1;
-      const bool coef = tile_fem && kk >= P.a && kk <= P.b;
-      const bool qc = coef && interior;
-      const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
-                             (qc ? S::Q_BYTES : 0);
-      uint64_t *bb = &bar[slot];
-      mbar_expect_tx(bb, bytes);
-      tma_load_4d(st + S::E_OFF, &L.cur, x0 - S::HX, y0 - 1, ksrc, ch, bb);
-      if (interior) tma_load_4d(st + S::O_OFF, &L.old, x0, y0, kk, ch, bb);
-      if (coef) tma_load_4d(st + S::S_OFF, &L.s, x0 - S::HX, y0 - 1, kk, ch, bb);
-      if (qc) tma_load_4d(st + S::Q_OFF, &L.q, x0, y0, kk, ch + 1, bb);
-    }
-    if (!ok) atomicOr(P.err, 4);
-    // every issued plane must land before the CTA can retire (bounded)
-    const int first = p > S::RING ? p - S::RING : 0;
-    for (int q = first; q < p; ++q)
-      mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), P.spin_limit);
+    if (tid == STEP_CONSUMERS)
+      produce_planes<S>(&L.cur, &L.old, &L.s, &L.q, smem, bar, emp, x0, y0, k0, k1, n, tile_fem, P.a, P.b,
+                        P.chan, P.spin_limit, P.err);
     return;
   }
 
@@ -455,38 +493,494 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   }
 }
 
-template <typename T, bool ADJ, int NB>
-static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(k_step<T, ADJ, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<T>::SMEM);
+// ---------------------------------------------------------------------------
+// FP32 step kernel, two x-adjacent nodes per thread
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+
+// acc + w v for a compile-time weight (0 and +-1 cost nothing extra).
+__device__ __forceinline__ float wacc(float acc, int w, float v) {
+  if (w == 0) return acc;
+  if (w == 1) return acc + v;
+  if (w == -1) return acc - v;
+  return fmaf((float)w, v, acc);
+}
+
+// Input component d of the two 15-point block stencils of the pair (a at x,
+// b at x+1): the centre values and the 7 (+o, -o) pair sums, added as
+// out_c += B_o[c][d] * (...), B = kb / 6 applied by the caller.
+__device__ __forceinline__ void block_acc_pair(int d, float v0a, const float pa[7], float v0b, const float pb[7],
+                                               float oa[3], float ob[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float ua = wacc(oa[c], kb(0, c * 3 + d), v0a);
+    float ub = wacc(ob[c], kb(0, c * 3 + d), v0b);
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+      ua = wacc(ua, kb(p + 1, c * 3 + d), pa[p]);
+      ub = wacc(ub, kb(p + 1, c * 3 + d), pb[p]);
+    }
+    oa[c] = ua;
+    ob[c] = ub;
+  }
+}
+
+// Values of one input component at the 22 positions the pair's two stencils
+// touch, plane k (row y: x-1..x+2; row y+1: x..x+2; row y-1: x-1..x+1), plane
+// k+1 (rows y, y+1: x..x+2) and plane k-1 (rows y, y-1: x-1..x+1), reduced to
+// the pair sums of each node.  f(position value, s index) returns the stencil
+// operand: s E in the forward, mu in the adjoint.
+struct PairVals {
+  float c0, c1, m, p2;            // plane k, row y: x, x+1, x-1, x+2
+  float yp0, yp1, yp2;            // plane k, row y+1: x, x+1, x+2
+  float ym0, ym1, ymm;            // plane k, row y-1: x, x+1, x-1
+  float pc0, pc1, pp2;            // plane k+1, row y: x, x+1, x+2
+  float pyp0, pyp1, pyp2;         // plane k+1, row y+1: x, x+1, x+2
+  float mc0, mc1, mm;             // plane k-1, row y: x, x+1, x-1
+  float mym0, mym1, mymm;         // plane k-1, row y-1: x, x+1, x-1
+};
+
+__device__ __forceinline__ void pair_sums(const PairVals &v, float pa[7], float pb[7]) {
+  // offsets (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,0,1) (0,1,1) (1,1,1)
+  pa[0] = v.c1 + v.m;
+  pa[1] = v.yp0 + v.ym0;
+  pa[2] = v.pc0 + v.mc0;
+  pa[3] = v.yp1 + v.ymm;
+  pa[4] = v.pc1 + v.mm;
+  pa[5] = v.pyp0 + v.mym0;
+  pa[6] = v.pyp1 + v.mymm;
+  pb[0] = v.p2 + v.c0;
+  pb[1] = v.yp1 + v.ym1;
+  pb[2] = v.pc1 + v.mc1;
+  pb[3] = v.yp2 + v.ym0;
+  pb[4] = v.pp2 + v.mc0;
+  pb[5] = v.pyp1 + v.mym1;
+  pb[6] = v.pyp2 + v.mym0;
+}
+
+// Field values of component d at the 22 positions; the ones the Laplacian
+// already loaded are passed in (cen, above, below, rows y-1 and y+1 at x,x+1,
+// x-1 and x+2 on plane k).
+__device__ __forceinline__ PairVals pair_field(const float *e0, const float *ep, const float *em, int ci, float2 cen,
+                                               float2 ab, float2 bl, float2 ym, float2 yp, float xm, float xp2) {
+  constexpr int BW = PairStage::BXW;
+  PairVals v;
+  v.c0 = cen.x;
+  v.c1 = cen.y;
+  v.m = xm;
+  v.p2 = xp2;
+  v.yp0 = yp.x;
+  v.yp1 = yp.y;
+  v.yp2 = e0[ci + BW + 2];
+  v.ym0 = ym.x;
+  v.ym1 = ym.y;
+  v.ymm = e0[ci - BW - 1];
+  v.pc0 = ab.x;
+  v.pc1 = ab.y;
+  v.pp2 = ep[ci + 2];
+  const float2 py = ld2(ep + ci + BW);
+  v.pyp0 = py.x;
+  v.pyp1 = py.y;
+  v.pyp2 = ep[ci + BW + 2];
+  v.mc0 = bl.x;
+  v.mc1 = bl.y;
+  v.mm = em[ci - 1];
+  const float2 my = ld2(em + ci - BW);
+  v.mym0 = my.x;
+  v.mym1 = my.y;
+  v.mymm = em[ci - BW - 1];
+  return v;
+}
+
+template <bool ADJ, int NB>
+__global__ void __launch_bounds__(STEP_THREADS, 2) k_step_pair(const __grid_constant__ StepLaunch<float, NB> L) {
+  using S = PairStage;
+  constexpr int RE = S::RE, BW = S::BXW, TXY = S::TXY;
+  const int prob = NB == 1 ? 0 : (int)blockIdx.z / L.zchunks;
+  const int zc = NB == 1 ? (int)blockIdx.z : (int)blockIdx.z - prob * L.zchunks;
+  const int zchunks = NB == 1 ? (int)gridDim.z : L.zchunks;
+  const StepParams<float> &P = L.p[prob];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);
+  uint64_t *emp = bar + S::RING;
+  const int n = P.n;
+  const int tid = threadIdx.x;
+
+  if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
+    const long long nb = (long long)gridDim.x * gridDim.y * zchunks * blockDim.x;
+    long long t = ((long long)blockIdx.x + gridDim.x * ((long long)blockIdx.y + gridDim.y * zc)) *
+                      blockDim.x + tid;
+    for (; t < 3LL * P.n_det; t += nb) {
+      const int d = (int)(t / 3), c = (int)(t - 3LL * d);
+      P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
+    }
+  }
+
+  const int x0 = blockIdx.x * S::TX, y0 = blockIdx.y * S::TY;
+  const int k0 = zc * P.kz;
+  if (k0 >= n) return;  // uniform per CTA
+  const int k1 = min(k0 + P.kz, n);
+  const bool tile_fem = x0 <= P.b - 1 && x0 + S::TX - 1 >= P.a + 1 && y0 <= P.b - 1 && y0 + S::TY - 1 >= P.a + 1;
+
+  if (tid == 0) {
+    for (int s = 0; s < S::RING; ++s) {
+      mbar_init(&bar[s], 1);
+      mbar_init(&emp[s], STEP_CONSUMERS / 32);
+    }
+    mbar_fence_init();
+    tma_prefetch_desc(&L.cur);
+    tma_prefetch_desc(&L.old);
+    tma_prefetch_desc(&L.s);
+    tma_prefetch_desc(&L.q);
+  }
+  __syncthreads();
+
+  if (tid >= STEP_CONSUMERS) {
+    if (tid == STEP_CONSUMERS)
+      produce_planes<S>(&L.cur, &L.old, &L.s, &L.q, smem, bar, emp, x0, y0, k0, k1, n, tile_fem, P.a, P.b,
+                        P.chan, P.spin_limit, P.err);
+    return;
+  }
+
+  // nodes a = (x, y) and b = (x + 1, y) of every plane; lanes 0-15 of warp w
+  // take row 2w, lanes 16-31 row 2w + 1
+  const int lane = tid & 31;
+  const int yy = 2 * (tid >> 5) + (lane >> 4);
+  const int xl = 2 * (lane & 15);
+  const int x = x0 + xl, y = y0 + yy;
+  const int ci = (yy + 1) * BW + S::HX + xl;  // centre of node a in a staged plane (even)
+  const int oi = yy * S::TX + xl;             // node a in a centre box (even)
+  const bool live_a = x < n && y < n, live_b = x + 1 < n && y < n;
+  const int dym = (y == 0) ? BW : -BW, dyp = (y == n - 1) ? -BW : BW;  // mirror rows
+  const bool ex0 = x == 0, exa = x == n - 1, exb = x + 1 == n - 1;   // mirror columns
+  const bool rowfem = y > P.a && y < P.b;
+  const bool colfem = rowfem && x + 1 > P.a && x < P.b;  // either node strictly inside the cube
+  const bool fem_a = rowfem && x > P.a && x < P.b, fem_b = rowfem && x + 1 > P.a && x + 1 < P.b;
+  const bool rowfree = y >= P.f0 && y < P.f0 + P.nf;
+  const bool free_a = rowfree && x >= P.f0 && x < P.f0 + P.nf;
+  const bool free_b = rowfree && x + 1 >= P.f0 && x + 1 < P.f0 + P.nf;
+  const uint32_t sides = (P.abs_now | P.abs_next) & (DDFD_ABS_X0 | DDFD_ABS_X1 | DDFD_ABS_Y0 | DDFD_ABS_Y1);
+  const bool ybnd = (y == 0 && (sides & DDFD_ABS_Y0)) || (y == n - 1 && (sides & DDFD_ABS_Y1));
+  const bool bnd_a = ybnd || (x == 0 && (sides & DDFD_ABS_X0)) || (x == n - 1 && (sides & DDFD_ABS_X1));
+  const bool bnd_b = ybnd || (x + 1 == n - 1 && (sides & DDFD_ABS_X1));
+  const long long plane = (long long)P.px * n;
+  const uint32_t cs = (uint32_t)P.cs;
+  float *out = P.old + (long long)k0 * plane + (long long)P.px * y + x;
+
+  // one absorbing-face / source / residual update of node (xn, y): the
+  // boundary form of the update coefficients and the extra terms of R
+  auto boundary = [&](int xn, int k, float R[3], float &A, float &Bc, float &Cq) {
+    const int fn = face_count(xn, y, k, n, P.abs_now);
+    const float cc = P.cb * (float)fn;
+    const float ccn = ADJ ? P.cb * (float)face_count(xn, y, k, n, P.abs_next) : cc;
+    const float inv = P.inv_tab[fn];  // 1 / (1 + cc)
+    A = (1.f - ccn) * inv;
+    Bc = (ccn - cc) * inv;
+    Cq = inv;
+    if (!ADJ && k == n - 1 && P.src_on) {
+      if (!P.oblique) {
+        R[1] -= P.src_y;
+      } else {
+        const double v = P.src_scale * pulse_value(P.pulse_kind, P.freq, P.t0, P.width, P.t_n - P.delay[xn + n * y]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) R[c] -= (float)(P.pol[c] * v);
+      }
+    }
+    if (ADJ && k == n - 1 && P.n_det > 0) {
+      const int q0 = P.det_ptr[xn + n * y], q1 = P.det_ptr[xn + n * y + 1];
+      if (q1 > q0) {
+        const double wx = (xn == 0 || xn == n - 1) ? 0.5 : 1.0;
+        const double wy = (y == 0 || y == n - 1) ? 0.5 : 1.0;
+        const double sc = P.tau2 * P.inv_h3 / (wx * wy * 0.5);
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int qq = q0; qq < q1; ++qq) {
+          const int d = P.det_list[qq];
+          acc[0] += P.res_k[3 * d + 0];
+          acc[1] += P.res_k[3 * d + 1];
+          acc[2] += P.res_k[3 * d + 2];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) R[c] += (float)(sc * acc[c]);
+      }
+    }
+  };
+
+  int wq = 0, wslot = 0;   // planes waited so far, slot of the next wait
+  uint32_t wphase = 0;     // parity of the next wait
+  int sm1 = 0, s0 = 1, sp1 = 2;  // slots of planes p-1, p, p+1 (p = k - k0 + 1)
+  float2 below[3], cen[3];
+  for (int k = k0; k < k1; ++k) {
+    const int p = k - k0 + 1;
+    bool ok = true;
+    while (wq <= p + 1) {
+      if (!mbar_wait_bounded(&bar[wslot], wphase, P.spin_limit)) {
+        ok = false;
+        break;
+      }
+      ++wq;
+      if (++wslot == S::RING) {
+        wslot = 0;
+        wphase ^= 1u;
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform, so __syncwarp below stays safe
+      if (lane == 0) atomicOr(P.err, 4);
+      break;  // the producer times out on the slots we no longer release
+    }
+    const unsigned char *bm1 = smem + sm1 * S::BYTES;
+    const unsigned char *b0 = smem + s0 * S::BYTES;
+    const unsigned char *bp1 = smem + sp1 * S::BYTES;
+    const float *Em = (const float *)(bm1 + S::E_OFF);
+    const float *E0 = (const float *)(b0 + S::E_OFF);
+    const float *Ep = (const float *)(bp1 + S::E_OFF);
+    const bool kfem = k > P.a && k < P.b;
+    const bool kfree = k >= P.f0 && k < P.f0 + P.nf;
+    const bool kbnd = (k == 0 && ((P.abs_now | P.abs_next) & DDFD_ABS_BOTTOM)) || k == n - 1;
+    float2 ab[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (k == k0) {
+        below[c] = ld2(Em + c * RE + ci);
+        cen[c] = ld2(E0 + c * RE + ci);
+      }
+      ab[c] = ld2(Ep + c * RE + ci);
+    }
+    if (live_a) {
+      float Ra[3], Rb[3], xm[3], xp2[3];
+      float2 ym[3], yp[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float *e = E0 + c * RE + ci;
+        ym[c] = ld2(e + dym);
+        yp[c] = ld2(e + dyp);
+        xm[c] = e[-1];
+        xp2[c] = e[2];
+        const float xma = ex0 ? cen[c].y : xm[c];   // ghost x-1 = x+1 at x = 0
+        const float xpa = exa ? xm[c] : cen[c].y;   // ghost x+1 = x-1 at x = n-1
+        const float xpb = exb ? cen[c].x : xp2[c];
+        Ra[c] = 6.f * cen[c].x - (((((xpa + xma) + yp[c].x) + ym[c].x) + ab[c].x) + below[c].x);
+        Rb[c] = 6.f * cen[c].y - (((((xpb + cen[c].x) + yp[c].y) + ym[c].y) + ab[c].y) + below[c].y);
+      }
+      float Aa = 1.f, Ab = 1.f, Ba = 0.f, Bb = 0.f, Ca = 1.f, Cb = 1.f;
+      float sxa[3] = {0.f, 0.f, 0.f}, sxb[3] = {0.f, 0.f, 0.f};
+      const bool fre_a = free_a && kfree, fre_b = free_b && kfree;
+      if (colfem && kfem) {
+        const float *Q0 = (const float *)(b0 + S::Q_OFF);
+        const float2 q1 = ld2(Q0 + oi), q2 = ld2(Q0 + TXY + oi);
+        Aa = q1.x;
+        Ab = q1.y;
+        Ca = q2.x;
+        Cb = q2.y;
+        if (P.ebe_r) {
+          // element-by-element rows computed by k_ebe for this step
+          const int fm = P.b - P.a - 1;
+          const long long row = (x - P.a - 1) + (long long)fm * ((y - P.a - 1) + (long long)fm * (k - P.a - 1));
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (fem_a) {
+              Ra[c] = P.ebe_r[c * P.ebe_rows + row];
+              if (ADJ) sxa[c] = P.ebe_q[c * P.ebe_rows + row];
+            }
+            if (fem_b) {
+              Rb[c] = P.ebe_r[c * P.ebe_rows + row + 1];
+              if (ADJ) sxb[c] = P.ebe_q[c * P.ebe_rows + row + 1];
+            }
+          }
+        } else if (!ADJ) {
+          // forward: sum_o B_o (s E)_{i+o} for both nodes
+          const float *S0 = (const float *)(b0 + S::S_OFF);
+          const float *Sp = (const float *)(bp1 + S::S_OFF);
+          const float *Sm = (const float *)(bm1 + S::S_OFF);
+          PairVals s;
+          {
+            const float2 c2 = ld2(S0 + ci), y2 = ld2(S0 + ci + BW), m2 = ld2(S0 + ci - BW);
+            const float2 pc = ld2(Sp + ci), py = ld2(Sp + ci + BW);
+            const float2 mc = ld2(Sm + ci), my = ld2(Sm + ci - BW);
+            s.c0 = c2.x;
+            s.c1 = c2.y;
+            s.m = S0[ci - 1];
+            s.p2 = S0[ci + 2];
+            s.yp0 = y2.x;
+            s.yp1 = y2.y;
+            s.yp2 = S0[ci + BW + 2];
+            s.ym0 = m2.x;
+            s.ym1 = m2.y;
+            s.ymm = S0[ci - BW - 1];
+            s.pc0 = pc.x;
+            s.pc1 = pc.y;
+            s.pp2 = Sp[ci + 2];
+            s.pyp0 = py.x;
+            s.pyp1 = py.y;
+            s.pyp2 = Sp[ci + BW + 2];
+            s.mc0 = mc.x;
+            s.mc1 = mc.y;
+            s.mm = Sm[ci - 1];
+            s.mym0 = my.x;
+            s.mym1 = my.y;
+            s.mymm = Sm[ci - BW - 1];
+          }
+          float oa[3] = {0.f, 0.f, 0.f}, ob[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            PairVals v = pair_field(E0 + d * RE, Ep + d * RE, Em + d * RE, ci, cen[d], ab[d], below[d], ym[d],
+                                    yp[d], xm[d], xp2[d]);
+            v.c0 *= s.c0; v.c1 *= s.c1; v.m *= s.m; v.p2 *= s.p2;
+            v.yp0 *= s.yp0; v.yp1 *= s.yp1; v.yp2 *= s.yp2;
+            v.ym0 *= s.ym0; v.ym1 *= s.ym1; v.ymm *= s.ymm;
+            v.pc0 *= s.pc0; v.pc1 *= s.pc1; v.pp2 *= s.pp2;
+            v.pyp0 *= s.pyp0; v.pyp1 *= s.pyp1; v.pyp2 *= s.pyp2;
+            v.mc0 *= s.mc0; v.mc1 *= s.mc1; v.mm *= s.mm;
+            v.mym0 *= s.mym0; v.mym1 *= s.mym1; v.mymm *= s.mymm;
+            float pa[7], pb[7];
+            pair_sums(v, pa, pb);
+            block_acc_pair(d, v.c0, pa, v.c1, pb, oa, ob);
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            Ra[c] += oa[c] * (1.f / 6.f);
+            Rb[c] += ob[c] * (1.f / 6.f);
+          }
+        } else {
+          // adjoint: s_i sum_o B_o mu_{i+o}; the sums are kept for the gradient
+          const float2 s0v = ld2((const float *)(b0 + S::S_OFF) + ci);
+          if (s0v.x != 0.f || s0v.y != 0.f || fre_a || fre_b) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const PairVals v = pair_field(E0 + d * RE, Ep + d * RE, Em + d * RE, ci, cen[d], ab[d], below[d],
+                                            ym[d], yp[d], xm[d], xp2[d]);
+              float pa[7], pb[7];
+              pair_sums(v, pa, pb);
+              block_acc_pair(d, v.c0, pa, v.c1, pb, sxa, sxb);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              sxa[c] *= (1.f / 6.f);
+              sxb[c] *= (1.f / 6.f);
+              Ra[c] += s0v.x * sxa[c];
+              Rb[c] += s0v.y * sxb[c];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Ra[c] *= P.r2;
+        Rb[c] *= P.r2;
+      }
+      if (bnd_a || kbnd) boundary(x, k, Ra, Aa, Ba, Ca);
+      if (live_b && (bnd_b || kbnd)) boundary(x + 1, k, Rb, Ab, Bb, Cb);
+      const float *O0 = (const float *)(b0 + S::O_OFF);
+      float2 od[3], nw[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        od[c] = ld2(O0 + c * TXY + oi);
+        nw[c].x = cen[c].x + (Aa * (cen[c].x - od[c].x) + (Ba * cen[c].x - Ca * Ra[c]));
+        nw[c].y = cen[c].y + (Ab * (cen[c].y - od[c].y) + (Bb * cen[c].y - Cb * Rb[c]));
+        if (live_b)
+          *reinterpret_cast<float2 *>(out + c * cs) = nw[c];
+        else
+          out[c * cs] = nw[c].x;
+      }
+      if (fre_a || fre_b) {
+        const long long fi = (x - P.f0) + (long long)P.nf * ((y - P.f0) + (long long)P.nf * (k - P.f0));
+        if (!ADJ) {
+          if (P.hist_w) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              if (fre_a) P.hist_w[c * P.n_free + fi] = nw[c].x;
+              if (fre_b) P.hist_w[c * P.n_free + fi + 1] = nw[c].y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 0 ? !fre_a : !fre_b) continue;
+            const long long f = fi + h;
+            float ge = 0.f, gs = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float hv = __ldg(P.hist_r + c * P.n_free + f);
+              const float nv = h ? nw[c].y : nw[c].x, cv = h ? cen[c].y : cen[c].x, ov = h ? od[c].y : od[c].x;
+              const float sv = h ? sxb[c] : sxa[c];
+              ge += hv * ((nv - 2.f * cv + ov) + P.r2 * sv);
+              gs += hv * (nv - ov);
+            }
+            // block sums in FP32, folded into the FP64 accumulators
+            float2 *gp = reinterpret_cast<float2 *>(P.gpart) + f;
+            if (!(P.gmode & GM_FIRST)) {
+              const float2 prev = *gp;
+              ge = prev.x + ge;
+              gs = prev.y + gs;
+            }
+            if (P.gmode & GM_FOLD) {
+              P.gacc_e[f] += (double)ge;
+              P.gacc_s[f] += (double)gs;
+            } else {
+              *gp = make_float2(ge, gs);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      below[c] = cen[c];
+      cen[c] = ab[c];
+    }
+    out += plane;
+    // release plane p-1 (its slot) to the producer: one arrival per warp
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&emp[sm1]);
+    sm1 = s0;
+    s0 = sp1;
+    sp1 = (sp1 + 1 == S::RING) ? 0 : sp1 + 1;
+  }
+}
+
+template <bool ADJ, int NB>
+static cudaError_t set_smem_f64() {
+  return cudaFuncSetAttribute(k_step<double, ADJ, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Stage<double>::SMEM);
+}
+template <bool ADJ, int NB>
+static cudaError_t set_smem_f32() {
+  return cudaFuncSetAttribute(k_step_pair<ADJ, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairStage::SMEM);
 }
 
 cudaError_t prepare_step_kernels() {
   cudaError_t e;
-  if ((e = set_smem<float, false, 1>()) != cudaSuccess || (e = set_smem<float, true, 1>()) != cudaSuccess ||
-      (e = set_smem<double, false, 1>()) != cudaSuccess || (e = set_smem<double, true, 1>()) != cudaSuccess ||
-      (e = set_smem<float, false, BATCH_MAX>()) != cudaSuccess ||
-      (e = set_smem<float, true, BATCH_MAX>()) != cudaSuccess ||
-      (e = set_smem<double, false, BATCH_MAX>()) != cudaSuccess ||
-      (e = set_smem<double, true, BATCH_MAX>()) != cudaSuccess)
+  if ((e = set_smem_f32<false, 1>()) != cudaSuccess || (e = set_smem_f32<true, 1>()) != cudaSuccess ||
+      (e = set_smem_f64<false, 1>()) != cudaSuccess || (e = set_smem_f64<true, 1>()) != cudaSuccess ||
+      (e = set_smem_f32<false, BATCH_MAX>()) != cudaSuccess || (e = set_smem_f32<true, BATCH_MAX>()) != cudaSuccess ||
+      (e = set_smem_f64<false, BATCH_MAX>()) != cudaSuccess || (e = set_smem_f64<true, BATCH_MAX>()) != cudaSuccess)
     return e;
   return cudaSuccess;
 }
 
-template <typename T, bool ADJ, int NB>
-static void launch_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
-  const int ty = Stage<T>::TY;
-  const StepParams<T> &P = L.p[0];
+template <bool ADJ, int NB>
+static void launch_step(const StepLaunch<double, NB> &L, cudaStream_t s) {
+  const int ty = Stage<double>::TY;
+  const StepParams<double> &P = L.p[0];
   const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
-  k_step<T, ADJ, NB><<<grid, STEP_THREADS, Stage<T>::SMEM, s>>>(L);
+  k_step<double, ADJ, NB><<<grid, STEP_THREADS, Stage<double>::SMEM, s>>>(L);
+}
+template <bool ADJ, int NB>
+static void launch_step(const StepLaunch<float, NB> &L, cudaStream_t s) {
+  const int ty = PairStage::TY;
+  const StepParams<float> &P = L.p[0];
+  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
+  k_step_pair<ADJ, NB><<<grid, STEP_THREADS, PairStage::SMEM, s>>>(L);
 }
 
 template <typename T, int NB>
 void launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
-  launch_step<T, false, NB>(L, s);
+  launch_step<false, NB>(L, s);
 }
 template <typename T, int NB>
 void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
-  launch_step<T, true, NB>(L, s);
+  launch_step<true, NB>(L, s);
 }
 
 #define DDFD_STEP_INST(T, NB)                                                      \
