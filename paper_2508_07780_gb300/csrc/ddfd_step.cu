@@ -157,12 +157,40 @@ struct PairStage {
   static constexpr int Q_OFF = S_OFF + round128(S_BYTES);
   static constexpr int BYTES = Q_OFF + round128(Q_BYTES);
   static constexpr int RING = 5;
-  static constexpr int SMEM = RING * BYTES + 2 * RING * 8 + 128;
+  // stages, full and empty barriers, release counters, two ints, alignment
+  static constexpr int SMEM = RING * BYTES + 2 * RING * 8 + RING * 4 + 8 + 128;
 };
 
 // Warp roles: warps 0..7 compute, warp 8 stages planes.
 constexpr int STEP_CONSUMERS = 256;
 constexpr int STEP_THREADS = STEP_CONSUMERS + 32;
+
+// Stages plane p = kk - (k0 - 1) of the chunk into slot p % RING and arms the
+// slot's "full" barrier with the byte count: the current level (halo box;
+// mirrored ghost planes at kk = -1 and kk = n), the previous level (centre
+// box, computed planes only) and, on tiles touching the FEM cube, s (halo
+// box, planes a..b) and (q1, q2) (centre box, computed planes a..b).
+template <class S>
+__device__ __forceinline__ void stage_plane(int p, const CUtensorMap *mcur, const CUtensorMap *mold,
+                                            const CUtensorMap *ms, const CUtensorMap *mq, unsigned char *smem,
+                                            uint64_t *bar, int x0, int y0, int k0, int k1, int n, bool tile_fem,
+                                            int a, int b, int ch) {
+  const int slot = p % S::RING;
+  const int kk = k0 - 1 + p;
+  const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
+  unsigned char *st = smem + slot * S::BYTES;
+  const bool interior = kk >= k0 && kk < k1;
+  const bool coef = tile_fem && kk >= a && kk <= b;
+  const bool qc = coef && interior;
+  const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
+                         (qc ? S::Q_BYTES : 0);
+  uint64_t *bb = &bar[slot];
+  mbar_expect_tx(bb, bytes);
+  tma_load_4d(st + S::E_OFF, mcur, x0 - S::HX, y0 - 1, ksrc, ch, bb);
+  if (interior) tma_load_4d(st + S::O_OFF, mold, x0, y0, kk, ch, bb);
+  if (coef) tma_load_4d(st + S::S_OFF, ms, x0 - S::HX, y0 - 1, kk, ch, bb);
+  if (qc) tma_load_4d(st + S::Q_OFF, mq, x0, y0, kk, ch + 1, bb);
+}
 
 // Producer (one thread): stages plane p = kk - (k0 - 1) of the chunk into
 // slot p % RING once the consumers have released the slot's previous plane
@@ -188,20 +216,7 @@ __device__ __forceinline__ void produce_planes(const CUtensorMap *mcur, const CU
       ok = false;
       break;
     }
-    const int kk = k0 - 1 + p;
-    const int ksrc = kk < 0 ? 1 : (kk >= n ? n - 2 : kk);  // mirror ghost planes
-    unsigned char *st = smem + slot * S::BYTES;
-    const bool interior = kk >= k0 && kk < k1;
-    const bool coef = tile_fem && kk >= a && kk <= b;
-    const bool qc = coef && interior;
-    const uint32_t bytes = S::E_BYTES + (interior ? S::O_BYTES : 0) + (coef ? S::S_BYTES : 0) +
-                           (qc ? S::Q_BYTES : 0);
-    uint64_t *bb = &bar[slot];
-    mbar_expect_tx(bb, bytes);
-    tma_load_4d(st + S::E_OFF, mcur, x0 - S::HX, y0 - 1, ksrc, ch, bb);
-    if (interior) tma_load_4d(st + S::O_OFF, mold, x0, y0, kk, ch, bb);
-    if (coef) tma_load_4d(st + S::S_OFF, ms, x0 - S::HX, y0 - 1, kk, ch, bb);
-    if (qc) tma_load_4d(st + S::Q_OFF, mq, x0, y0, kk, ch + 1, bb);
+    stage_plane<S>(p, mcur, mold, ms, mq, smem, bar, x0, y0, k0, k1, n, tile_fem, a, b, ch);
   }
   if (!ok) atomicOr(err, 4);
   // every issued plane must land before the CTA can retire (bounded)
@@ -593,8 +608,21 @@ __device__ __forceinline__ PairVals pair_field(const float *e0, const float *ep,
   return v;
 }
 
+// Staging: the forward CTA has no producer warp: thread 0 stages the first
+// RING planes, and afterwards the last of the 8 warps to release a slot
+// stages the plane that reuses it (per-slot release counters in shared
+// memory); 8 warps per CTA and 2 CTAs per SM leave up to 128 registers per
+// thread.  The adjoint CTA has a producer warp (warp 8) fed by per-slot
+// "empty" mbarriers; it measured faster there (80 vs 84 us per 201^3 step).
+template <bool ADJ>
+struct PairMode {
+  static constexpr bool PRODUCER_WARP = ADJ;
+  static constexpr int THREADS = PRODUCER_WARP ? STEP_THREADS : STEP_CONSUMERS;
+};
+
 template <bool ADJ, int NB>
-__global__ void __launch_bounds__(STEP_THREADS, 2) k_step_pair(const __grid_constant__ StepLaunch<float, NB> L) {
+__global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const __grid_constant__ StepLaunch<float, NB> L) {
+  constexpr bool PW = PairMode<ADJ>::PRODUCER_WARP;
   using S = PairStage;
   constexpr int RE = S::RE, BW = S::BXW, TXY = S::TXY;
   const int prob = NB == 1 ? 0 : (int)blockIdx.z / L.zchunks;
@@ -603,8 +631,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_pair(const __grid_cons
   const StepParams<float> &P = L.p[prob];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);
-  uint64_t *emp = bar + S::RING;
+  uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);  // "full": plane landed
+  uint64_t *emp = bar + S::RING;                              // producer warp: "empty" barriers
+  unsigned *rel = (unsigned *)(emp + S::RING);                // otherwise: per-slot warp releases
+  int *issued = (int *)(rel + S::RING);                       // planes staged so far (a prefix)
+  int *exited = issued + 1;                                   // warps that left the loop
   const int n = P.n;
   const int tid = threadIdx.x;
 
@@ -623,21 +654,30 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_pair(const __grid_cons
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
   const bool tile_fem = x0 <= P.b - 1 && x0 + S::TX - 1 >= P.a + 1 && y0 <= P.b - 1 && y0 + S::TY - 1 >= P.a + 1;
+  const int nplanes = k1 - k0 + 2;
 
   if (tid == 0) {
     for (int s = 0; s < S::RING; ++s) {
       mbar_init(&bar[s], 1);
-      mbar_init(&emp[s], STEP_CONSUMERS / 32);
+      if (PW) mbar_init(&emp[s], STEP_CONSUMERS / 32);
+      rel[s] = 0;
     }
+    *exited = 0;
     mbar_fence_init();
     tma_prefetch_desc(&L.cur);
     tma_prefetch_desc(&L.old);
     tma_prefetch_desc(&L.s);
     tma_prefetch_desc(&L.q);
+    if (!PW) {
+      const int first = nplanes < S::RING ? nplanes : S::RING;
+      *issued = first;
+      for (int q = 0; q < first; ++q)
+        stage_plane<S>(q, &L.cur, &L.old, &L.s, &L.q, smem, bar, x0, y0, k0, k1, n, tile_fem, P.a, P.b, P.chan);
+    }
   }
   __syncthreads();
 
-  if (tid >= STEP_CONSUMERS) {
+  if (PW && tid >= STEP_CONSUMERS) {
     if (tid == STEP_CONSUMERS)
       produce_planes<S>(&L.cur, &L.old, &L.s, &L.q, smem, bar, emp, x0, y0, k0, k1, n, tile_fem, P.a, P.b,
                         P.chan, P.spin_limit, P.err);
@@ -930,12 +970,40 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_pair(const __grid_cons
       cen[c] = ab[c];
     }
     out += plane;
-    // release plane p-1 (its slot) to the producer: one arrival per warp
+    // release plane p-1: the warp that completes the slot's release count
+    // stages plane p-1+RING into it
     __syncwarp();
-    if (lane == 0) mbar_arrive(&emp[sm1]);
+    if (PW) {
+      if (lane == 0) mbar_arrive(&emp[sm1]);
+    } else if (lane == 0) {
+      __threadfence_block();
+      const unsigned prev = atomicAdd(&rel[sm1], 1u);
+      if ((prev + 1) % (STEP_CONSUMERS / 32) == 0) {
+        const int q = p - 1 + S::RING;
+        if (q < nplanes) {
+          __threadfence_block();
+          fence_proxy_async_smem();
+          stage_plane<S>(q, &L.cur, &L.old, &L.s, &L.q, smem, bar, x0, y0, k0, k1, n, tile_fem, P.a, P.b,
+                         P.chan);
+          atomicMax(issued, q + 1);
+        }
+      }
+    }
     sm1 = s0;
     s0 = sp1;
     sp1 = (sp1 + 1 == S::RING) ? 0 : sp1 + 1;
+  }
+  // the last warp out waits (bounded) for the copies still in flight, if a
+  // timeout cut the loop short (otherwise they have all landed already); with
+  // a producer warp, that warp does it
+  __syncwarp();
+  if (!PW && lane == 0) {
+    __threadfence_block();
+    if (atomicAdd(exited, 1) == STEP_CONSUMERS / 32 - 1) {
+      const int iss = atomicAdd(issued, 0);
+      for (int q = iss > S::RING ? iss - S::RING : 0; q < iss; ++q)
+        mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), P.spin_limit);
+    }
   }
 }
 
@@ -971,7 +1039,7 @@ static void launch_step(const StepLaunch<float, NB> &L, cudaStream_t s) {
   const int ty = PairStage::TY;
   const StepParams<float> &P = L.p[0];
   const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
-  k_step_pair<ADJ, NB><<<grid, STEP_THREADS, PairStage::SMEM, s>>>(L);
+  k_step_pair<ADJ, NB><<<grid, PairMode<ADJ>::THREADS, PairStage::SMEM, s>>>(L);
 }
 
 template <typename T, int NB>
