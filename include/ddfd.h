@@ -105,6 +105,8 @@ typedef struct {
   int64_t mem_budget;    /* device bytes the handle may allocate; 0 = no limit */
   int32_t tile_kz;       /* z planes per thread block of the step kernels (tuning;
                             0 = library default, else 2..n) */
+  int32_t forward_only;  /* nonzero: keep neither the E history nor snapshots (for
+                            data generation); ddfd_adjoint then fails with DDFD_E_STATE */
   void *stream;          /* cudaStream_t for all work, or NULL for the default stream */
 } ddfd_config;
 
@@ -277,6 +279,59 @@ typedef struct {
   int64_t device_bytes;
 } ddfd_batch_info;
 int ddfd_batch_get_info(const ddfd_batch *b, ddfd_batch_info *info);
+
+/* Conjugate gradient reconstruction (Sec. 4, the CGA): iterations m = 0, 1, ...
+ * of  1) E^m, lambda^m and g^m at (eps^m, sig^m) for every member of the batch
+ * (the members are the measurements -- incident waves -- of one model: same
+ * fem_n, and gamma_eps = gamma_sig = 0 in their configurations, the CG
+ * supplies the regularisation);  2)-3) Fletcher-Reeves directions
+ * d^m = -g^m + beta^m d^{m-1}, beta^m = ||g^m||^2 / ||g^{m-1}||^2, d^0 = -g^0, and
+ * updates eps^{m+1} = eps^m + alpha_eps^m d_eps^m (sigma likewise), clamped to
+ * [1, eps_max] x [0, sig_max];  4) alpha^{m+1} = -(g^m, d^m) / (gamma^m (d^m, d^m));
+ * 5) gamma^{m+1} = gamma^0 / (m+1)^p;  6) stop when (||eps^{m+1} - eps^m|| < eta1_eps
+ * or ||sig^{m+1} - sig^m|| < eta1_sig) and (||g_eps^m|| < eta2_eps or ||g_sig^m|| <
+ * eta2_sig), or after max_iter iterations.
+ * g^m is the L2(Omega) representative of the derivative of the discrete
+ * functional (the summed member gradients divided by the lumped mass h^3)
+ * plus gamma^m (eps^m - eps^0); (u, v) = h^3 sum over the free nodes; the
+ * initial guess eps^0, sig^0 is the regularisation centre (eq.
+ * tikhonov_functional).  Inner products, norms and step sizes are FP64;
+ * every vector operation runs on the GPU, the scalar rules on the host. */
+typedef struct {
+  int32_t max_iter;                 /* M >= 1 */
+  double gamma_eps0, gamma_sig0;    /* gamma^0 >= 0 */
+  double alpha_eps0, alpha_sig0;    /* alpha^0 */
+  double p;                         /* gamma schedule exponent, 0 <= p < 1 */
+  double eta1_eps, eta1_sig, eta2_eps, eta2_sig;  /* stopping tolerances (0: never) */
+  double eps_max, sig_max;          /* admissible box */
+  int32_t restart;                  /* nonzero (not in the paper): a direction with
+                                       (g^m, d^m) >= 0 is replaced by -g^m */
+} ddfd_cg_params;
+
+/* One iteration's record. */
+typedef struct {
+  int32_t iter, stop;
+  double J, J_data;                 /* functional with gamma^m, and its data part */
+  double gnorm_eps, gnorm_sig;      /* ||g^m|| */
+  double alpha_eps, alpha_sig, beta_eps, beta_sig, gamma_eps, gamma_sig;  /* used at m */
+  double step_eps, step_sig;        /* ||eps^{m+1} - eps^m||, ||sig^{m+1} - sig^m|| */
+  double ms;                        /* device time of the iteration (CUDA events) */
+} ddfd_cg_iter;
+
+/* Defaults: max_iter 20, gammas 1, alphas 1, p 0.5, tolerances 0, box 100, no restart. */
+void ddfd_cg_params_default(ddfd_cg_params *prm);
+
+/* Run the CGA on batch b.  eobs[i]: member i's observed trace (host, the
+ * layout of ddfd_adjoint).  eps, sig (host, free-node order): the initial
+ * guess on entry, the last iterate eps^{m+1} on return.  log (host, may be
+ * NULL): room for max_iter records; *iters (may be NULL): iterations done;
+ * eps_iters, sig_iters (host, may be NULL): [max_iter][n_free], iterate
+ * m+1 after iteration m.  The box must lie inside every member's eps_max,
+ * sig_max.  Errors: DDFD_E_ARG (members differ in fem_n or carry gammas, bad
+ * parameters), DDFD_E_COEFF (initial guess outside the box), the errors of
+ * the forward/adjoint calls; message in ddfd_batch_last_error. */
+int ddfd_cg_run(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *prm, double *eps,
+                double *sig, ddfd_cg_iter *log, int32_t *iters, double *eps_iters, double *sig_iters);
 
 /* Allocation-free data misfit, without a handle.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

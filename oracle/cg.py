@@ -22,6 +22,10 @@ regularisation centre (eq. tikhonov_functional names both eps^0); the
 "and/or" of the stopping rule groups as written above; after each update eps
 is clamped to [1, eps_max] and sigma to [0, sig_max] (the admissible set of
 eq. epsilon_sigma_constraint), the directions are not.
+
+Option (not in the paper, off by default): restart, the usual safeguard of
+nonlinear conjugate gradients -- when the Fletcher-Reeves direction is not a
+descent direction, (g^m, d^m) >= 0, it is replaced by -g^m.
 """
 from __future__ import annotations
 
@@ -45,6 +49,7 @@ class CGParams:
     eta2_sig: float = 0.0
     eps_max: float = 100.0
     sig_max: float = 100.0
+    restart: bool = False
 
 
 def cga(evaluate: Callable, eps0: np.ndarray, sig0: np.ndarray, m: np.ndarray, prm: CGParams,
@@ -83,6 +88,10 @@ def cga(evaluate: Callable, eps0: np.ndarray, sig0: np.ndarray, m: np.ndarray, p
             beta_s = gg_s / gg_s_prev if gg_s_prev > 0 else 0.0
             d_e = -g_e + beta_e * d_e
             d_s = -g_s + beta_s * d_s
+            if prm.restart and ip(g_e, d_e) >= 0.0:
+                beta_e, d_e = 0.0, -g_e
+            if prm.restart and ip(g_s, d_s) >= 0.0:
+                beta_s, d_s = 0.0, -g_s
         eps_new = np.clip(eps + alpha_e * d_e, 1.0, prm.eps_max)
         sig_new = np.clip(sig + alpha_s * d_s, 0.0, prm.sig_max)
         # step 4

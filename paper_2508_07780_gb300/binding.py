@@ -38,6 +38,7 @@ ABI_SYMBOLS = (
     "ddfd_autotune", "ddfd_create_batch", "ddfd_destroy_batch", "ddfd_batch_last_error",
     "ddfd_batch_member", "ddfd_batch_forward", "ddfd_batch_forward_dev", "ddfd_batch_adjoint",
     "ddfd_batch_adjoint_dev", "ddfd_batch_autotune", "ddfd_batch_get_info",
+    "ddfd_cg_params_default", "ddfd_cg_run",
 )
 
 
@@ -50,7 +51,8 @@ class ddfd_config(ctypes.Structure):
         ("det_ij", POINTER(c_int32)), ("absorbing_faces", c_uint32), ("gamma_eps", c_double),
         ("gamma_sig", c_double), ("z_delta_frac", c_double), ("eps_max", c_double),
         ("sig_max", c_double), ("n_snapshots", c_int32), ("cfl_check", c_int32),
-        ("mem_budget", c_int64), ("tile_kz", c_int32), ("stream", c_void_p),
+        ("mem_budget", c_int64), ("tile_kz", c_int32), ("forward_only", c_int32),
+        ("stream", c_void_p),
     ]
 
 
@@ -76,6 +78,25 @@ class ddfd_batch_info(ctypes.Structure):
         ("forward_loop_ms", c_double), ("adjoint_loop_ms", c_double),
         ("forward_step_kernels", c_int64), ("adjoint_step_kernels", c_int64),
         ("kernel_launches", c_int64), ("device_bytes", c_int64),
+    ]
+
+
+class ddfd_cg_params(ctypes.Structure):
+    _fields_ = [
+        ("max_iter", c_int32), ("gamma_eps0", c_double), ("gamma_sig0", c_double),
+        ("alpha_eps0", c_double), ("alpha_sig0", c_double), ("p", c_double),
+        ("eta1_eps", c_double), ("eta1_sig", c_double), ("eta2_eps", c_double),
+        ("eta2_sig", c_double), ("eps_max", c_double), ("sig_max", c_double), ("restart", c_int32),
+    ]
+
+
+class ddfd_cg_iter(ctypes.Structure):
+    _fields_ = [
+        ("iter", c_int32), ("stop", c_int32), ("J", c_double), ("J_data", c_double),
+        ("gnorm_eps", c_double), ("gnorm_sig", c_double), ("alpha_eps", c_double),
+        ("alpha_sig", c_double), ("beta_eps", c_double), ("beta_sig", c_double),
+        ("gamma_eps", c_double), ("gamma_sig", c_double), ("step_eps", c_double),
+        ("step_sig", c_double), ("ms", c_double),
     ]
 
 
@@ -135,9 +156,14 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).argtypes = [P, P]
     lib.ddfd_batch_autotune.argtypes = [P, c_int32, POINTER(c_int32)]
     lib.ddfd_batch_get_info.argtypes = [P, POINTER(ddfd_batch_info)]
+    lib.ddfd_cg_params_default.argtypes = [POINTER(ddfd_cg_params)]
+    lib.ddfd_cg_params_default.restype = None
+    lib.ddfd_cg_run.argtypes = [P, P, POINTER(ddfd_cg_params), P, P, POINTER(ddfd_cg_iter), POINTER(c_int32),
+                                P, P]
     for name in ABI_SYMBOLS:
         if name not in ("ddfd_config_default", "ddfd_destroy", "ddfd_last_error",
-                        "ddfd_create_error", "ddfd_destroy_batch", "ddfd_batch_last_error"):
+                        "ddfd_create_error", "ddfd_destroy_batch", "ddfd_batch_last_error",
+                        "ddfd_cg_params_default"):
             getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -445,3 +471,30 @@ class Batch:
             _dev(e, int(np.prod(m.trace_shape)))
         ptrs = (c_void_p * len(eobs))(*[e.data_ptr() for e in eobs])
         self._check(self._lib.ddfd_batch_adjoint_dev(self._h, ptrs))
+
+    def cg_run(self, eobs, eps0, sig0, iterates=False, **params):
+        """ddfd_cg_run: the CGA of Sec. 4 over the members (one model, several
+        measurements).  eobs: one observed trace per member (host); eps0, sig0:
+        initial guess on the free nodes; params: ddfd_cg_params fields.
+        Returns (eps, sig, log) with log a list of dicts, one per iteration
+        (with iterates=True each dict also holds that iteration's new eps, sig)."""
+        prm = ddfd_cg_params()
+        self._lib.ddfd_cg_params_default(ctypes.byref(prm))
+        for k, v in params.items():
+            setattr(prm, k, v)
+        nf = self.members[0].n_free
+        eps = _host(eps0, np.float64, nf).copy()
+        sig = _host(sig0, np.float64, nf).copy()
+        es = [_host(e, np.float64, int(np.prod(m.trace_shape))) for e, m in zip(eobs, self.members)]
+        ptrs = (c_void_p * len(es))(*[e.ctypes.data for e in es])
+        log = (ddfd_cg_iter * prm.max_iter)()
+        iters = c_int32()
+        ei = np.empty((prm.max_iter, nf)) if iterates else None
+        si = np.empty((prm.max_iter, nf)) if iterates else None
+        self._check(self._lib.ddfd_cg_run(self._h, ptrs, ctypes.byref(prm), _ptr(eps), _ptr(sig), log,
+                                          ctypes.byref(iters), _ptr(ei), _ptr(si)))
+        out = [{f: getattr(log[i], f) for f, _ in ddfd_cg_iter._fields_} for i in range(iters.value)]
+        if iterates:
+            for i, r in enumerate(out):
+                r["eps"], r["sig"] = ei[i], si[i]
+        return eps, sig, out

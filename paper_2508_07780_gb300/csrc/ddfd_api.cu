@@ -95,6 +95,7 @@ struct ddfd_problem {
   // batch's stacked slabs (not owned); the batch destroys its members
   ddfd_batch *batch = nullptr;
   int slot = 0;
+  bool fonly = false;         // forward_only: no history, no snapshots, no adjoint
 };
 
 namespace {
@@ -378,7 +379,8 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
         CK(cudaMemcpyAsync(sn + fbytes, p->E[io], fbytes, cudaMemcpyDeviceToDevice, sm));
       }
       set_forward_step(P, p, s, st, p->E[ic], p->E[io],
-                       p->nsnap ? nullptr : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free);
+                       (p->nsnap || p->fonly) ? nullptr
+                                              : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free);
       enqueue_ebe<T>(p, p->E[ic], false, sm, nk);
       launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
       ++*nk;
@@ -604,8 +606,8 @@ int encode_field_maps(std::string *err, FieldMaps *fm, void *const E[2], void *c
   for (int q = 0; q < 2; ++q)
     if ((st = encode_map(err, &fm->E_halo[q], E[q], n, px, fp32, ch, 3, true)) ||
         (st = encode_map(err, &fm->E_ctr[q], E[q], n, px, fp32, ch, 3, false)) ||
-        (st = encode_map(err, &fm->M_halo[q], Mu[q], n, px, fp32, ch, 3, true)) ||
-        (st = encode_map(err, &fm->M_ctr[q], Mu[q], n, px, fp32, ch, 3, false)))
+        (Mu[q] && (st = encode_map(err, &fm->M_halo[q], Mu[q], n, px, fp32, ch, 3, true))) ||
+        (Mu[q] && (st = encode_map(err, &fm->M_ctr[q], Mu[q], n, px, fp32, ch, 3, false))))
       return st;
   if ((st = encode_map(err, &fm->S, coef, n, px, fp32, ch, 1, true))) return st;
   return encode_map(err, &fm->Q, coef, n, px, fp32, ch, 2, false);
@@ -822,6 +824,7 @@ int functional_impl(ddfd_problem *p, const double *eobs, double *J, bool host) {
 }
 
 int adjoint_impl(ddfd_problem *p, const double *eobs, bool host) {
+  if (p->fonly) return fail(p, DDFD_E_STATE, "the handle was created forward_only");
   if (p->state < ST_FORWARD) return fail(p, DDFD_E_STATE, "ddfd_adjoint needs a forward run");
   if (!eobs && p->n_det > 0) return fail(p, DDFD_E_ARG, "eobs is required");
   const long long cnt = (long long)p->n_src * (p->Nt + 1) * p->n_det * 3;
@@ -982,12 +985,14 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   setup_sources(p, &delay_host);
   const size_t fbytes = 3 * (size_t)p->cs * p->esz;
   const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
-  if (cfg->n_snapshots > 0) {
+  p->fonly = cfg->forward_only != 0;
+  if (cfg->n_snapshots > 0 && !p->fonly) {
     p->seg = (p->Nt + cfg->n_snapshots - 1) / cfg->n_snapshots;
     p->nsnap = (p->Nt + p->seg - 1) / p->seg;
   }
-  const size_t histn = p->nsnap ? (size_t)(p->seg + 1) * 3 * p->n_free
-                                : (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
+  const size_t histn = p->fonly ? 0
+                       : p->nsnap ? (size_t)(p->seg + 1) * 3 * p->n_free
+                                  : (size_t)p->n_src * (p->Nt + 1) * 3 * p->n_free;
   if (ext) {
     for (int q = 0; q < 2; ++q) {
       p->E[q] = ext->E[q];
@@ -997,7 +1002,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
     p->batch = ext->batch;
     p->slot = ext->slot;
   } else if ((st = dalloc(p, fbytes, &p->E[0])) || (st = dalloc(p, fbytes, &p->E[1])) ||
-             (st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])) ||
+             (!p->fonly && ((st = dalloc(p, fbytes, &p->Mu[0])) || (st = dalloc(p, fbytes, &p->Mu[1])))) ||
              (st = dalloc(p, 3 * (size_t)p->cs * p->esz, &p->kcoef))) {
     return bail(st);
   }
@@ -1054,8 +1059,9 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   ++p->launches;
   if (cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream) ||
  cudaMemsetAsync(p->E[0], 0, fbytes, p->stream) ||
-      cudaMemsetAsync(p->E[1], 0, fbytes, p->stream) || cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream) ||
-      cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream)) {
+      cudaMemsetAsync(p->E[1], 0, fbytes, p->stream) ||
+      (p->Mu[0] && cudaMemsetAsync(p->Mu[0], 0, fbytes, p->stream)) ||
+      (p->Mu[1] && cudaMemsetAsync(p->Mu[1], 0, fbytes, p->stream))) {
     p->err = "memset failed";
     return bail(DDFD_E_CUDA);
   }
@@ -1260,6 +1266,10 @@ struct ddfd_batch {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double fwd_ms = 0.0, adj_ms = 0.0;
   int64_t fwd_kernels = 0, adj_kernels = 0;
+  // conjugate gradient work space (FP64, free nodes): 14 vectors, partial
+  // sums, the 6 reduced scalars
+  double *cg = nullptr;
+  long long cg_n = 0;
 };
 
 namespace {
@@ -1311,7 +1321,7 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
   p->kz = kz;
   for (int q = 0; q < 2; ++q) {
     CK(cudaMemsetAsync(p->E[q], 0, fbytes, sm));
-    CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, sm));
+    if (p->Mu[q]) CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, sm));
   }
   if (trn) CK(cudaMemsetAsync(p->res, 0, trn * sizeof(double), sm));
   CK(cudaEventRecord(p->ev[0], sm));
@@ -1320,13 +1330,14 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
   set_source(P, p, 0);
   int ic = 1, io = 0;
   for (int st = 0; st < steps; ++st) {
-    set_forward_step(P, p, 0, st, p->E[ic], p->E[io], (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
+    set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
+                     p->fonly ? nullptr : (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
     enqueue_ebe<T>(p, p->E[ic], false, sm, &nk);
     launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
     std::swap(ic, io);
   }
   ic = 1, io = 0;
-  for (int k = steps; k >= 1; --k) {
+  for (int k = p->fonly ? 0 : steps; k >= 1; --k) {  // forward_only handles time the forward alone
     set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free,
                      steps);
     enqueue_ebe<T>(p, p->Mu[ic], true, sm, &nk);
@@ -1400,7 +1411,7 @@ int enqueue_batch_forward(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
         b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io],
         [&](StepParams<T> &P, ddfd_problem *p) {
           set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
-                           p->nsnap ? nullptr : (T *)p->hist + (size_t)(st + 1) * 3 * p->n_free);
+                           (p->nsnap || p->fonly) ? nullptr : (T *)p->hist + (size_t)(st + 1) * 3 * p->n_free);
         },
         sm, nk);
     std::swap(ic, io);
@@ -1541,7 +1552,7 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
   b->kz = kz;
   for (int q = 0; q < 2; ++q) {
     BCK(cudaMemsetAsync(b->E[q], 0, slab, sm));
-    BCK(cudaMemsetAsync(b->Mu[q], 0, slab, sm));
+    if (b->Mu[q]) BCK(cudaMemsetAsync(b->Mu[q], 0, slab, sm));
   }
   for (ddfd_problem *p : b->m) {
     const size_t trn = (size_t)(p->Nt + 1) * p->n_det * 3;
@@ -1555,13 +1566,16 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
     launch_groups<T>(
         b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io],
         [&](StepParams<T> &P, ddfd_problem *p) {
-          set_forward_step(P, p, 0, st, p->E[ic], p->E[io], (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
+          set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
+                           p->fonly ? nullptr : (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
         },
         sm, &nk);
     std::swap(ic, io);
   }
+  bool any_fonly = false;
+  for (ddfd_problem *p : b->m) any_fonly |= p->fonly;
   ic = 1, io = 0;
-  for (int k = steps; k >= 1; --k) {
+  for (int k = any_fonly ? 0 : steps; k >= 1; --k) {  // forward_only members: forward trials only
     launch_groups<T>(
         b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io],
         [&](StepParams<T> &P, ddfd_problem *p) {
@@ -1605,6 +1619,8 @@ int batch_forward_impl(ddfd_batch *b, double *const *trace_out, cudaMemcpyKind k
 
 int batch_adjoint_impl(ddfd_batch *b, const double *const *eobs, bool host) {
   for (size_t i = 0; i < b->m.size(); ++i)
+    if (b->m[i]->fonly) return bfail(b, DDFD_E_STATE, "member " + std::to_string(i) + " was created forward_only");
+  for (size_t i = 0; i < b->m.size(); ++i)
     if (b->m[i]->state < ST_FORWARD)
       return bfail(b, DDFD_E_STATE, "member " + std::to_string(i) + " has no forward run");
   for (size_t i = 0; i < b->m.size(); ++i) {
@@ -1624,6 +1640,148 @@ int batch_adjoint_impl(ddfd_batch *b, const double *const *eobs, bool host) {
   if ((st = batch_check_err(b))) return st;
   BCK(cudaStreamSynchronize(b->stream));
   for (ddfd_problem *p : b->m) p->state = ST_ADJOINT;
+  return DDFD_OK;
+}
+
+// The CGA of Sec. 4 over the batch's members (see ddfd_cg_run in ddfd.h).
+int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *prm, double *eps_h,
+                double *sig_h, ddfd_cg_iter *log, int32_t *iters, double *eps_it, double *sig_it) {
+  if (!prm || !eps_h || !sig_h) return bfail(b, DDFD_E_ARG, "parameters, eps and sigma are required");
+  if (prm->max_iter < 1 || !(prm->gamma_eps0 >= 0) || !(prm->gamma_sig0 >= 0) || !(prm->p >= 0 && prm->p < 1) ||
+      !(prm->eps_max >= 1) || !(prm->sig_max >= 0) || !std::isfinite(prm->alpha_eps0) || !std::isfinite(prm->alpha_sig0))
+    return bfail(b, DDFD_E_ARG, "bad CG parameters");
+  ddfd_problem *p0 = b->m[0];
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    const ddfd_problem *p = b->m[i];
+    if (p->fem_n != p0->fem_n) return bfail(b, DDFD_E_ARG, "CG members must share fem_n");
+    if (p->cfg.gamma_eps != 0.0 || p->cfg.gamma_sig != 0.0)
+      return bfail(b, DDFD_E_ARG, "CG members must have gamma_eps = gamma_sig = 0 (the CG regularises)");
+    if (p->fonly) return bfail(b, DDFD_E_ARG, "CG members cannot be forward_only");
+    const long long cnt = (long long)(p->Nt + 1) * p->n_det * 3;
+    if (cnt > 0 && (!eobs || !eobs[i])) return bfail(b, DDFD_E_ARG, "eobs of member " + std::to_string(i) + " is missing");
+  }
+  const long long n = p0->n_free;
+  cudaStream_t sm = b->stream;
+  if (!b->cg || b->cg_n != n) {
+    if (b->cg) {
+      cudaFree(b->cg);
+      b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)b->cg));
+    }
+    const size_t bytes = (14 * (size_t)n + 6 * CG_BLOCKS + 8) * sizeof(double);
+    if (cudaMalloc((void **)&b->cg, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      b->cg = nullptr;
+      return bfail(b, DDFD_E_OOM, "cudaMalloc of the CG work space failed");
+    }
+    b->allocs.push_back(b->cg);
+    b->bytes += (int64_t)bytes;
+    b->cg_n = n;
+  }
+  double *v[14];
+  for (int q = 0; q < 14; ++q) v[q] = b->cg + (size_t)q * n;
+  double *eps = v[0], *sig = v[1], *eps_n = v[2], *sig_n = v[3], *re = v[4], *rs = v[5];
+  double *Ge = v[6], *Gs = v[7], *Te = v[8], *Ts = v[9], *gte = v[10], *gts = v[11], *de = v[12], *ds = v[13];
+  double *part = b->cg + 14 * (size_t)n, *out = part + 6 * CG_BLOCKS;
+  const size_t nb = (size_t)n * sizeof(double);
+  BCK(cudaMemcpyAsync(eps, eps_h, nb, cudaMemcpyHostToDevice, sm));
+  BCK(cudaMemcpyAsync(sig, sig_h, nb, cudaMemcpyHostToDevice, sm));
+  BCK(cudaMemcpyAsync(re, eps, nb, cudaMemcpyDeviceToDevice, sm));
+  BCK(cudaMemcpyAsync(rs, sig, nb, cudaMemcpyDeviceToDevice, sm));
+  std::vector<const double *> eobs_dev(b->m.size(), nullptr);
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    ddfd_problem *p = b->m[i];
+    const long long cnt = (long long)(p->Nt + 1) * p->n_det * 3;
+    if (cnt > 0) BCK(cudaMemcpyAsync(p->eobs_stage, eobs[i], cnt * sizeof(double), cudaMemcpyHostToDevice, sm));
+    eobs_dev[i] = p->eobs_stage;
+  }
+  const double m = p0->h * p0->h * p0->h;  // lumped mass of a free node
+  double gam_e = prm->gamma_eps0, gam_s = prm->gamma_sig0;
+  double alp_e = prm->alpha_eps0, alp_s = prm->alpha_sig0;
+  double gg_e_prev = 0.0, gg_s_prev = 0.0;
+  int done = 0;
+  for (int it = 0; it < prm->max_iter; ++it) {
+    BCK(cudaEventRecord(b->ev[0], sm));
+    // 1. E^m, lambda^m, g^m
+    int st;
+    for (ddfd_problem *p : b->m)
+      if ((st = set_coeffs_impl(p, eps, sig, nullptr, nullptr, cudaMemcpyDeviceToDevice)))
+        return bfail(b, st, p->err);
+    if ((st = batch_forward_impl(b, nullptr, cudaMemcpyDeviceToDevice))) return st;
+    double J_data = 0.0;
+    for (size_t i = 0; i < b->m.size(); ++i) {
+      double Ji = 0.0;
+      if ((st = functional_impl(b->m[i], eobs_dev[i], &Ji, false))) return bfail(b, st, b->m[i]->err);
+      J_data += Ji;
+    }
+    if ((st = batch_adjoint_impl(b, eobs_dev.data(), false))) return st;
+    for (size_t i = 0; i < b->m.size(); ++i) {
+      const bool first = i == 0;
+      if ((st = gradient_impl(b->m[i], first ? Ge : Te, first ? Gs : Ts, false))) return bfail(b, st, b->m[i]->err);
+      if (!first) launch_cg_accum(Ge, Gs, Te, Ts, n, sm);
+    }
+    launch_cg_grad(Ge, Gs, eps, sig, re, rs, 1.0 / m, gam_e, gam_s, gte, gts, de, ds, it > 0, n, part, out, sm);
+    double r4[6];
+    BCK(cudaMemcpyAsync(r4, out, sizeof(r4), cudaMemcpyDeviceToHost, sm));
+    BCK(cudaStreamSynchronize(sm));
+    const double gg_e = m * r4[0], gg_s = m * r4[1];
+    const double J = J_data + 0.5 * gam_e * m * r4[2] + 0.5 * gam_s * m * r4[3];
+    // 2.-3. Fletcher-Reeves directions and clamped updates; with restart, a
+    // direction that is not a descent one, (g, -g + beta d) >= 0, becomes -g
+    double beta_e = (it > 0 && gg_e_prev > 0) ? gg_e / gg_e_prev : 0.0;
+    double beta_s = (it > 0 && gg_s_prev > 0) ? gg_s / gg_s_prev : 0.0;
+    if (prm->restart && it > 0 && -gg_e + beta_e * m * r4[4] >= 0.0) beta_e = 0.0;
+    if (prm->restart && it > 0 && -gg_s + beta_s * m * r4[5] >= 0.0) beta_s = 0.0;
+    launch_cg_update(gte, gts, de, ds, beta_e, beta_s, alp_e, alp_s, eps, sig, eps_n, sig_n, prm->eps_max,
+                     prm->sig_max, it == 0, n, part, out, sm);
+    double r6[6];
+    BCK(cudaMemcpyAsync(r6, out, sizeof(r6), cudaMemcpyDeviceToHost, sm));
+    BCK(cudaEventRecord(b->ev[1], sm));
+    BCK(cudaEventSynchronize(b->ev[1]));
+    float ms = 0.0f;
+    BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+    b->launches += 4 + (int64_t)b->m.size();
+    // 4. step sizes, 5. regularisation schedule, 6. stopping rule
+    const double gd_e = m * r6[0], dd_e = m * r6[1], gd_s = m * r6[3], dd_s = m * r6[4];
+    const double step_e = std::sqrt(m * r6[2]), step_s = std::sqrt(m * r6[5]);
+    const double alp_e_next = (gam_e > 0 && dd_e > 0) ? -gd_e / (gam_e * dd_e) : alp_e;
+    const double alp_s_next = (gam_s > 0 && dd_s > 0) ? -gd_s / (gam_s * dd_s) : alp_s;
+    const bool stop = (step_e < prm->eta1_eps || step_s < prm->eta1_sig) &&
+                      (std::sqrt(gg_e) < prm->eta2_eps || std::sqrt(gg_s) < prm->eta2_sig);
+    if (log) {
+      ddfd_cg_iter &L = log[it];
+      L.iter = it;
+      L.stop = stop ? 1 : 0;
+      L.J = J;
+      L.J_data = J_data;
+      L.gnorm_eps = std::sqrt(gg_e);
+      L.gnorm_sig = std::sqrt(gg_s);
+      L.alpha_eps = alp_e;
+      L.alpha_sig = alp_s;
+      L.beta_eps = beta_e;
+      L.beta_sig = beta_s;
+      L.gamma_eps = gam_e;
+      L.gamma_sig = gam_s;
+      L.step_eps = step_e;
+      L.step_sig = step_s;
+      L.ms = ms;
+    }
+    if (eps_it) BCK(cudaMemcpyAsync(eps_it + (size_t)it * n, eps_n, nb, cudaMemcpyDeviceToHost, sm));
+    if (sig_it) BCK(cudaMemcpyAsync(sig_it + (size_t)it * n, sig_n, nb, cudaMemcpyDeviceToHost, sm));
+    std::swap(eps, eps_n);
+    std::swap(sig, sig_n);
+    alp_e = alp_e_next;
+    alp_s = alp_s_next;
+    gam_e = prm->gamma_eps0 / std::pow((double)(it + 1), prm->p);
+    gam_s = prm->gamma_sig0 / std::pow((double)(it + 1), prm->p);
+    gg_e_prev = gg_e;
+    gg_s_prev = gg_s;
+    done = it + 1;
+    if (stop) break;
+  }
+  BCK(cudaMemcpyAsync(eps_h, eps, nb, cudaMemcpyDeviceToHost, sm));
+  BCK(cudaMemcpyAsync(sig_h, sig, nb, cudaMemcpyDeviceToHost, sm));
+  BCK(cudaStreamSynchronize(sm));
+  if (iters) *iters = done;
   return DDFD_OK;
 }
 
@@ -1659,7 +1817,7 @@ int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out) {
   const size_t fbytes = 3 * (size_t)p->cs * p->esz;
   for (int q = 0; q < 2; ++q) {
     CK(cudaMemsetAsync(p->E[q], 0, fbytes, p->stream));
-    CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, p->stream));
+    if (p->Mu[q]) CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, p->stream));
   }
   if (st) return st;
   if (tile_kz_out) *tile_kz_out = p->kz;
@@ -1726,8 +1884,11 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(DDFD_E_CUDA, "stream creation failed");
   const size_t slab = 3 * (size_t)b->cs * b->esz * count;
-  void **bufs[5] = {&b->E[0], &b->E[1], &b->Mu[0], &b->Mu[1], &b->kcoef};
+  bool all_fonly = true;
+  for (int i = 0; i < count; ++i) all_fonly &= cfgs[i].forward_only != 0;
+  void **bufs[5] = {&b->E[0], &b->E[1], &b->kcoef, &b->Mu[0], &b->Mu[1]};
   for (void **v : bufs) {
+    if (all_fonly && (v == &b->Mu[0] || v == &b->Mu[1])) continue;  // no adjoint fields
     if (cudaMalloc(v, slab) != cudaSuccess) {
       cudaGetLastError();
       *v = nullptr;
@@ -1753,7 +1914,7 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
     MemberSlot ms;
     for (int q = 0; q < 2; ++q) {
       ms.E[q] = (char *)b->E[q] + i * fb;
-      ms.Mu[q] = (char *)b->Mu[q] + i * fb;
+      ms.Mu[q] = b->Mu[q] ? (char *)b->Mu[q] + i * fb : nullptr;
     }
     ms.kcoef = (char *)b->kcoef + i * fb;
     ms.batch = b;
@@ -1825,12 +1986,29 @@ int ddfd_batch_autotune(ddfd_batch *b, int32_t steps, int32_t *tile_kz_out) {
   const size_t slab = 3 * (size_t)b->cs * b->esz * b->m.size();
   for (int q = 0; q < 2; ++q) {
     BCK(cudaMemsetAsync(b->E[q], 0, slab, b->stream));
-    BCK(cudaMemsetAsync(b->Mu[q], 0, slab, b->stream));
+    if (b->Mu[q]) BCK(cudaMemsetAsync(b->Mu[q], 0, slab, b->stream));
   }
   if (st) return st;
   if (tile_kz_out) *tile_kz_out = b->kz;
   BCK(cudaStreamSynchronize(b->stream));
   return DDFD_OK;
+}
+
+void ddfd_cg_params_default(ddfd_cg_params *prm) {
+  if (!prm) return;
+  std::memset(prm, 0, sizeof(*prm));
+  prm->max_iter = 20;
+  prm->gamma_eps0 = prm->gamma_sig0 = 1.0;
+  prm->alpha_eps0 = prm->alpha_sig0 = 1.0;
+  prm->p = 0.5;
+  prm->eps_max = prm->sig_max = 100.0;
+}
+
+int ddfd_cg_run(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *prm, double *eps, double *sig,
+                ddfd_cg_iter *log, int32_t *iters, double *eps_iters, double *sig_iters) {
+  if (!b) return DDFD_E_ARG;
+  b->err.clear();
+  return cg_run_impl(b, eobs, prm, eps, sig, log, iters, eps_iters, sig_iters);
 }
 
 int ddfd_batch_get_info(const ddfd_batch *b, ddfd_batch_info *info) {

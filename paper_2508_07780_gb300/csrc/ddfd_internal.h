@@ -182,4 +182,17 @@ void launch_apply_op(const double *x, double *y, int n, int px, int a, int b, co
 void launch_norm2(const double *x, long long count, double *part, int n_part, cudaStream_t s);
 void launch_scale(double *x, long long count, const double *norm2, cudaStream_t s);
 
+// Conjugate gradient vector kernels (csrc/ddfd_cg.cu), FP64 over the free
+// nodes; part holds CG_BLOCKS x 6 partial sums, out the 4 or 6 sums.
+constexpr int CG_BLOCKS = 256;
+void launch_cg_accum(double *ge, double *gs, const double *te, const double *ts, long long n, cudaStream_t s);
+void launch_cg_grad(const double *Ge, const double *Gs, const double *eps, const double *sig, const double *re,
+                    const double *rs, double inv_m, double gam_e, double gam_s, double *gte, double *gts,
+                    const double *dpe, const double *dps, int use_d, long long n, double *part, double *out,
+                    cudaStream_t s);
+void launch_cg_update(const double *gte, const double *gts, double *de, double *ds, double beta_e, double beta_s,
+                      double alpha_e, double alpha_s, const double *eps, const double *sig, double *eps_new,
+                      double *sig_new, double eps_max, double sig_max, int first, long long n, double *part,
+                      double *out, cudaStream_t s);
+
 }  // namespace ddfd

@@ -1,0 +1,132 @@
+"""Gradient-based reconstruction of eps and sigma with the conjugate gradient
+algorithm of Sec. 4 on the GPU (ddfd_cg_run), on a synthetic workload.
+
+The default workload is 8 incident plane waves (normal incidence and 7
+hemisphere directions) on a 241^3 grid with a 61^3 FEM cube and 2400 steps,
+FP32 fields.  The observed data come from a forward run on the 2x finer grid
+(481^3, FEM cube 121^3, 4800 steps, FP64 by default) of the same physical
+model, sampled at the coarse detector nodes and times, with 1% multiplicative
+Gaussian noise.  The initial guess is the layers-only model (the known skin
+layers); the target is the model with its inclusions.
+
+    python -m paper_2508_07780_gb300.reconstruct [--n 241] [--fem-n 61]
+        [--sources 8] [--iters 20] [--fine-precision fp64|fp32] [--out report.json]
+
+Prints one JSON report: per CG variant and iteration J, gradient norms, step
+sizes, device time, and the relative L2 errors of eps and sigma on the free
+nodes.  Variants: "literal" (the paper's rules) and "restart" (the same with
+the Fletcher-Reeves restart safeguard, ddfd_cg_params.restart).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=241)
+    ap.add_argument("--fem-n", type=int, default=61)
+    ap.add_argument("--steps", type=int, default=None, help="coarse steps (default: T = 3)")
+    ap.add_argument("--sources", type=int, default=8)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--incl", type=int, default=1)
+    ap.add_argument("--det", type=int, default=32)
+    ap.add_argument("--noise", type=float, default=0.01)
+    ap.add_argument("--fine-precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--p", type=float, default=0.5)
+    ap.add_argument("--step0", type=float, default=1.0,
+                    help="first update's RMS change of eps on the free nodes")
+    ap.add_argument("--variants", default="literal,restart",
+                    help="CG variants: literal (the paper's rules) and/or restart (FR restart safeguard)")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import torch
+    from synth import box_bounds, detector_grid, free_box, layered_inclusion_model, shard_directions
+    from . import Batch
+
+    n, fem_n = a.n, a.fem_n
+    cfl = 0.3
+    h = 1.0 / (n - 1)
+    nt = a.steps or int(round(3.0 / (cfl * h)))
+    nf_, fem_f, nt_f = 2 * (n - 1) + 1, 2 * (fem_n - 1) + 1, 2 * nt
+    dirs = shard_directions(a.sources)
+    det = detector_grid(n, fem_n, a.det)
+    report = dict(workload=dict(grid=n, fem_n=fem_n, n_steps=nt, sources=a.sources, detectors=int(det.shape[0]),
+                                fine_grid=nf_, fine_fem_n=fem_f, fine_steps=nt_f, fine_precision=a.fine_precision,
+                                noise=a.noise, seed=a.seed, inclusions=a.incl,
+                                fem="uniform Kuhn cube (no local refinement)"))
+    stream = torch.cuda.current_stream().cuda_stream
+
+    # observed data: the finer forward of the same physical model
+    t0 = time.perf_counter()
+    ef, sf = layered_inclusion_model(nf_, fem_f, a.seed, a.incl, box=free_box(n, fem_n))
+    fine = Batch([dict(n=nf_, fem_n=fem_f, n_steps=nt_f, cfl=cfl, precision=a.fine_precision,
+                       src_dir=d[None, :], det_ij=2 * det, forward_only=1, stream=stream) for d in dirs])
+    for m in fine.members:
+        m.set_coeffs(ef, sf)
+    traces = fine.forward()
+    fine_info = fine.get_info()
+    fine.close()
+    rng = np.random.default_rng(a.seed)
+    eobs = []
+    for tr in traces:
+        coarse = tr[:, ::2][:, : nt + 1]                     # t_n = n tau = 2n tau_fine
+        eobs.append(np.ascontiguousarray(coarse * (1.0 + a.noise * rng.standard_normal(coarse.shape))))
+    report["data"] = dict(seconds=time.perf_counter() - t0, fine_forward_ms=fine_info.forward_loop_ms,
+                          fine_device_bytes=int(fine_info.device_bytes))
+
+    # reconstruction
+    e_true, s_true = layered_inclusion_model(n, fem_n, a.seed, a.incl)
+    e0, s0 = layered_inclusion_model(n, fem_n, a.seed, 0)
+    b = Batch([dict(n=n, fem_n=fem_n, n_steps=nt, cfl=cfl, precision="fp32", src_dir=d[None, :], det_ij=det,
+                    stream=stream) for d in dirs])
+    kz = b.autotune(steps=4)
+    # step sizes: the first update moves eps by step0 (RMS over the free box);
+    # gamma^0 = 1/alpha^0 keeps the step rule's alpha^1 at the same scale
+    _, _, probe = b.cg_run(eobs, e0, s0, max_iter=1, gamma_eps0=1.0, gamma_sig0=1.0, alpha_eps0=0.0,
+                           alpha_sig0=0.0)
+    _, _, f0, f1 = box_bounds(n, fem_n)
+    vol = ((f1 - f0) * h) ** 3
+    ge0, gs0 = probe[0]["gnorm_eps"], probe[0]["gnorm_sig"]
+    alpha_e = a.step0 * np.sqrt(vol) / ge0
+    alpha_s = 0.1 * a.step0 * np.sqrt(vol) / gs0
+    ne, ns = np.linalg.norm(e_true), np.linalg.norm(s_true)
+    report["initial_eps_rel_err"] = float(np.linalg.norm(e0 - e_true) / ne)
+    report["initial_sig_rel_err"] = float(np.linalg.norm(s0 - s_true) / ns)
+    report["tile_kz"] = kz
+    report["updates_per_iteration"] = 2 * n ** 3 * nt * a.sources
+    for variant in a.variants.split(","):
+        prm = dict(max_iter=a.iters, gamma_eps0=1.0 / alpha_e, gamma_sig0=1.0 / alpha_s, alpha_eps0=alpha_e,
+                   alpha_sig0=alpha_s, p=a.p, eps_max=100.0, sig_max=100.0, restart=int(variant == "restart"))
+        eps, sig, log = b.cg_run(eobs, e0, s0, iterates=True, **prm)
+        rows = []
+        for r in log:
+            rows.append({k: float(v) for k, v in r.items() if k not in ("eps", "sig")})
+            rows[-1]["eps_rel_err"] = float(np.linalg.norm(r["eps"] - e_true) / ne)
+            rows[-1]["sig_rel_err"] = float(np.linalg.norm(r["sig"] - s_true) / ns)
+        ms = [r["ms"] for r in log]
+        report["cg_" + variant] = dict(params=prm, ms_per_iteration=float(np.mean(ms)),
+                                       updates_per_s=report["updates_per_iteration"] / (np.mean(ms) / 1e3),
+                                       iterations=rows)
+    report["device_bytes"] = int(b.get_info().device_bytes)
+    b.close()
+    txt = json.dumps(report)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(txt + "\n")
+    print(txt, flush=True)
+
+
+if __name__ == "__main__":
+    main()

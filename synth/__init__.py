@@ -11,6 +11,7 @@ from .models import (  # noqa: F401
     Workload,
     box_bounds,
     detector_grid,
+    free_box,
     hemisphere_directions,
     layered_inclusion_model,
     shard_directions,

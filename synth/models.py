@@ -64,7 +64,7 @@ INCL_SIG = (0.5, 1.0)
 INCL_SEMI_AXIS = (0.1, 0.2)
 
 
-def layered_inclusion_model(n: int, fem_n: int, seed: int, n_incl: int):
+def layered_inclusion_model(n: int, fem_n: int, seed: int, n_incl: int, box=None):
     """Nodal (eps, sigma) on the free nodes, flattened x fastest.
 
     Draw order from one SplitMix64 stream: (eps, sigma) for each layer from
@@ -72,6 +72,11 @@ def layered_inclusion_model(n: int, fem_n: int, seed: int, n_incl: int):
     coordinates and (eps, sigma).  The layers-only model of the same seed
     (n_incl = 0) is therefore the inclusion model without its inclusions.
     A later inclusion overwrites an earlier one where they overlap.
+
+    box: (lo, hi), the physical extent [lo, hi]^3 the model is defined on
+    (default: this grid's free box).  Passing another grid's box samples the
+    same physical model on this grid (free nodes outside the box are vacuum,
+    eps = 1, sigma = 0): a finer grid then carries the coarse grid's model.
     """
     h = 1.0 / (n - 1)
     _, _, f0, f1 = box_bounds(n, fem_n)
@@ -85,7 +90,7 @@ def layered_inclusion_model(n: int, fem_n: int, seed: int, n_incl: int):
     shape = (nf, nf, nf)
     eps = np.empty(shape)
     sig = np.empty(shape)
-    z_lo, z_hi = x[0], x[-1]
+    z_lo, z_hi = (x[0], x[-1]) if box is None else (float(box[0]), float(box[1]))
     height = z_hi - z_lo
     cuts = [z_hi - LAYER_FRACTIONS[0] * height,
             z_hi - (LAYER_FRACTIONS[0] + LAYER_FRACTIONS[1]) * height]
@@ -111,7 +116,21 @@ def layered_inclusion_model(n: int, fem_n: int, seed: int, n_incl: int):
         inside = np.broadcast_to(inside, shape)
         eps[inside] = e
         sig[inside] = s
+    if box is not None:
+        tol = 1e-9 * h
+        outside = ((X < z_lo - tol) | (X > z_hi + tol) | (Y < z_lo - tol) | (Y > z_hi + tol)
+                   | (Z < z_lo - tol) | (Z > z_hi + tol))
+        outside = np.broadcast_to(outside, shape)
+        eps[outside] = 1.0
+        sig[outside] = 0.0
     return eps.ravel().copy(), sig.ravel().copy()
+
+
+def free_box(n: int, fem_n: int):
+    """Physical extent (lo, hi) of the free box of a grid."""
+    _, _, f0, f1 = box_bounds(n, fem_n)
+    h = 1.0 / (n - 1)
+    return f0 * h, f1 * h
 
 
 def detector_grid(n: int, fem_n: int, d: int) -> np.ndarray:

@@ -54,6 +54,17 @@ def test_hand_iterated_sequence():
         assert [r[key] for r in log[:2]] == pytest.approx(g[key], rel=1e-14), key
 
 
+def test_restart_option():
+    g = golden()
+    m = np.array([2.0])
+    eps, sig, log = cga(scalar_problem(m), np.array([2.0]), np.array([0.0]), m,
+                        CGParams(max_iter=3, restart=True, **PRM))
+    assert eps[0] == pytest.approx(g["eps3_restart"][0], rel=1e-14)
+    assert sig[0] == pytest.approx(g["sig3_restart"][0], rel=1e-14)
+    assert [r["beta_eps"] for r in log] == pytest.approx([0.0, 0.25, g["beta2_restart"][0]])
+    assert [r["J"] for r in log] == pytest.approx(g["J"], rel=1e-14)
+
+
 def test_stopping_rule():
     g = golden()
     m = np.array([2.0])
