@@ -337,7 +337,7 @@ def run_ours(args, w, rank, world, local_rank):
     src_dir = w.directions() if world == 1 else shard_directions(world)[rank:rank + 1]
     kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision=w.precision,
               src_dir=src_dir, det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
-              stream=stream.cuda_stream)
+              n_snapshots=args.snapshots, stream=stream.cuda_stream)
     p = Problem(**kw)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     # observed data: the layers-only model's trace (the inclusions are what
@@ -428,6 +428,7 @@ def run_ours(args, w, rank, world, local_rank):
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_s = float(e2e_t.item())
     nf, ntr = p.n_free, int(np.prod(p.trace_shape))
+    dev_bytes = p.get_info().device_bytes
     h2d = 2 * nf * 8 + 2 * ntr * 8
     d2h = ntr * 8 + 2 * nf * 8 + 3 * 8
     if world > 1:                       # the gradient through the all-reduce and back
@@ -440,7 +441,10 @@ def run_ours(args, w, rank, world, local_rank):
     fwd_b, adj_b = algorithmic_bytes(w)
     fwd_avg = fwd_ms / max(nk, 1)
     adj_avg = adj_ms / max(nk, 1)
-    which, nbytes, dur = ("adjoint", adj_b, adj_avg) if adj_ms >= fwd_ms else ("forward", fwd_b, fwd_avg)
+    # with checkpointing the adjoint sequence also holds the replayed forward
+    # steps, so the roofline is taken on the forward launches
+    adj_first = adj_ms >= fwd_ms and not args.snapshots
+    which, nbytes, dur = ("adjoint", adj_b, adj_avg) if adj_first else ("forward", fwd_b, fwd_avg)
     peak, peak_kind = measured_peak()
     achieved = nbytes / (dur / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -456,6 +460,9 @@ def run_ours(args, w, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": describe(w), "grid": w.n, "fem_n": w.fem_n,
                        "n_steps": w.n_steps, "n_src": w.n_src, "problems_per_gpu": 1,
+                       "e_history": (f"checkpointing, {args.snapshots} snapshots, replayed segments"
+                                     if args.snapshots else "full E history on the free nodes"),
+                       "device_bytes": int(dev_bytes),
                        "l2": "inputs larger than L2: 2 field levels of 3 x n^3 plus the "
                              "E history on the free nodes, re-streamed every step",
                        "parallelism": "single GPU" if world == 1 else
@@ -495,6 +502,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison pass")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 16-problem workload")
+    ap.add_argument("--snapshots", type=int, default=0,
+                    help="checkpointing with this many state snapshots instead of the full E history")
     args = ap.parse_args()
     w = workload(args.workload)
     if args.precision:
