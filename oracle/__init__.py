@@ -17,7 +17,10 @@ What it computes, in plain numpy/scipy, FP64, with no blocking or fusion:
     solver.adjoint);
   * the gradient with respect to epsilon and sigma (Sec. 4, eq. gradeps, taken
     as the exact derivative of the discrete functional; solver.gradient);
-  * the leapfrog stability bound by power iteration (cfl.py).
+  * the leapfrog stability bound by power iteration (cfl.py);
+  * the conjugate gradient reconstruction of Sec. 4 (cg.py);
+  * all of the above on a locally refined FEM mesh given as explicit
+    (new nodes, tetrahedra) (grid.RefinedGrid, OracleProblem(mesh=...)).
 
 It shares no code with the CUDA path.  Seeded inputs come from the separate
 ``synth`` package, which holds none of the method's arithmetic.
@@ -27,7 +30,7 @@ mathematics rather than by this code: closed-form spectra, exactness on
 polynomials, a 1-D textbook reduction, d'Alembert's solution, a discrete energy
 identity, the space-time adjoint dot test and central finite differences.
 """
-from .grid import Grid  # noqa: F401
+from .grid import Grid, RefinedGrid  # noqa: F401
 from .hybrid import HybridOperator  # noqa: F401
 from .source import SourceSpec  # noqa: F401
 from .solver import OracleProblem  # noqa: F401

@@ -48,12 +48,16 @@ def fd_laplacian(g: Grid) -> sp.csr_matrix:
     W = sp.diags(h * _w1(n))
     L = (sp.kron(W, sp.kron(W, K)) + sp.kron(W, sp.kron(K, W))
          + sp.kron(K, sp.kron(W, W)))
+    extra = g.nn - n ** 3            # nodes of a refined FEM mesh: no FD rows
+    if extra:
+        L = sp.block_diag((L, sp.csr_matrix((extra, extra))))
     return L.tocsr()
 
 
 def fd_mass(g: Grid) -> np.ndarray:
     w = _w1(g.n)
-    return g.h ** 3 * np.kron(w, np.kron(w, w))
+    m = g.h ** 3 * np.kron(w, np.kron(w, w))
+    return np.concatenate([m, np.zeros(g.nn - g.n ** 3)])
 
 
 def fd_face_mass(g: Grid, face: str) -> np.ndarray:

@@ -86,3 +86,48 @@ class Grid:
                 v.append(w)
             tets.append(np.stack([self.nid(x[:, 0], x[:, 1], x[:, 2]) for x in v], axis=1))
         return np.concatenate(tets, axis=0)
+
+
+class RefinedGrid(Grid):
+    """The same grid with an explicit, locally refined FEM mesh (given as
+    input geometry: new nodes as midpoints of two parent nodes, and the
+    tetrahedra replacing the Kuhn split of the FEM cube).
+
+    Node ids: grid nodes as in Grid, new node e is n^3 + e.  Every new node is
+    a FEM row and a free (coefficient) node; the free-node order is the grid's
+    free nodes, then the new nodes in order.  FD rows and the domain faces are
+    those of the grid nodes."""
+
+    def __init__(self, n: int, fem_n: int, parents, tets):
+        super().__init__(n, fem_n)
+        parents = np.asarray(parents, dtype=np.int64).reshape(-1, 2)
+        self.n_grid = n ** 3
+        self.n_extra = parents.shape[0]
+        self.nn = self.n_grid + self.n_extra
+        X = np.zeros((self.nn, 3))
+        X[:self.n_grid] = self.coords
+        for e, (p, q) in enumerate(parents):
+            if p >= self.n_grid + e or q >= self.n_grid + e:
+                raise ValueError("a new node's parents must precede it")
+            X[self.n_grid + e] = 0.5 * (X[p] + X[q])
+        self.coords = X
+        pad = -np.ones(self.n_extra, dtype=self.i_of.dtype)
+        self.i_of = np.concatenate([self.i_of, pad])
+        self.j_of = np.concatenate([self.j_of, pad])
+        self.k_of = np.concatenate([self.k_of, pad])
+        self.parents = parents
+        self._tets = np.asarray(tets, dtype=np.int64).reshape(-1, 4)
+
+    @property
+    def fem_rows(self):
+        m = self.in_box(self.a + 1, self.b - 1)
+        m[self.n_grid:] = True
+        return m
+
+    @property
+    def free_nodes(self):
+        grid_free = np.nonzero(self.in_box(self.f0, self.f1))[0]
+        return np.concatenate([grid_free, np.arange(self.n_grid, self.nn)])
+
+    def kuhn_tets(self):
+        return self._tets

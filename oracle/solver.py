@@ -48,7 +48,7 @@ from typing import Callable, Optional, Sequence
 
 import numpy as np
 
-from .grid import Grid
+from .grid import Grid, RefinedGrid
 from .hybrid import HybridOperator
 from .source import SourceSpec, z_delta
 
@@ -76,8 +76,10 @@ class OracleProblem:
                  eps_free, sig_free, det_ij, sources: Sequence[SourceSpec],
                  absorbing: int = ABS_BOTTOM | ABS_TOP, z_delta_frac: float = 0.1,
                  gamma_eps: float = 0.0, gamma_sig: float = 0.0,
-                 eps0_free=None, sig0_free=None):
-        self.g = Grid(n, fem_n)
+                 eps0_free=None, sig0_free=None, mesh=None):
+        # mesh: None (the Kuhn split of the FEM cube) or an explicit refined
+        # FEM mesh (parents, tets) as described in grid.RefinedGrid
+        self.g = Grid(n, fem_n) if mesh is None else RefinedGrid(n, fem_n, *mesh)
         self.op = HybridOperator(self.g, eps_free, sig_free)
         self.n_steps = int(n_steps)
         self.tau = cfl * self.g.h
