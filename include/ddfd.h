@@ -66,7 +66,9 @@ typedef enum {
 
 enum { DDFD_FP64 = 0, DDFD_FP32 = 1 };           /* field precision; reductions are FP64 */
 enum { DDFD_SRC_GAUSS = 0, DDFD_SRC_SINE = 1 };  /* pulse shape, see ddfd_config */
-enum { DDFD_FEM_STENCIL = 0, DDFD_FEM_EBE = 1 };  /* FEM apply: Kuhn block stencil / element gather */
+/* FEM apply: Kuhn block stencil / element gather over the Kuhn split /
+ * element gather over an explicit, locally refined mesh (mesh_* fields) */
+enum { DDFD_FEM_STENCIL = 0, DDFD_FEM_EBE = 1, DDFD_FEM_MESH = 2 };
 enum {
   DDFD_ABS_BOTTOM = 1, DDFD_ABS_TOP = 2, /* top: only after the source phase */
   DDFD_ABS_X0 = 4, DDFD_ABS_X1 = 8, DDFD_ABS_Y0 = 16, DDFD_ABS_Y1 = 32
@@ -78,7 +80,7 @@ typedef struct {
   int32_t n_steps;       /* Nt >= 1 time steps */
   double cfl;            /* tau = cfl * h; 0 < cfl */
   int32_t precision;     /* DDFD_FP64 or DDFD_FP32 */
-  int32_t fem_kind;      /* DDFD_FEM_STENCIL (default) or DDFD_FEM_EBE */
+  int32_t fem_kind;      /* DDFD_FEM_STENCIL (default), DDFD_FEM_EBE or DDFD_FEM_MESH */
   int32_t n_src;         /* incident plane waves, >= 1; J and g sum over them */
   const double *src_dir; /* [n_src][3] propagation directions k (k_z < 0), or NULL
                             for normal incidence k = (0,0,-1); copied */
@@ -107,6 +109,19 @@ typedef struct {
                             0 = library default, else 2..n) */
   int32_t forward_only;  /* nonzero: keep neither the E history nor snapshots (for
                             data generation); ddfd_adjoint then fails with DDFD_E_STATE */
+  /* fem_kind = DDFD_FEM_MESH: the tetrahedra of the FEM cube [a, b]^3, a locally
+     refined mesh (Sec. 4, the adaptive refinement that eq. meshref marks).  Node
+     ids: grid node i + n (j + n k) (inside [a, b]^3), new node e = n^3 + e, the
+     midpoint of its two parents mesh_parents[e] (ids below n^3 + e).  New nodes
+     must lie in the free box [a+2, b-2]^3 and are free nodes: the coefficient
+     arrays list the grid's free nodes (x fastest), then the new nodes.  Rows of
+     the grid nodes strictly inside the cube and of the new nodes are P1 rows
+     over these tetrahedra (lumped masses); the time step must suit the smallest
+     elements.  Not combined with n_snapshots or cfl_check.  Copied. */
+  int32_t mesh_n_new;
+  const int32_t *mesh_parents;   /* [mesh_n_new][2] */
+  int64_t mesh_n_tets;
+  const int32_t *mesh_tets;      /* [mesh_n_tets][4] */
   void *stream;          /* cudaStream_t for all work, or NULL for the default stream */
 } ddfd_config;
 
@@ -224,9 +239,10 @@ int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out);
 int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out);
 
 /* Batched heterogeneous problems.  count (1..256) problems with the same n,
- * n_steps, cfl and precision and the stencil FEM apply, each with its own
- * FEM cube size fem_n, detectors, absorbing faces, regularisation,
- * n_snapshots and one incident plane wave (n_src = 1, src_dir may differ;
+ * n_steps, cfl and precision, each with its own FEM cube size fem_n, FEM
+ * apply (fem_kind; element members add their own gather and new-node
+ * launches around the batched step), detectors, absorbing faces,
+ * regularisation, n_snapshots and one incident plane wave (n_src = 1, src_dir may differ;
  * several waves on one model are several members with the same
  * coefficients).  The members' fields are stacked in one allocation and
  * every time step of the whole batch is one kernel launch per group of 16

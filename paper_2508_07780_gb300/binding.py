@@ -21,7 +21,7 @@ DDFD_OK, DDFD_E_ARG, DDFD_E_CFL, DDFD_E_STATE = 0, -1, -2, -3
 DDFD_E_CUDA, DDFD_E_OOM, DDFD_E_NONFINITE, DDFD_E_TIMEOUT, DDFD_E_COEFF = -4, -5, -6, -7, -8
 DDFD_FP64, DDFD_FP32 = 0, 1
 DDFD_SRC_GAUSS, DDFD_SRC_SINE = 0, 1
-DDFD_FEM_STENCIL, DDFD_FEM_EBE = 0, 1
+DDFD_FEM_STENCIL, DDFD_FEM_EBE, DDFD_FEM_MESH = 0, 1, 2
 DDFD_ABS_BOTTOM, DDFD_ABS_TOP, DDFD_ABS_X0, DDFD_ABS_X1, DDFD_ABS_Y0, DDFD_ABS_Y1 = 1, 2, 4, 8, 16, 32
 
 STATUS_NAMES = {0: "DDFD_OK", -1: "DDFD_E_ARG", -2: "DDFD_E_CFL", -3: "DDFD_E_STATE",
@@ -52,7 +52,8 @@ class ddfd_config(ctypes.Structure):
         ("gamma_sig", c_double), ("z_delta_frac", c_double), ("eps_max", c_double),
         ("sig_max", c_double), ("n_snapshots", c_int32), ("cfl_check", c_int32),
         ("mem_budget", c_int64), ("tile_kz", c_int32), ("forward_only", c_int32),
-        ("stream", c_void_p),
+        ("mesh_n_new", c_int32), ("mesh_parents", POINTER(c_int32)), ("mesh_n_tets", c_int64),
+        ("mesh_tets", POINTER(c_int32)), ("stream", c_void_p),
     ]
 
 
@@ -228,6 +229,16 @@ def make_config(lib, kw, keep):
             keep.append(arr)
             cfg.det_ij = arr.ctypes.data_as(POINTER(c_int32))
             cfg.n_det = arr.shape[0]
+        elif k == "mesh":
+            # (parents [E][2], tets [T][4]): an explicit refined FEM mesh
+            par = _host(v[0], np.int32).reshape(-1, 2)
+            tet = _host(v[1], np.int32).reshape(-1, 4)
+            keep += [par, tet]
+            cfg.fem_kind = DDFD_FEM_MESH
+            cfg.mesh_n_new = par.shape[0]
+            cfg.mesh_parents = par.ctypes.data_as(POINTER(c_int32))
+            cfg.mesh_n_tets = tet.shape[0]
+            cfg.mesh_tets = tet.ctypes.data_as(POINTER(c_int32))
         elif k == "stream":
             cfg.stream = c_void_p(v)
         elif k == "precision" and isinstance(v, str):

@@ -96,6 +96,13 @@ struct ddfd_problem {
   ddfd_batch *batch = nullptr;
   int slot = 0;
   bool fonly = false;         // forward_only: no history, no snapshots, no adjoint
+  // explicit refined FEM mesh (fem_kind = DDFD_FEM_MESH): new nodes keep their
+  // fields and (s, q1, q2) in arrays of their own, [3][n_new]
+  int n_new = 0;
+  long long n_free_grid = 0;  // free grid nodes; new node e is free node n_free_grid + e
+  std::vector<int32_t> mesh_parents, mesh_tets;
+  void *X[2] = {nullptr, nullptr}, *XMu[2] = {nullptr, nullptr}, *xcoef = nullptr;
+  double *mass_free = nullptr;  // lumped mass of every free node (refined meshes)
 };
 
 namespace {
@@ -151,7 +158,22 @@ int validate(const ddfd_config *c, std::string *m) {
   if (c->n_steps < 1) return *m = "n_steps must be >= 1", DDFD_E_ARG;
   if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) return *m = "cfl must be positive", DDFD_E_ARG;
   if (c->precision != DDFD_FP64 && c->precision != DDFD_FP32) return *m = "bad precision", DDFD_E_ARG;
-  if (c->fem_kind != DDFD_FEM_STENCIL && c->fem_kind != DDFD_FEM_EBE) return *m = "bad fem_kind", DDFD_E_ARG;
+  if (c->fem_kind != DDFD_FEM_STENCIL && c->fem_kind != DDFD_FEM_EBE && c->fem_kind != DDFD_FEM_MESH)
+    return *m = "bad fem_kind", DDFD_E_ARG;
+  if (c->fem_kind == DDFD_FEM_MESH) {
+    if (c->mesh_n_new < 0 || c->mesh_n_tets < 1 || !c->mesh_tets || (c->mesh_n_new > 0 && !c->mesh_parents))
+      return *m = "fem_kind DDFD_FEM_MESH needs mesh_tets (and mesh_parents for new nodes)", DDFD_E_ARG;
+    if (c->n_snapshots > 0 || c->cfl_check)
+      return *m = "refined meshes take neither n_snapshots nor cfl_check", DDFD_E_ARG;
+    const long long n3 = (long long)c->n * c->n * c->n;
+    for (int e = 0; e < c->mesh_n_new; ++e)
+      for (int q = 0; q < 2; ++q) {
+        const long long v = c->mesh_parents[2 * e + q];
+        if (v < 0 || v >= n3 + e) return *m = "mesh_parents: a parent must be a grid node or an earlier new node", DDFD_E_ARG;
+      }
+    for (long long t = 0; t < 4 * c->mesh_n_tets; ++t)
+      if (c->mesh_tets[t] < 0 || c->mesh_tets[t] >= n3 + c->mesh_n_new) return *m = "mesh_tets: node id out of range", DDFD_E_ARG;
+  }
   if (c->n_src < 1) return *m = "n_src must be >= 1", DDFD_E_ARG;
   if (c->source_kind != DDFD_SRC_GAUSS && c->source_kind != DDFD_SRC_SINE) return *m = "bad source_kind", DDFD_E_ARG;
   if (!(c->freq > 0.0) || (c->source_kind == DDFD_SRC_GAUSS && !(c->width > 0.0)))
@@ -335,7 +357,8 @@ int capture_slot(const ddfd_problem *p, int step) {
 
 // The element-by-element rows of the current level (fem_kind = DDFD_FEM_EBE).
 template <typename T>
-void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, int64_t *nk) {
+void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, int64_t *nk,
+                 const void *xfield = nullptr) {
   if (!p->ebe_rows) return;
   EbeParams<T> E;
   E.n_rows = p->ebe_rows;
@@ -351,7 +374,37 @@ void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, 
   E.cs = p->cs;
   E.out_r = (T *)p->ebe_out_r;
   E.out_q = (T *)p->ebe_out_q;
+  E.xfield = (const T *)xfield;
+  E.xs = (const T *)p->xcoef;
+  E.n_new = p->n_new;
   launch_ebe<T>(E, adj, sm);
+  ++*nk;
+}
+
+// The new nodes of a refined mesh, one step (after the rows of enqueue_ebe).
+template <typename T>
+void enqueue_new_step(ddfd_problem *p, const void *cur, void *old, bool adj, const StepParams<T> &S,
+                      cudaStream_t sm, int64_t *nk) {
+  if (!p->n_new) return;
+  NewStepParams<T> N;
+  N.n_new = p->n_new;
+  N.row0 = p->ebe_rows - p->n_new;
+  N.ebe_rows = p->ebe_rows;
+  N.ebe_r = (const T *)p->ebe_out_r;
+  N.ebe_q = (const T *)p->ebe_out_q;
+  N.cur = (const T *)cur;
+  N.old = (T *)old;
+  N.xcoef = (const T *)p->xcoef;
+  N.r2 = S.r2;
+  N.n_free = p->n_free;
+  N.f0 = p->n_free_grid;
+  N.hist_w = S.hist_w;
+  N.hist_r = S.hist_r;
+  N.gacc_e = S.gacc_e;
+  N.gacc_s = S.gacc_s;
+  N.gpart = S.gpart;
+  N.gmode = S.gmode;
+  launch_new_step<T>(N, adj, sm);
   ++*nk;
 }
 
@@ -365,6 +418,10 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
   for (int s = 0; s < p->n_src; ++s) {
     CK(cudaMemsetAsync(p->E[0], 0, fbytes, sm));
     CK(cudaMemsetAsync(p->E[1], 0, fbytes, sm));
+    if (p->n_new) {
+      CK(cudaMemsetAsync(p->X[0], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+      CK(cudaMemsetAsync(p->X[1], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+    }
     if (s == 0) {
       const int sl = capture_slot(p, 0);
       if (sl >= 0) CK(cudaMemsetAsync((char *)p->capE + sl * fbytes, 0, fbytes, sm));
@@ -381,8 +438,9 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
       set_forward_step(P, p, s, st, p->E[ic], p->E[io],
                        (p->nsnap || p->fonly) ? nullptr
                                               : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free);
-      enqueue_ebe<T>(p, p->E[ic], false, sm, nk);
+      enqueue_ebe<T>(p, p->E[ic], false, sm, nk, p->X[ic]);
       launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
+      enqueue_new_step<T>(p, p->X[ic], p->X[io], false, P, sm, nk);
       ++*nk;
       std::swap(ic, io);
       if (s == 0) {
@@ -409,6 +467,10 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
   for (int s = 0; s < p->n_src; ++s) {
     CK(cudaMemsetAsync(p->Mu[0], 0, fbytes, sm));
     CK(cudaMemsetAsync(p->Mu[1], 0, fbytes, sm));
+    if (p->n_new) {
+      CK(cudaMemsetAsync(p->XMu[0], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+      CK(cudaMemsetAsync(p->XMu[1], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+    }
     int ic = 1, io = 0;  // buffers holding mu^k and mu^{k+1}
     StepParams<T> P = base_params<T>(p);
     // segments [n0, n1): all of [0, Nt) at once when the whole history is
@@ -441,8 +503,9 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
       }
       for (int k = n1; k >= n0 + 1; --k) {
         set_adjoint_step(P, p, s, k, p->Mu[ic], p->Mu[io], hbase + (size_t)(k - n0) * 3 * p->n_free, Nt);
-        enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk);
+        enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk, p->XMu[ic]);
         launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
+        enqueue_new_step<T>(p, p->XMu[ic], p->XMu[io], true, P, sm, nk);
         ++*nk;
         std::swap(ic, io);
         if (s == 0) {
@@ -716,6 +779,157 @@ int build_ebe(ddfd_problem *p) {
   return DDFD_OK;
 }
 
+// Explicit refined FEM mesh (fem_kind = DDFD_FEM_MESH): node coordinates
+// (new nodes as midpoints of their parents, in FP64), per-tet sqrt|K| g,
+// the incidences of the FEM rows -- the grid nodes strictly inside the cube in
+// the order of build_ebe, then the new nodes -- with their lumped masses, the
+// masses of every free node, and the new nodes' field and coefficient arrays.
+int build_mesh(ddfd_problem *p) {
+  const int a = p->a, b = p->b, n = p->n;
+  const long long n3 = (long long)n * n * n;
+  const int fm = b - a - 1;
+  const long long grid_rows = (long long)fm * fm * fm;
+  const long long rows = grid_rows + p->n_new;
+  const long long ntet = (long long)p->mesh_tets.size() / 4;
+  if (p->cs + (long long)p->n_new >= (1LL << 31) || 4 * ntet >= (1LL << 31))
+    return fail(p, DDFD_E_ARG, "refined mesh too large for 32-bit node offsets");
+  std::vector<double> X((size_t)p->n_new * 3);
+  auto xyz = [&](long long v, double out[3]) {
+    if (v < n3) {
+      out[0] = (double)(v % n) * p->h;
+      out[1] = (double)((v / n) % n) * p->h;
+      out[2] = (double)(v / ((long long)n * n)) * p->h;
+    } else {
+      for (int d = 0; d < 3; ++d) out[d] = X[(size_t)(v - n3) * 3 + d];
+    }
+  };
+  const double lo = (p->f0 - 1e-9) * p->h, hi = (p->f0 + p->nf - 1 + 1e-9) * p->h;
+  for (int e = 0; e < p->n_new; ++e) {
+    double u[3], w[3];
+    xyz(p->mesh_parents[2 * e], u);
+    xyz(p->mesh_parents[2 * e + 1], w);
+    for (int d = 0; d < 3; ++d) {
+      X[(size_t)e * 3 + d] = 0.5 * (u[d] + w[d]);
+      if (!(X[(size_t)e * 3 + d] >= lo && X[(size_t)e * 3 + d] <= hi))
+        return fail(p, DDFD_E_ARG, "mesh: new node " + std::to_string(e) + " outside the free box");
+    }
+  }
+  auto in_cube = [&](long long v) {
+    const long long i = v % n, j = (v / n) % n, k = v / ((long long)n * n);
+    return i >= a && i <= b && j >= a && j <= b && k >= a && k <= b;
+  };
+  auto rowof = [&](long long v) -> long long {
+    if (v >= n3) return grid_rows + (v - n3);
+    const long long i = v % n, j = (v / n) % n, k = v / ((long long)n * n);
+    if (i <= a || i >= b || j <= a || j >= b || k <= a || k >= b) return -1;
+    return (i - a - 1) + (long long)fm * ((j - a - 1) + (long long)fm * (k - a - 1));
+  };
+  auto off = [&](long long v) -> int {
+    if (v >= n3) return (int)(p->cs + (v - n3));
+    const long long i = v % n, j = (v / n) % n, k = v / ((long long)n * n);
+    return (int)(i + (long long)p->px * (j + (long long)n * k));
+  };
+  std::vector<int> tnode((size_t)ntet * 4), rptr((size_t)rows + 1, 0);
+  std::vector<double> tgrad((size_t)ntet * 12), mass((size_t)rows, 0.0);
+  double vol_sum = 0.0;
+  for (long long t = 0; t < ntet; ++t) {
+    double A[4][4], C[4][4];
+    for (int q = 0; q < 4; ++q) {
+      const long long v = p->mesh_tets[t * 4 + q];
+      if (v < n3 && !in_cube(v)) return fail(p, DDFD_E_ARG, "mesh: a grid node outside the FEM cube");
+      double x[3];
+      xyz(v, x);
+      A[q][0] = 1.0;
+      for (int d = 0; d < 3; ++d) A[q][d + 1] = x[d];
+    }
+    if (!invert4(A, C)) return fail(p, DDFD_E_ARG, "mesh: degenerate tetrahedron");
+    double e1[3], e2[3], e3[3];
+    for (int d = 0; d < 3; ++d) {
+      e1[d] = A[1][d + 1] - A[0][d + 1];
+      e2[d] = A[2][d + 1] - A[0][d + 1];
+      e3[d] = A[3][d + 1] - A[0][d + 1];
+    }
+    const double vol = std::fabs(e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                                 e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+    vol_sum += vol;
+    const double sv = std::sqrt(vol);
+    for (int q = 0; q < 4; ++q) {
+      const long long v = p->mesh_tets[t * 4 + q];
+      tnode[t * 4 + q] = off(v);
+      for (int d = 0; d < 3; ++d) tgrad[t * 12 + q * 3 + d] = sv * C[d + 1][q];
+      const long long r = rowof(v);
+      if (r >= 0) {
+        rptr[r + 1]++;
+        mass[r] += vol / 4.0;
+      }
+    }
+  }
+  const double cube = std::pow((b - a) * p->h, 3);
+  if (std::fabs(vol_sum - cube) > 1e-9 * cube)
+    return fail(p, DDFD_E_ARG, "mesh: the tetrahedra do not fill the FEM cube");
+  for (long long r = 0; r < rows; ++r) {
+    if (!(mass[r] > 0.0)) return fail(p, DDFD_E_ARG, "mesh: a FEM row without elements");
+    rptr[r + 1] += rptr[r];
+  }
+  const long long ninc = rptr[rows];
+  std::vector<int> itet((size_t)ninc), iloc((size_t)ninc), fillp(rptr.begin(), rptr.end() - 1), rnode((size_t)rows);
+  std::vector<double> scale((size_t)rows);
+  for (long long t = 0; t < ntet; ++t)
+    for (int q = 0; q < 4; ++q) {
+      const long long r = rowof(p->mesh_tets[t * 4 + q]);
+      if (r >= 0) {
+        itet[fillp[r]] = (int)t;
+        iloc[fillp[r]++] = q;
+      }
+    }
+  for (long long k = a + 1; k < b; ++k)
+    for (long long j = a + 1; j < b; ++j)
+      for (long long i = a + 1; i < b; ++i) {
+        const long long v = i + n * (j + n * k);
+        rnode[rowof(v)] = off(v);
+      }
+  for (int e = 0; e < p->n_new; ++e) rnode[grid_rows + e] = off(n3 + e);
+  for (long long r = 0; r < rows; ++r) scale[r] = p->h * p->h / mass[r];
+  // lumped masses of the free nodes: grid free nodes, then the new nodes
+  std::vector<double> mfree((size_t)p->n_free);
+  for (long long f = 0; f < p->n_free_grid; ++f) {
+    const long long li = f % p->nf, lj = (f / p->nf) % p->nf, lk = f / ((long long)p->nf * p->nf);
+    mfree[f] = mass[rowof((p->f0 + li) + n * ((p->f0 + lj) + (long long)n * (p->f0 + lk)))];
+  }
+  for (int e = 0; e < p->n_new; ++e) mfree[p->n_free_grid + e] = mass[grid_rows + e];
+  int st;
+  const size_t es = p->esz, xb = 3 * (size_t)std::max(p->n_new, 1) * es;
+  if ((st = dalloc_t(p, (size_t)rows, &p->ebe_row_node)) || (st = dalloc_t(p, (size_t)rows + 1, &p->ebe_row_ptr)) ||
+      (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_tet)) || (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_local)) ||
+      (st = dalloc_t(p, (size_t)ntet * 4, &p->ebe_tet_node)) || (st = dalloc(p, (size_t)ntet * 12 * es, &p->ebe_tet_grad)) ||
+      (st = dalloc_t(p, (size_t)rows, &p->ebe_scale)) || (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_r)) ||
+      (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_q)) || (st = dalloc_t(p, (size_t)p->n_free, &p->mass_free)) ||
+      (st = dalloc(p, xb, &p->X[0])) || (st = dalloc(p, xb, &p->X[1])) || (st = dalloc(p, xb, &p->xcoef)) ||
+      (!p->fonly && ((st = dalloc(p, xb, &p->XMu[0])) || (st = dalloc(p, xb, &p->XMu[1])))))
+    return st;
+  std::vector<float> tgf;
+  const void *gsrc = tgrad.data();
+  if (p->fp32) {
+    tgf.assign(tgrad.begin(), tgrad.end());
+    gsrc = tgf.data();
+  }
+  CK(cudaMemcpy(p->ebe_row_node, rnode.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_row_ptr, rptr.data(), (rows + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_inc_tet, itet.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_inc_local, iloc.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_tet_node, tnode.data(), ntet * 4 * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_tet_grad, gsrc, ntet * 12 * es, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_scale, scale.data(), rows * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->mass_free, mfree.data(), p->n_free * sizeof(double), cudaMemcpyHostToDevice));
+  for (int q = 0; q < 2; ++q) {
+    CK(cudaMemset(p->X[q], 0, xb));
+    if (p->XMu[q]) CK(cudaMemset(p->XMu[q], 0, xb));
+  }
+  CK(cudaMemset(p->xcoef, 0, xb));
+  p->ebe_rows = (int)rows;
+  return DDFD_OK;
+}
+
 int build_maps(ddfd_problem *p) {
   FieldMaps fm;
   const int st = encode_field_maps(&p->err, &fm, p->E, p->Mu, p->kcoef, p->n, p->px, p->fp32, 1);
@@ -769,8 +983,13 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
   if (st) return st;
   if (flag) return fail(p, DDFD_E_COEFF, "coefficient outside [1, eps_max] x [0, sig_max] or non-finite");
   CK(cudaMemcpyAsync(p->coef, p->coef_stage, 4 * nfb, cudaMemcpyDeviceToDevice, p->stream));
-  launch_expand_coeffs(p->fp32, p->coef, p->nf, p->f0, p->n, p->px, p->cs, p->tau, p->kcoef, p->stream);
+  launch_expand_coeffs(p->fp32, p->coef, p->nf, p->f0, p->n, p->px, p->cs, p->tau, p->kcoef, p->stream,
+                       p->n_free);
   ++p->launches;
+  if (p->n_new) {
+    launch_expand_new(p->fp32, p->coef, p->n_free, p->n_free_grid, p->n_new, p->tau, p->xcoef, p->stream);
+    ++p->launches;
+  }
   p->state = ST_READY;
   if (p->cfg.cfl_check) {
     st = cfl_check(p);
@@ -808,7 +1027,7 @@ int functional_impl(ddfd_problem *p, const double *eobs, double *J, bool host) {
   }
   launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
   launch_sum(p->part, p->n_part, p->scal, p->stream);
-  launch_regulariser(p->coef, (int)p->n_free, p->part, p->n_part, p->stream);
+  launch_regulariser(p->coef, (int)p->n_free, p->part, p->n_part, p->stream, p->mass_free);
   launch_sum(p->part, p->n_part, p->scal + 1, p->stream);
   launch_sum(p->part + p->n_part, p->n_part, p->scal + 2, p->stream);
   p->launches += 5;
@@ -816,7 +1035,7 @@ int functional_impl(ddfd_problem *p, const double *eobs, double *J, bool host) {
   CK(cudaMemcpyAsync(v, p->scal, sizeof(v), cudaMemcpyDeviceToHost, p->stream));
   int st = sync_check(p);
   if (st) return st;
-  const double m = p->h * p->h * p->h;
+  const double m = p->mass_free ? 1.0 : p->h * p->h * p->h;  // with per-node masses the sums carry them
   const double Jv = 0.5 * p->tau * v[0] + 0.5 * p->cfg.gamma_eps * m * v[1] + 0.5 * p->cfg.gamma_sig * m * v[2];
   if (!std::isfinite(Jv)) return fail(p, DDFD_E_NONFINITE, "non-finite functional");
   *J = Jv;
@@ -850,8 +1069,13 @@ int gradient_impl(ddfd_problem *p, double *g_eps, double *g_sig, bool host) {
   const double m = p->h * p->h * p->h;
   double *ge = host ? p->gout : g_eps;
   double *gs = host ? p->gout + p->n_free : g_sig;
-  launch_grad_finalize(p->coef, (int)p->n_free, p->gacc, p->gacc + p->n_free, m / (p->tau * p->tau),
-                       m / (2.0 * p->tau), m, p->cfg.gamma_eps, p->cfg.gamma_sig, ge, gs, p->stream);
+  if (p->mass_free)
+    launch_grad_finalize(p->coef, (int)p->n_free, p->gacc, p->gacc + p->n_free, 1.0 / (p->tau * p->tau),
+                         1.0 / (2.0 * p->tau), m, p->cfg.gamma_eps, p->cfg.gamma_sig, ge, gs, p->stream,
+                         p->mass_free);
+  else
+    launch_grad_finalize(p->coef, (int)p->n_free, p->gacc, p->gacc + p->n_free, m / (p->tau * p->tau),
+                         m / (2.0 * p->tau), m, p->cfg.gamma_eps, p->cfg.gamma_sig, ge, gs, p->stream);
   CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream));
   launch_nonfinite(ge, p->n_free, p->flag, p->stream);
   launch_nonfinite(gs, p->n_free, p->flag, p->stream);
@@ -934,6 +1158,13 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   ddfd_problem *p = new ddfd_problem();
   p->cfg = *cfg;
   if (cfg->src_dir) p->src_dir.assign(cfg->src_dir, cfg->src_dir + 3 * cfg->n_src);
+  if (cfg->fem_kind == DDFD_FEM_MESH) {
+    p->mesh_parents.assign(cfg->mesh_parents, cfg->mesh_parents + 2 * (size_t)cfg->mesh_n_new);
+    p->mesh_tets.assign(cfg->mesh_tets, cfg->mesh_tets + 4 * (size_t)cfg->mesh_n_tets);
+    p->n_new = cfg->mesh_n_new;
+  }
+  p->cfg.mesh_parents = nullptr;
+  p->cfg.mesh_tets = nullptr;
   if (cfg->n_det > 0) p->det_ij.assign(cfg->det_ij, cfg->det_ij + 2 * cfg->n_det);
   p->cfg.src_dir = nullptr;
   p->cfg.det_ij = nullptr;
@@ -943,7 +1174,8 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   p->b = p->a + cfg->fem_n - 1;
   p->f0 = p->a + 2;
   p->nf = cfg->fem_n - 4;
-  p->n_free = (long long)p->nf * p->nf * p->nf;
+  p->n_free_grid = (long long)p->nf * p->nf * p->nf;
+  p->n_free = p->n_free_grid + p->n_new;
   p->nn = (long long)p->n * p->n * p->n;
   p->px = (p->n + 7) / 8 * 8;
   p->cs = (long long)p->px * p->n * p->n;
@@ -1071,6 +1303,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   }
   if ((st = build_maps(p))) return bail(st);
   if (cfg->fem_kind == DDFD_FEM_EBE && (st = build_ebe(p))) return bail(st);
+  if (cfg->fem_kind == DDFD_FEM_MESH && (st = build_mesh(p))) return bail(st);
   // vacuum coefficients
   std::vector<double> one((size_t)p->n_free, 1.0), zero((size_t)p->n_free, 0.0);
   const bool chk = p->cfg.cfl_check != 0;
@@ -1332,7 +1565,7 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
   for (int st = 0; st < steps; ++st) {
     set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
                      p->fonly ? nullptr : (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
-    enqueue_ebe<T>(p, p->E[ic], false, sm, &nk);
+    enqueue_ebe<T>(p, p->E[ic], false, sm, &nk, p->X[ic]);
     launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
     std::swap(ic, io);
   }
@@ -1340,7 +1573,7 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
   for (int k = p->fonly ? 0 : steps; k >= 1; --k) {  // forward_only handles time the forward alone
     set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free,
                      steps);
-    enqueue_ebe<T>(p, p->Mu[ic], true, sm, &nk);
+    enqueue_ebe<T>(p, p->Mu[ic], true, sm, &nk, p->XMu[ic]);
     launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
     std::swap(ic, io);
   }
@@ -1398,6 +1631,11 @@ int enqueue_batch_forward(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
   *nk = 0;
   BCK(cudaMemsetAsync(b->E[0], 0, slab, sm));
   BCK(cudaMemsetAsync(b->E[1], 0, slab, sm));
+  for (ddfd_problem *p : b->m)
+    if (p->n_new) {
+      BCK(cudaMemsetAsync(p->X[0], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+      BCK(cudaMemsetAsync(p->X[1], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+    }
   const std::vector<int> all = all_members(b);
   int ic = 1, io = 0;
   for (int st = 0; st < Nt; ++st) {
@@ -1407,13 +1645,19 @@ int enqueue_batch_forward(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
         BCK(cudaMemcpyAsync(sn, p->E[ic], fbytes, cudaMemcpyDeviceToDevice, sm));
         BCK(cudaMemcpyAsync(sn + fbytes, p->E[io], fbytes, cudaMemcpyDeviceToDevice, sm));
       }
-    launch_groups<T>(
-        b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io],
-        [&](StepParams<T> &P, ddfd_problem *p) {
-          set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
-                           (p->nsnap || p->fonly) ? nullptr : (T *)p->hist + (size_t)(st + 1) * 3 * p->n_free);
-        },
-        sm, nk);
+    auto fill = [&](StepParams<T> &P, ddfd_problem *p) {
+      set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
+                       (p->nsnap || p->fonly) ? nullptr : (T *)p->hist + (size_t)(st + 1) * 3 * p->n_free);
+    };
+    // element-by-element members: their FEM rows of this level first
+    for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->E[ic], false, sm, nk, p->X[ic]);
+    launch_groups<T>(b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io], fill, sm, nk);
+    for (ddfd_problem *p : b->m)
+      if (p->n_new) {
+        StepParams<T> P = base_params<T>(p);
+        fill(P, p);
+        enqueue_new_step<T>(p, p->X[ic], p->X[io], false, P, sm, nk);
+      }
     std::swap(ic, io);
   }
   BCK(cudaGetLastError());
@@ -1434,6 +1678,11 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
   for (ddfd_problem *p : b->m) BCK(cudaMemsetAsync(p->gacc, 0, 2 * (size_t)p->n_free * sizeof(double), sm));
   BCK(cudaMemsetAsync(b->Mu[0], 0, slab, sm));
   BCK(cudaMemsetAsync(b->Mu[1], 0, slab, sm));
+  for (ddfd_problem *p : b->m)
+    if (p->n_new) {
+      BCK(cudaMemsetAsync(p->XMu[0], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+      BCK(cudaMemsetAsync(p->XMu[1], 0, 3 * (size_t)p->n_new * sizeof(T), sm));
+    }
   const std::vector<int> all = all_members(b);
   std::vector<int> ck;  // checkpointing members: replayed segment by segment
   for (size_t i = 0; i < b->m.size(); ++i)
@@ -1453,6 +1702,7 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
       }
       int fc = 1, fo = 0;
       for (int st = n0; st < n1; ++st) {
+        for (int i : ck) enqueue_ebe<T>(b->m[i], b->m[i]->E[fc], false, sm, nk, b->m[i]->X[fc]);
         launch_groups<T>(
             b, false, ck, b->maps.E_halo[fc], b->maps.E_ctr[fo],
             [&](StepParams<T> &P, ddfd_problem *p) {
@@ -1463,13 +1713,18 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
       }
     }
     for (int k = n1; k >= n0 + 1; --k) {
-      launch_groups<T>(
-          b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io],
-          [&](StepParams<T> &P, ddfd_problem *p) {
-            const long long hk = p->nsnap ? k - n0 : k;
-            set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free, Nt);
-          },
-          sm, nk);
+      auto fill = [&](StepParams<T> &P, ddfd_problem *p) {
+        const long long hk = p->nsnap ? k - n0 : k;
+        set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free, Nt);
+      };
+      for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk, p->XMu[ic]);
+      launch_groups<T>(b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io], fill, sm, nk);
+      for (ddfd_problem *p : b->m)
+        if (p->n_new) {
+          StepParams<T> P = base_params<T>(p);
+          fill(P, p);
+          enqueue_new_step<T>(p, p->XMu[ic], p->XMu[io], true, P, sm, nk);
+        }
       std::swap(ic, io);
     }
   }
@@ -1653,7 +1908,8 @@ int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *
   ddfd_problem *p0 = b->m[0];
   for (size_t i = 0; i < b->m.size(); ++i) {
     const ddfd_problem *p = b->m[i];
-    if (p->fem_n != p0->fem_n) return bfail(b, DDFD_E_ARG, "CG members must share fem_n");
+    if (p->fem_n != p0->fem_n || p->n_free != p0->n_free || p->n_new != p0->n_new)
+      return bfail(b, DDFD_E_ARG, "CG members must share fem_n (and their refined mesh)");
     if (p->cfg.gamma_eps != 0.0 || p->cfg.gamma_sig != 0.0)
       return bfail(b, DDFD_E_ARG, "CG members must have gamma_eps = gamma_sig = 0 (the CG regularises)");
     if (p->fonly) return bfail(b, DDFD_E_ARG, "CG members cannot be forward_only");
@@ -1694,7 +1950,11 @@ int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *
     if (cnt > 0) BCK(cudaMemcpyAsync(p->eobs_stage, eobs[i], cnt * sizeof(double), cudaMemcpyHostToDevice, sm));
     eobs_dev[i] = p->eobs_stage;
   }
-  const double m = p0->h * p0->h * p0->h;  // lumped mass of a free node
+  // lumped mass of a free node (uniform mesh), or per-node masses carried by
+  // the reductions themselves (refined mesh: m = 1 on the host)
+  const double *mass = p0->mass_free;
+  const double hm = p0->h * p0->h * p0->h;
+  const double m = mass ? 1.0 : hm;
   double gam_e = prm->gamma_eps0, gam_s = prm->gamma_sig0;
   double alp_e = prm->alpha_eps0, alp_s = prm->alpha_sig0;
   double gg_e_prev = 0.0, gg_s_prev = 0.0;
@@ -1719,7 +1979,8 @@ int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *
       if ((st = gradient_impl(b->m[i], first ? Ge : Te, first ? Gs : Ts, false))) return bfail(b, st, b->m[i]->err);
       if (!first) launch_cg_accum(Ge, Gs, Te, Ts, n, sm);
     }
-    launch_cg_grad(Ge, Gs, eps, sig, re, rs, 1.0 / m, gam_e, gam_s, gte, gts, de, ds, it > 0, n, part, out, sm);
+    launch_cg_grad(Ge, Gs, eps, sig, re, rs, 1.0 / hm, gam_e, gam_s, gte, gts, de, ds, it > 0, n, part, out, sm,
+                   mass);
     double r4[6];
     BCK(cudaMemcpyAsync(r4, out, sizeof(r4), cudaMemcpyDeviceToHost, sm));
     BCK(cudaStreamSynchronize(sm));
@@ -1732,7 +1993,7 @@ int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *
     if (prm->restart && it > 0 && -gg_e + beta_e * m * r4[4] >= 0.0) beta_e = 0.0;
     if (prm->restart && it > 0 && -gg_s + beta_s * m * r4[5] >= 0.0) beta_s = 0.0;
     launch_cg_update(gte, gts, de, ds, beta_e, beta_s, alp_e, alp_s, eps, sig, eps_n, sig_n, prm->eps_max,
-                     prm->sig_max, it == 0, n, part, out, sm);
+                     prm->sig_max, it == 0, n, part, out, sm, mass);
     double r6[6];
     BCK(cudaMemcpyAsync(r6, out, sizeof(r6), cudaMemcpyDeviceToHost, sm));
     BCK(cudaEventRecord(b->ev[1], sm));
@@ -1844,8 +2105,8 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
       g_create_err = "member " + std::to_string(i) + ": n, n_steps, cfl and precision must match member 0";
       return DDFD_E_ARG;
     }
-    if (c.n_src != 1 || c.fem_kind != DDFD_FEM_STENCIL) {
-      g_create_err = "member " + std::to_string(i) + ": batch members take one source and the stencil FEM apply";
+    if (c.n_src != 1) {
+      g_create_err = "member " + std::to_string(i) + ": batch members take one source";
       return DDFD_E_ARG;
     }
     if (c.n_snapshots > 0) {

@@ -54,13 +54,14 @@ void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const
 // so that the step update reads E^{n+1} = E^n + q1 (E^n - E^{n-1}) - q2 tau^2 R.
 // Vacuum nodes hold s = 0, q1 = q2 = 1 (set once at creation).
 template <typename T>
-__global__ void k_expand(const double *coef, int nf, int f0, int n, int px, long long cs, double tau, T *out) {
+__global__ void k_expand(const double *coef, int nf, int f0, int n, int px, long long cs, double tau, T *out,
+                         long long stride) {
   const long long n_free = (long long)nf * nf * nf;
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n_free;
        f += (long long)gridDim.x * blockDim.x) {
     const int li = (int)(f % nf), lj = (int)((f / nf) % nf), lk = (int)(f / ((long long)nf * nf));
     const long long off = (f0 + li) + (long long)px * ((f0 + lj) + (long long)n * (f0 + lk));
-    const double eps = coef[f], c = coef[n_free + f] * tau * 0.5;
+    const double eps = coef[f], c = coef[stride + f] * tau * 0.5;
     out[off] = (T)(eps - 1.0);
     out[cs + off] = (T)((eps - c) / (eps + c));
     out[2 * cs + off] = (T)(1.0 / (eps + c));
@@ -88,13 +89,35 @@ void launch_coef_vacuum(int fp32, long long cs, void *coef, cudaStream_t s) {
 }
 
 void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int n, int px,
-                          long long cs, double tau, void *coef, cudaStream_t s) {
+                          long long cs, double tau, void *coef, cudaStream_t s, long long stride) {
   const long long nfree = (long long)nf * nf * nf;
+  if (stride < 0) stride = nfree;
   const int blocks = (int)((nfree + 255) / 256 < 4096 ? (nfree + 255) / 256 : 4096);
   if (fp32)
-    k_expand<float><<<blocks, 256, 0, s>>>(coef_free, nf, f0, n, px, cs, tau, (float *)coef);
+    k_expand<float><<<blocks, 256, 0, s>>>(coef_free, nf, f0, n, px, cs, tau, (float *)coef, stride);
   else
-    k_expand<double><<<blocks, 256, 0, s>>>(coef_free, nf, f0, n, px, cs, tau, (double *)coef);
+    k_expand<double><<<blocks, 256, 0, s>>>(coef_free, nf, f0, n, px, cs, tau, (double *)coef, stride);
+}
+
+template <typename T>
+__global__ void k_expand_new(const double *coef, long long stride, long long first, int n_new, double tau,
+                             T *out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_new; e += gridDim.x * blockDim.x) {
+    const double eps = coef[first + e], c = coef[stride + first + e] * tau * 0.5;
+    out[e] = (T)(eps - 1.0);
+    out[n_new + e] = (T)((eps - c) / (eps + c));
+    out[2 * n_new + e] = (T)(1.0 / (eps + c));
+  }
+}
+
+void launch_expand_new(int fp32, const double *coef_free, long long stride, long long first, int n_new,
+                       double tau, void *xcoef, cudaStream_t s) {
+  if (n_new <= 0) return;
+  const int blocks = (n_new + 255) / 256 < 1024 ? (n_new + 255) / 256 : 1024;
+  if (fp32)
+    k_expand_new<float><<<blocks, 256, 0, s>>>(coef_free, stride, first, n_new, tau, (float *)xcoef);
+  else
+    k_expand_new<double><<<blocks, 256, 0, s>>>(coef_free, stride, first, n_new, tau, (double *)xcoef);
 }
 
 __global__ void k_check(const double *coef, int n_free, double eps_max, double sig_max, int *flag) {
@@ -141,13 +164,14 @@ void launch_residual(const double *trace, const double *eobs, const double *z, i
 }
 
 // sum_f (eps - eps0)^2 into part[0..n_part), sum_f (sig - sig0)^2 into part[n_part..2 n_part)
-__global__ void k_regul(const double *coef, int n_free, double *part, int n_part) {
+__global__ void k_regul(const double *coef, int n_free, double *part, int n_part, const double *mass) {
   double ae = 0.0, as = 0.0;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n_free; f += gridDim.x * blockDim.x) {
     const double de = coef[f] - coef[2 * n_free + f];
     const double ds = coef[n_free + f] - coef[3 * n_free + f];
-    ae += de * de;
-    as += ds * ds;
+    const double w = mass ? mass[f] : 1.0;
+    ae += w * de * de;
+    as += w * ds * ds;
   }
   const double be = block_sum(ae);
   const double bs = block_sum(as);
@@ -157,8 +181,9 @@ __global__ void k_regul(const double *coef, int n_free, double *part, int n_part
   }
 }
 
-void launch_regulariser(const double *coef_free, int n_free, double *part, int n_part, cudaStream_t s) {
-  k_regul<<<n_part, RB, 0, s>>>(coef_free, n_free, part, n_part);
+void launch_regulariser(const double *coef_free, int n_free, double *part, int n_part, cudaStream_t s,
+                        const double *mass) {
+  k_regul<<<n_part, RB, 0, s>>>(coef_free, n_free, part, n_part, mass);
 }
 
 __global__ void k_sum(const double *part, int n_part, double *out) {
@@ -172,22 +197,30 @@ void launch_sum(const double *part, int n_part, double *out, cudaStream_t s) {
   k_sum<<<1, RB, 0, s>>>(part, n_part, out);
 }
 
+// With mass (refined meshes), node f has lumped mass mass[f] and the scales
+// are given per unit mass; without it, every free node has mass m.
 __global__ void k_grad_final(const double *coef, int n_free, const double *ge, const double *gs,
                              double ge_scale, double gs_scale, double m, double gam_e, double gam_s,
-                             double *g_eps, double *g_sig) {
+                             double *g_eps, double *g_sig, const double *mass) {
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n_free; f += gridDim.x * blockDim.x) {
-    g_eps[f] = gam_e * m * (coef[f] - coef[2 * n_free + f]) + ge_scale * ge[f];
-    g_sig[f] = gam_s * m * (coef[n_free + f] - coef[3 * n_free + f]) + gs_scale * gs[f];
+    if (mass) {
+      const double mf = mass[f];
+      g_eps[f] = gam_e * mf * (coef[f] - coef[2 * n_free + f]) + mf * ge_scale * ge[f];
+      g_sig[f] = gam_s * mf * (coef[n_free + f] - coef[3 * n_free + f]) + mf * gs_scale * gs[f];
+    } else {
+      g_eps[f] = gam_e * m * (coef[f] - coef[2 * n_free + f]) + ge_scale * ge[f];
+      g_sig[f] = gam_s * m * (coef[n_free + f] - coef[3 * n_free + f]) + gs_scale * gs[f];
+    }
   }
 }
 
 void launch_grad_finalize(const double *coef_free, int n_free, const double *gacc_e,
                           const double *gacc_s, double ge_scale, double gs_scale, double m,
                           double gamma_e, double gamma_s, double *g_eps, double *g_sig,
-                          cudaStream_t s) {
+                          cudaStream_t s, const double *mass) {
   const int blocks = (n_free + 255) / 256 < 2048 ? (n_free + 255) / 256 : 2048;
   k_grad_final<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(coef_free, n_free, gacc_e, gacc_s, ge_scale,
-                                                       gs_scale, m, gamma_e, gamma_s, g_eps, g_sig);
+                                                       gs_scale, m, gamma_e, gamma_s, g_eps, g_sig, mass);
 }
 
 __global__ void k_nonfinite(const double *x, long long count, int *flag) {

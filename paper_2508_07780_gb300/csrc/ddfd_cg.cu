@@ -41,24 +41,28 @@ __global__ void k_cg_accum(double *ge, double *gs, const double *te, const doubl
 
 // g = G / m + gamma (x - x_ref) for eps and sigma; partial sums of g_e^2, g_s^2,
 // (eps - ref)^2, (sig - ref)^2 and, when use_d, (g, d_prev) for eps and sigma.
+// With mass (refined meshes) node i has lumped mass mass[i]: the
+// representative divides by it and the sums carry it as their weight;
+// without it every node has mass 1/inv_m and the host scales the sums.
 __global__ void k_cg_grad(const double *Ge, const double *Gs, const double *eps, const double *sig,
                           const double *re, const double *rs, double inv_m, double gam_e, double gam_s,
                           double *gte, double *gts, const double *dpe, const double *dps, int use_d, long long n,
-                          double *part) {
+                          double *part, const double *mass) {
   double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double w = mass ? mass[i] : 1.0, im = mass ? 1.0 / mass[i] : inv_m;
     const double de = eps[i] - re[i], ds = sig[i] - rs[i];
-    const double a = Ge[i] * inv_m + gam_e * de;
-    const double b = Gs[i] * inv_m + gam_s * ds;
+    const double a = Ge[i] * im + gam_e * de;
+    const double b = Gs[i] * im + gam_s * ds;
     gte[i] = a;
     gts[i] = b;
-    v[0] += a * a;
-    v[1] += b * b;
-    v[2] += de * de;
-    v[3] += ds * ds;
+    v[0] += w * a * a;
+    v[1] += w * b * b;
+    v[2] += w * de * de;
+    v[3] += w * ds * ds;
     if (use_d) {
-      v[4] += a * dpe[i];
-      v[5] += b * dps[i];
+      v[4] += w * a * dpe[i];
+      v[5] += w * b * dps[i];
     }
   }
   block_partials<6>(v, part);
@@ -69,9 +73,10 @@ __global__ void k_cg_grad(const double *Ge, const double *Gs, const double *eps,
 __global__ void k_cg_update(const double *gte, const double *gts, double *de, double *ds, double beta_e,
                             double beta_s, double alpha_e, double alpha_s, const double *eps, const double *sig,
                             double *eps_new, double *sig_new, double eps_max, double sig_max, int first,
-                            long long n, double *part) {
+                            long long n, double *part, const double *mass) {
   double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double w = mass ? mass[i] : 1.0;
     const double ge = gte[i], gs = gts[i];
     const double d1 = first ? -ge : -ge + beta_e * de[i];
     const double d2 = first ? -gs : -gs + beta_s * ds[i];
@@ -81,12 +86,12 @@ __global__ void k_cg_update(const double *gte, const double *gts, double *de, do
     const double s1 = fmin(fmax(sig[i] + alpha_s * d2, 0.0), sig_max);
     eps_new[i] = e1;
     sig_new[i] = s1;
-    v[0] += ge * d1;
-    v[1] += d1 * d1;
-    v[2] += (e1 - eps[i]) * (e1 - eps[i]);
-    v[3] += gs * d2;
-    v[4] += d2 * d2;
-    v[5] += (s1 - sig[i]) * (s1 - sig[i]);
+    v[0] += w * ge * d1;
+    v[1] += w * d1 * d1;
+    v[2] += w * (e1 - eps[i]) * (e1 - eps[i]);
+    v[3] += w * gs * d2;
+    v[4] += w * d2 * d2;
+    v[5] += w * (s1 - sig[i]) * (s1 - sig[i]);
   }
   block_partials<6>(v, part);
 }
@@ -111,18 +116,18 @@ void launch_cg_accum(double *ge, double *gs, const double *te, const double *ts,
 void launch_cg_grad(const double *Ge, const double *Gs, const double *eps, const double *sig, const double *re,
                     const double *rs, double inv_m, double gam_e, double gam_s, double *gte, double *gts,
                     const double *dpe, const double *dps, int use_d, long long n, double *part, double *out,
-                    cudaStream_t s) {
+                    cudaStream_t s, const double *mass) {
   k_cg_grad<<<CG_BLOCKS, CG_THREADS, 0, s>>>(Ge, Gs, eps, sig, re, rs, inv_m, gam_e, gam_s, gte, gts, dpe, dps,
-                                             use_d, n, part);
+                                             use_d, n, part, mass);
   k_cg_sum<<<6, 32, 0, s>>>(part, CG_BLOCKS, 6, out);
 }
 
 void launch_cg_update(const double *gte, const double *gts, double *de, double *ds, double beta_e, double beta_s,
                       double alpha_e, double alpha_s, const double *eps, const double *sig, double *eps_new,
                       double *sig_new, double eps_max, double sig_max, int first, long long n, double *part,
-                      double *out, cudaStream_t s) {
+                      double *out, cudaStream_t s, const double *mass) {
   k_cg_update<<<CG_BLOCKS, CG_THREADS, 0, s>>>(gte, gts, de, ds, beta_e, beta_s, alpha_e, alpha_s, eps, sig,
-                                               eps_new, sig_new, eps_max, sig_max, first, n, part);
+                                               eps_new, sig_new, eps_max, sig_max, first, n, part, mass);
   k_cg_sum<<<6, 32, 0, s>>>(part, CG_BLOCKS, 6, out);
 }
 

@@ -149,9 +149,39 @@ struct EbeParams {
   long long cs;             // component stride
   T *out_r;                 // [3][n_rows] h^2 M^-1 (K E) or (K^T mu)
   T *out_q;                 // [3][n_rows] adjoint: h^2 M^-1 (D^T D mu)
+  // refined meshes: a node offset >= cs names new node (offset - cs), whose
+  // field and s are xfield[c * n_new + e], xs[e]
+  const T *xfield;
+  const T *xs;
+  int n_new;
 };
 template <typename T>
 void launch_ebe(const EbeParams<T> &P, bool adj, cudaStream_t s);
+
+// Update of the new nodes of a refined FEM mesh (their rows are FEM rows
+// computed by k_ebe; interior nodes: no boundary or source terms), with the
+// history writes (forward) or the gradient accumulation (adjoint) of the
+// step kernels.
+template <typename T>
+struct NewStepParams {
+  int n_new;
+  int row0;              // row of new node 0 in ebe_r / ebe_q
+  int ebe_rows;          // component stride of ebe_r / ebe_q
+  const T *ebe_r, *ebe_q;
+  const T *cur;          // [3][n_new] E^n (forward) or mu^k (adjoint)
+  T *old;                // [3][n_new] in: E^{n-1} / mu^{k+1}, out: E^{n+1} / mu^{k-1}
+  const T *xcoef;        // [3][n_new] (s, q1, q2)
+  T r2;
+  long long n_free;      // history / accumulator stride
+  long long f0;          // free-node index of new node 0
+  T *hist_w;
+  const T *hist_r;
+  double *gacc_e, *gacc_s;
+  float *gpart;
+  int gmode;
+};
+template <typename T>
+void launch_new_step(const NewStepParams<T> &P, bool adj, cudaStream_t s);
 
 // Small kernels.
 void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const int *det_node,
@@ -159,7 +189,11 @@ void launch_gather_trace(const void *E, int fp32, long long cs, int n_det, const
 // (s, q1, q2) of the free nodes into the padded full-grid coefficient field;
 // launch_coef_vacuum sets every node to the vacuum values (0, 1, 1) first.
 void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int n, int px,
-                          long long cs, double tau, void *coef, cudaStream_t s);
+                          long long cs, double tau, void *coef, cudaStream_t s, long long stride = -1);
+// (s, q1, q2) of the new nodes of a refined mesh: free entries first .. first+n_new-1
+// of the coefficient array (stride n_free between eps and sigma) into xcoef [3][n_new]
+void launch_expand_new(int fp32, const double *coef_free, long long stride, long long first, int n_new,
+                       double tau, void *xcoef, cudaStream_t s);
 void launch_coef_vacuum(int fp32, long long cs, void *coef, cudaStream_t s);
 void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, double sig_max,
                          int *flag, cudaStream_t s);
@@ -169,12 +203,12 @@ void launch_residual(const double *trace, const double *eobs, const double *z, i
                      int n_det, int n_src, double tau, double *res, double *part, int n_part,
                      cudaStream_t s);
 void launch_regulariser(const double *coef_free, int n_free, double *part, int n_part,
-                        cudaStream_t s);
+                        cudaStream_t s, const double *mass = nullptr);
 void launch_sum(const double *part, int n_part, double *out, cudaStream_t s);
 void launch_grad_finalize(const double *coef_free, int n_free, const double *gacc_e,
                           const double *gacc_s, double ge_scale, double gs_scale, double m,
                           double gamma_e, double gamma_s, double *g_eps, double *g_sig,
-                          cudaStream_t s);
+                          cudaStream_t s, const double *mass = nullptr);
 void launch_nonfinite(const double *x, long long count, int *flag, cudaStream_t s);
 // power iteration helpers (FP64): y = M_eps^-1 K x, and the squared norm.
 void launch_apply_op(const double *x, double *y, int n, int px, int a, int b, const void *coef_s, int fp32,
@@ -189,10 +223,10 @@ void launch_cg_accum(double *ge, double *gs, const double *te, const double *ts,
 void launch_cg_grad(const double *Ge, const double *Gs, const double *eps, const double *sig, const double *re,
                     const double *rs, double inv_m, double gam_e, double gam_s, double *gte, double *gts,
                     const double *dpe, const double *dps, int use_d, long long n, double *part, double *out,
-                    cudaStream_t s);
+                    cudaStream_t s, const double *mass = nullptr);
 void launch_cg_update(const double *gte, const double *gts, double *de, double *ds, double beta_e, double beta_s,
                       double alpha_e, double alpha_s, const double *eps, const double *sig, double *eps_new,
                       double *sig_new, double eps_max, double sig_max, int first, long long n, double *part,
-                      double *out, cudaStream_t s);
+                      double *out, cudaStream_t s, const double *mass = nullptr);
 
 }  // namespace ddfd

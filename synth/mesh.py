@@ -214,3 +214,34 @@ def refined_fem_mesh(n: int, fem_n: int, eps_free, sig_free, beta_eps: float = 0
     marked = [ti for ti in marked_all if ti in inner_set]
     mesh.refine_marked(marked, levels)
     return mesh.result()
+
+
+def extend_to_new_nodes(n: int, fem_n: int, parents, eps_free, sig_free):
+    """Coefficients on the free nodes of a refined mesh: the grid's free nodes
+    (x fastest) followed by the new nodes, each the mean of its parents (the
+    P1 interpolant at an edge midpoint, the interpolation onto the refined
+    mesh of Sec. 4)."""
+    a = (n - fem_n) // 2
+    f0, f1 = a + 2, a + fem_n - 3
+    nf = f1 - f0 + 1
+    n3 = n ** 3
+    E = np.asarray(eps_free, dtype=np.float64).reshape(nf, nf, nf)
+    S = np.asarray(sig_free, dtype=np.float64).reshape(nf, nf, nf)
+    parents = np.asarray(parents, dtype=np.int64).reshape(-1, 2)
+    ne = np.empty(parents.shape[0])
+    ns = np.empty(parents.shape[0])
+
+    def value(v):
+        if v >= n3:
+            return ne[v - n3], ns[v - n3]
+        i, j, k = v % n, (v // n) % n, v // (n * n)
+        if f0 <= i <= f1 and f0 <= j <= f1 and f0 <= k <= f1:
+            return E[k - f0, j - f0, i - f0], S[k - f0, j - f0, i - f0]
+        return 1.0, 0.0
+
+    for e, (p, q) in enumerate(parents):
+        (ep, sp), (eq, sq) = value(p), value(q)
+        ne[e] = 0.5 * (ep + eq)
+        ns[e] = 0.5 * (sp + sq)
+    return (np.concatenate([np.asarray(eps_free, float).ravel(), ne]),
+            np.concatenate([np.asarray(sig_free, float).ravel(), ns]))

@@ -3,6 +3,8 @@ include/ddfd.h, and rejects bad configurations before touching a GPU."""
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -72,7 +74,6 @@ def test_no_gpu_fails_loudly(lib):
     ([dict(n=21, fem_n=11, n_steps=3, precision="fp32"), dict(n=21, fem_n=11, n_steps=3)],
      "must match member 0"),
     ([dict(n=21, fem_n=11, n_steps=3, src_dir=[[0, 0, -1.0], [0, 0.1, -1.0]])], "one source"),
-    ([dict(n=21, fem_n=11, n_steps=3, fem_kind=1)], "stencil FEM"),
     ([dict(n=21, fem_n=11, n_steps=30, n_snapshots=3), dict(n=21, fem_n=9, n_steps=30, n_snapshots=5)],
      "segment length"),
     ([dict(n=21, fem_n=11, n_steps=3), dict(n=21, fem_n=30, n_steps=3)], "member 1: fem_n"),
@@ -82,4 +83,17 @@ def test_create_batch_rejects_mismatched_members(lib, cfgs, what):
     from paper_2508_07780_gb300 import Batch, DDFDError
     with pytest.raises(DDFDError) as e:
         Batch(cfgs)
+    assert e.value.code == -1 and what in str(e.value), str(e.value)
+
+
+@pytest.mark.parametrize("mesh_kw,what", [
+    (dict(fem_kind=2), "needs mesh_tets"),
+    (dict(mesh=(np.array([[0, 7]]), np.zeros((6, 4), int)), n_snapshots=2), "n_snapshots"),
+    (dict(mesh=(np.array([[5, 3000]]), np.zeros((6, 4), int))), "parent"),
+    (dict(mesh=(np.zeros((0, 2), int), np.full((6, 4), 99999))), "out of range"),
+])
+def test_create_rejects_bad_refined_meshes(lib, mesh_kw, what):
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    with pytest.raises(DDFDError) as e:
+        Problem(n=13, fem_n=9, n_steps=3, **mesh_kw)
     assert e.value.code == -1 and what in str(e.value), str(e.value)
