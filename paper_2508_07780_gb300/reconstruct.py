@@ -47,12 +47,16 @@ def main(argv=None):
                     help="first update's RMS change of eps on the free nodes")
     ap.add_argument("--variants", default="literal,restart",
                     help="CG variants: literal (the paper's rules) and/or restart (FR restart safeguard)")
+    ap.add_argument("--refine", action="store_true",
+                    help="refine the FEM cube once where eq. meshref marks the model with its inclusion "
+                         "(beta_eps 0.8, marking limited to the central 40%% of the free box)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
     import torch
     from synth import box_bounds, detector_grid, free_box, layered_inclusion_model, shard_directions
+    from synth.mesh import extend_to_new_nodes, refined_fem_mesh
     from . import Batch
 
     n, fem_n = a.n, a.fem_n
@@ -65,7 +69,8 @@ def main(argv=None):
     report = dict(workload=dict(grid=n, fem_n=fem_n, n_steps=nt, sources=a.sources, detectors=int(det.shape[0]),
                                 fine_grid=nf_, fine_fem_n=fem_f, fine_steps=nt_f, fine_precision=a.fine_precision,
                                 noise=a.noise, seed=a.seed, inclusions=a.incl,
-                                fem="uniform Kuhn cube (no local refinement)"))
+                                fem=("Kuhn cube refined once around the inclusion" if a.refine
+                                     else "uniform Kuhn cube (no local refinement)")))
     stream = torch.cuda.current_stream().cuda_stream
 
     # observed data: the finer forward of the same physical model
@@ -89,8 +94,35 @@ def main(argv=None):
     # reconstruction
     e_true, s_true = layered_inclusion_model(n, fem_n, a.seed, a.incl)
     e0, s0 = layered_inclusion_model(n, fem_n, a.seed, 0)
+    extra = {}
+    if a.refine:
+        _, _, f0, f1 = box_bounds(n, fem_n)
+        nfr = f1 - f0 + 1
+        t1 = time.perf_counter()
+        par, tets = refined_fem_mesh(n, fem_n, e_true, s_true, beta_eps=0.8, beta_sig=0.0,
+                                     region=(f0 + int(0.3 * nfr), f0 + int(0.7 * nfr)))
+        report["mesh"] = dict(new_nodes=int(par.shape[0]), tets=int(tets.shape[0]),
+                              base_tets=6 * (fem_n - 1) ** 3, seconds=time.perf_counter() - t1)
+        # the truth at the new nodes is the physical model there: they sit on
+        # the finer grid, which carries the same model
+        _, _, F0, F1 = box_bounds(nf_, fem_f)
+        NF = F1 - F0 + 1
+        EF, SF = ef.reshape(NF, NF, NF), sf.reshape(NF, NF, NF)
+        X = np.zeros((par.shape[0], 3), dtype=np.int64)   # fine-grid indices of the new nodes
+        n3 = n ** 3
+        for e, (p, q) in enumerate(par):
+            pts = []
+            for v in (p, q):
+                pts.append(X[v - n3] if v >= n3 else 2 * np.array([v % n, (v // n) % n, v // (n * n)]))
+            X[e] = (pts[0] + pts[1]) // 2
+        li = X - F0
+        e_new, s_new = EF[li[:, 2], li[:, 1], li[:, 0]], SF[li[:, 2], li[:, 1], li[:, 0]]
+        e_true = np.concatenate([e_true, e_new])
+        s_true = np.concatenate([s_true, s_new])
+        e0, s0 = extend_to_new_nodes(n, fem_n, par, e0, s0)
+        extra = dict(mesh=(par, tets))
     b = Batch([dict(n=n, fem_n=fem_n, n_steps=nt, cfl=cfl, precision="fp32", src_dir=d[None, :], det_ij=det,
-                    stream=stream) for d in dirs])
+                    stream=stream, **extra) for d in dirs])
     kz = b.autotune(steps=4)
     # step sizes: the first update moves eps by step0 (RMS over the free box);
     # gamma^0 = 1/alpha^0 keeps the step rule's alpha^1 at the same scale

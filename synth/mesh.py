@@ -45,13 +45,29 @@ def kuhn_cube(n: int, fem_n: int):
 
 
 class RefinedMesh:
-    """Conforming bisection refinement of the Kuhn mesh of the FEM cube."""
+    """Conforming bisection refinement of the Kuhn mesh of the FEM cube.
 
-    def __init__(self, n: int, fem_n: int):
+    active: optional node box (lo, hi) (grid indices); only the Kuhn elements
+    inside it take part in the refinement bookkeeping, the others are kept
+    as they are (an error is raised if the conformity closure reaches them)."""
+
+    def __init__(self, n: int, fem_n: int, active=None):
         self.n = n
         self.h = 1.0 / (n - 1)
         self.n3 = n ** 3
         t = kuhn_cube(n, fem_n)
+        if active is not None:
+            lo, hi = active
+            ijk = np.stack([t % n, (t // n) % n, t // (n * n)], axis=2)
+            inside = np.all((ijk >= lo) & (ijk <= hi), axis=(1, 2))
+            self.static = t[~inside]
+            t = t[inside]
+            # nodes shared with static elements: edges between two such nodes
+            # may not be cut
+            self.frozen = set(map(int, np.unique(self.static)))
+        else:
+            self.static = np.zeros((0, 4), dtype=np.int64)
+            self.frozen = set()
         self.tets = [list(map(int, r)) for r in t]
         self.tag = [3] * len(self.tets)
         self.gen = [0] * len(self.tets)
@@ -92,6 +108,8 @@ class RefinedMesh:
 
     # ---- bisection ------------------------------------------------------------
     def _midpoint(self, e):
+        if e[0] in self.frozen and e[1] in self.frozen:
+            raise RuntimeError("refinement closure reached the inactive part of the mesh")
         if e not in self.mid:
             v = self.n3 + len(self.parents)
             self.parents.append(e)
@@ -165,9 +183,9 @@ class RefinedMesh:
         return out
 
     def result(self):
-        tets = np.array([t for t, al in zip(self.tets, self.alive) if al], dtype=np.int64)
+        tets = np.array([t for t, al in zip(self.tets, self.alive) if al], dtype=np.int64).reshape(-1, 4)
         par = np.array(self.parents, dtype=np.int64).reshape(-1, 2)
-        return par, tets
+        return par, np.concatenate([self.static, tets])
 
 
 def mark_elements(mesh: RefinedMesh, node_eps, node_sig, beta_eps: float, beta_sig: float):
@@ -182,19 +200,33 @@ def mark_elements(mesh: RefinedMesh, node_eps, node_sig, beta_eps: float, beta_s
 
 
 def refined_fem_mesh(n: int, fem_n: int, eps_free, sig_free, beta_eps: float = 0.8, beta_sig: float = 0.8,
-                     levels: int = 1):
+                     levels: int = 1, region=None):
     """The FEM cube's Kuhn mesh refined `levels` times where eq. meshref marks
     it, for nodal coefficients given on the free nodes [a+2, b-2]^3 (x fastest;
     eps = 1, sigma = 0 elsewhere).  Marking only looks at elements whose nodes
-    all lie in [a+3, b-3]^3, so that the closure stays inside the free box.
-    Returns (parents (E, 2), tets (T, 4)) as described in the module header."""
+    all lie in [a+3, b-3]^3 (and in region = (lo, hi), node indices, if given),
+    so that the closure stays inside the free box.  Returns (parents (E, 2), tets (T, 4)) as described in the module header."""
     a = (n - fem_n) // 2
     b = a + fem_n - 1
     f0, f1 = a + 2, b - 2
     nf = f1 - f0 + 1
     E = np.asarray(eps_free, dtype=np.float64).reshape(nf, nf, nf)
     S = np.asarray(sig_free, dtype=np.float64).reshape(nf, nf, nf)
-    mesh = RefinedMesh(n, fem_n)
+    # refinement bookkeeping only around the marked candidates (the
+    # closure of newest-vertex bisection on a Kuhn mesh stays within a few
+    # cells of them)
+    cand = (E >= beta_eps * E.max()) & (S >= beta_sig * S.max()) if beta_eps > 0 or beta_sig > 0 else None
+    rlo, rhi = (a + 3, b - 3) if region is None else (max(a + 3, region[0]), min(b - 3, region[1]))
+    if cand is not None:
+        K, J, I = np.meshgrid(*(np.arange(f0, f1 + 1),) * 3, indexing="ij")
+        cand &= (I >= rlo) & (I <= rhi) & (J >= rlo) & (J <= rhi) & (K >= rlo) & (K <= rhi)
+    active = None
+    if cand is not None and cand.any():
+        idx = np.argwhere(cand)  # (k, j, i) of free nodes
+        lo = max(a, int(idx.min()) + f0 - 4)
+        hi = min(b, int(idx.max()) + f0 + 4)
+        active = (lo, hi)
+    mesh = RefinedMesh(n, fem_n, active)
 
     def ijk(v):
         return v % n, (v // n) % n, v // (n * n)
@@ -208,7 +240,7 @@ def refined_fem_mesh(n: int, fem_n: int, eps_free, sig_free, beta_eps: float = 0
         return f
 
     inner = [ti for ti in range(len(mesh.tets))  # marking restricted to these
-             if all(a + 3 <= c <= b - 3 for v in mesh.tets[ti] for c in ijk(v))]
+             if all(rlo <= c <= rhi for v in mesh.tets[ti] for c in ijk(v))]
     marked_all = mark_elements(mesh, val(E, 1.0), val(S, 0.0), beta_eps, beta_sig)
     inner_set = set(inner)
     marked = [ti for ti in marked_all if ti in inner_set]
