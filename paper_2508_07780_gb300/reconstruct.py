@@ -60,7 +60,9 @@ def main(argv=None):
     from . import Batch
 
     n, fem_n = a.n, a.fem_n
-    cfl = 0.3
+    # one level of refinement halves the smallest elements: its vacuum
+    # stability bound is tau/h ~ 0.27 (eps >= 1 only raises it)
+    cfl = 0.25 if a.refine else 0.3
     h = 1.0 / (n - 1)
     nt = a.steps or int(round(3.0 / (cfl * h)))
     nf_, fem_f, nt_f = 2 * (n - 1) + 1, 2 * (fem_n - 1) + 1, 2 * nt
