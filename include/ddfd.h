@@ -345,7 +345,11 @@ void ddfd_cg_params_default(ddfd_cg_params *prm);
  * m+1 after iteration m.  The box must lie inside every member's eps_max,
  * sig_max.  Errors: DDFD_E_ARG (members differ in fem_n or carry gammas, bad
  * parameters), DDFD_E_COEFF (initial guess outside the box), the errors of
- * the forward/adjoint calls; message in ddfd_batch_last_error. */
+ * the forward/adjoint calls; message in ddfd_batch_last_error.  When an
+ * iteration m fails (e.g. DDFD_E_NONFINITE: the stabilized operator with a
+ * rough iterate has growing modes), *iters = m, log[0..m) and eps_iters /
+ * sig_iters rows [0..m) are filled, and eps, sig hold the iterate eps^m,
+ * sig^m whose evaluation failed. */
 int ddfd_cg_run(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *prm, double *eps,
                 double *sig, ddfd_cg_iter *log, int32_t *iters, double *eps_iters, double *sig_iters);
 

@@ -488,7 +488,9 @@ class Batch:
         measurements).  eobs: one observed trace per member (host); eps0, sig0:
         initial guess on the free nodes; params: ddfd_cg_params fields.
         Returns (eps, sig, log) with log a list of dicts, one per iteration
-        (with iterates=True each dict also holds that iteration's new eps, sig)."""
+        (with iterates=True each dict also holds that iteration's new eps, sig).
+        A failed iteration raises DDFDError carrying .log (the iterations
+        before it) and .eps, .sig (the iterate whose evaluation failed)."""
         prm = ddfd_cg_params()
         self._lib.ddfd_cg_params_default(ctypes.byref(prm))
         for k, v in params.items():
@@ -502,10 +504,15 @@ class Batch:
         iters = c_int32()
         ei = np.empty((prm.max_iter, nf)) if iterates else None
         si = np.empty((prm.max_iter, nf)) if iterates else None
-        self._check(self._lib.ddfd_cg_run(self._h, ptrs, ctypes.byref(prm), _ptr(eps), _ptr(sig), log,
-                                          ctypes.byref(iters), _ptr(ei), _ptr(si)))
+        st = self._lib.ddfd_cg_run(self._h, ptrs, ctypes.byref(prm), _ptr(eps), _ptr(sig), log,
+                                   ctypes.byref(iters), _ptr(ei), _ptr(si))
         out = [{f: getattr(log[i], f) for f, _ in ddfd_cg_iter._fields_} for i in range(iters.value)]
         if iterates:
             for i, r in enumerate(out):
                 r["eps"], r["sig"] = ei[i], si[i]
+        try:
+            self._check(st)
+        except DDFDError as e:
+            e.log, e.eps, e.sig = out, eps, sig
+            raise
         return eps, sig, out

@@ -1901,6 +1901,7 @@ int batch_adjoint_impl(ddfd_batch *b, const double *const *eobs, bool host) {
 // The CGA of Sec. 4 over the batch's members (see ddfd_cg_run in ddfd.h).
 int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *prm, double *eps_h,
                 double *sig_h, ddfd_cg_iter *log, int32_t *iters, double *eps_it, double *sig_it) {
+  if (iters) *iters = 0;
   if (!prm || !eps_h || !sig_h) return bfail(b, DDFD_E_ARG, "parameters, eps and sigma are required");
   if (prm->max_iter < 1 || !(prm->gamma_eps0 >= 0) || !(prm->gamma_sig0 >= 0) || !(prm->p >= 0 && prm->p < 1) ||
       !(prm->eps_max >= 1) || !(prm->sig_max >= 0) || !std::isfinite(prm->alpha_eps0) || !std::isfinite(prm->alpha_sig0))
@@ -1959,24 +1960,34 @@ int cg_run_impl(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *
   double alp_e = prm->alpha_eps0, alp_s = prm->alpha_sig0;
   double gg_e_prev = 0.0, gg_s_prev = 0.0;
   int done = 0;
+  // an iteration that fails (typically DDFD_E_NONFINITE) keeps the records of
+  // the iterations before it and hands back the iterate it was evaluating
+  auto failed = [&](int st) {
+    if (iters) *iters = done;
+    cudaMemcpyAsync(eps_h, eps, nb, cudaMemcpyDeviceToHost, sm);
+    cudaMemcpyAsync(sig_h, sig, nb, cudaMemcpyDeviceToHost, sm);
+    cudaStreamSynchronize(sm);
+    return st;
+  };
   for (int it = 0; it < prm->max_iter; ++it) {
     BCK(cudaEventRecord(b->ev[0], sm));
     // 1. E^m, lambda^m, g^m
     int st;
     for (ddfd_problem *p : b->m)
       if ((st = set_coeffs_impl(p, eps, sig, nullptr, nullptr, cudaMemcpyDeviceToDevice)))
-        return bfail(b, st, p->err);
-    if ((st = batch_forward_impl(b, nullptr, cudaMemcpyDeviceToDevice))) return st;
+        return failed(bfail(b, st, p->err));
+    if ((st = batch_forward_impl(b, nullptr, cudaMemcpyDeviceToDevice))) return failed(st);
     double J_data = 0.0;
     for (size_t i = 0; i < b->m.size(); ++i) {
       double Ji = 0.0;
-      if ((st = functional_impl(b->m[i], eobs_dev[i], &Ji, false))) return bfail(b, st, b->m[i]->err);
+      if ((st = functional_impl(b->m[i], eobs_dev[i], &Ji, false))) return failed(bfail(b, st, b->m[i]->err));
       J_data += Ji;
     }
-    if ((st = batch_adjoint_impl(b, eobs_dev.data(), false))) return st;
+    if ((st = batch_adjoint_impl(b, eobs_dev.data(), false))) return failed(st);
     for (size_t i = 0; i < b->m.size(); ++i) {
       const bool first = i == 0;
-      if ((st = gradient_impl(b->m[i], first ? Ge : Te, first ? Gs : Ts, false))) return bfail(b, st, b->m[i]->err);
+      if ((st = gradient_impl(b->m[i], first ? Ge : Te, first ? Gs : Ts, false)))
+        return failed(bfail(b, st, b->m[i]->err));
       if (!first) launch_cg_accum(Ge, Gs, Te, Ts, n, sm);
     }
     launch_cg_grad(Ge, Gs, eps, sig, re, rs, 1.0 / hm, gam_e, gam_s, gte, gts, de, ds, it > 0, n, part, out, sm,

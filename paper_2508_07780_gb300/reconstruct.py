@@ -43,8 +43,10 @@ def main(argv=None):
     ap.add_argument("--noise", type=float, default=0.01)
     ap.add_argument("--fine-precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--p", type=float, default=0.5)
-    ap.add_argument("--step0", type=float, default=1.0,
+    ap.add_argument("--step0", type=float, default=0.5,
                     help="first update's RMS change of eps on the free nodes")
+    ap.add_argument("--eps-max", type=float, default=30.0, help="admissible box: eps in [1, eps_max]")
+    ap.add_argument("--sig-max", type=float, default=5.0, help="admissible box: sigma in [0, sig_max]")
     ap.add_argument("--variants", default="literal,restart",
                     help="CG variants: literal (the paper's rules) and/or restart (FR restart safeguard)")
     ap.add_argument("--refine", action="store_true",
@@ -57,7 +59,7 @@ def main(argv=None):
     import torch
     from synth import box_bounds, detector_grid, free_box, layered_inclusion_model, shard_directions
     from synth.mesh import extend_to_new_nodes, refined_fem_mesh
-    from . import Batch
+    from . import Batch, DDFDError
 
     n, fem_n = a.n, a.fem_n
     # one level of refinement halves the smallest elements: its vacuum
@@ -124,7 +126,8 @@ def main(argv=None):
         e0, s0 = extend_to_new_nodes(n, fem_n, par, e0, s0)
         extra = dict(mesh=(par, tets))
     b = Batch([dict(n=n, fem_n=fem_n, n_steps=nt, cfl=cfl, precision="fp32", src_dir=d[None, :], det_ij=det,
-                    stream=stream, **extra) for d in dirs])
+                    eps_max=max(100.0, a.eps_max), sig_max=max(100.0, a.sig_max), stream=stream, **extra)
+               for d in dirs])
     kz = b.autotune(steps=4)
     # step sizes: the first update moves eps by step0 (RMS over the free box);
     # gamma^0 = 1/alpha^0 keeps the step rule's alpha^1 at the same scale
@@ -142,17 +145,27 @@ def main(argv=None):
     report["updates_per_iteration"] = 2 * n ** 3 * nt * a.sources
     for variant in a.variants.split(","):
         prm = dict(max_iter=a.iters, gamma_eps0=1.0 / alpha_e, gamma_sig0=1.0 / alpha_s, alpha_eps0=alpha_e,
-                   alpha_sig0=alpha_s, p=a.p, eps_max=100.0, sig_max=100.0, restart=int(variant == "restart"))
-        eps, sig, log = b.cg_run(eobs, e0, s0, iterates=True, **prm)
+                   alpha_sig0=alpha_s, p=a.p, eps_max=a.eps_max, sig_max=a.sig_max,
+                   restart=int(variant == "restart"))
+        err = None
+        try:
+            eps, sig, log = b.cg_run(eobs, e0, s0, iterates=True, **prm)
+        except DDFDError as exc:  # recorded with the iterations before it; the other variants still run
+            err, eps, sig, log = exc, exc.eps, exc.sig, exc.log
         rows = []
         for r in log:
             rows.append({k: float(v) for k, v in r.items() if k not in ("eps", "sig")})
             rows[-1]["eps_rel_err"] = float(np.linalg.norm(r["eps"] - e_true) / ne)
             rows[-1]["sig_rel_err"] = float(np.linalg.norm(r["sig"] - s_true) / ns)
-        ms = [r["ms"] for r in log]
-        report["cg_" + variant] = dict(params=prm, ms_per_iteration=float(np.mean(ms)),
-                                       updates_per_s=report["updates_per_iteration"] / (np.mean(ms) / 1e3),
-                                       iterations=rows)
+        out = dict(params=prm, iterations=rows)
+        if log:
+            ms = float(np.mean([r["ms"] for r in log]))
+            out.update(ms_per_iteration=ms, updates_per_s=report["updates_per_iteration"] / (ms / 1e3))
+        if err is not None:
+            out.update(error=str(err), failed_iteration=len(log),
+                       failed_iterate=dict(eps_min=float(eps.min()), eps_max=float(eps.max()),
+                                           sig_max=float(sig.max())))
+        report["cg_" + variant] = out
     report["device_bytes"] = int(b.get_info().device_bytes)
     b.close()
     txt = json.dumps(report)

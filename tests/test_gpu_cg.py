@@ -139,3 +139,22 @@ def test_forward_only_handles():
         p.adjoint(np.zeros(p.trace_shape))
     assert e.value.code == -3
     p.close()
+
+
+def test_failed_iteration_keeps_log_and_iterate(oracle_run):
+    """An iteration that fails hands back what came before it: here the
+    functional of iteration 0 overflows (observations of 1e300), so no record
+    is kept and the iterate returned is the initial guess; the handle stays
+    usable."""
+    from paper_2508_07780_gb300 import DDFDError
+    o = oracle_run
+    b = make_batch("fp64")
+    huge = [np.full_like(e, 1e300) for e in o["eobs"]]
+    with pytest.raises(DDFDError) as e:
+        b.cg_run(huge, o["e0"], o["s0"], max_iter=3, iterates=True, **PRM)
+    assert e.value.code == -6 and "functional" in str(e.value)
+    assert e.value.log == []
+    assert np.array_equal(e.value.eps, o["e0"]) and np.array_equal(e.value.sig, o["s0"])
+    eps, sig, log = b.cg_run(o["eobs"], o["e0"], o["s0"], max_iter=1, **PRM)
+    b.close()
+    assert log[0]["J"] == pytest.approx(o["log"][0]["J"], rel=1e-8)

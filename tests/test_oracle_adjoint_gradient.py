@@ -9,7 +9,8 @@
 * J vanishes for Eobs equal to the model's own trace and is quadratic in the
   residual;
 * the power-iteration bound against dense eigenvalues and the closed-form
-  vacuum maximum 12/h^2;
+  vacuum maximum 12/h^2; a real spectrum for eps = 1 and a non-real one for
+  variable eps (the Gauss-law term is not self-adjoint);
 * source flux totals, the integer switch step and z_delta's shape.
 """
 import math
@@ -132,6 +133,22 @@ def test_power_iteration_matches_dense_spectrum():
     assert lam == pytest.approx(np.abs(w).max(), rel=1e-3)
     # the workloads' CFL 0.3 is far inside the stability bound
     assert P.tau < 0.8 * 2.0 / math.sqrt(np.abs(w).max())
+
+
+def test_spectrum_real_for_eps_one_complex_for_variable_eps():
+    """The Gauss-law term -grad div((eps - 1) E) of Sec. 2 is not self-adjoint
+    once eps varies: with eps = 1 the stepped operator M_eps^-1 K has a real
+    spectrum, with eps jumping at the FEM cube (and varying inside it) some
+    eigenvalues leave the real axis -- modes that grow at any time step, and
+    the reason rough iterates of the CGA can make the forward run overflow."""
+    def spectrum(P):
+        return sla.eigvals(P.op.sparse_K().toarray() / np.tile(P.M, 3)[:, None])
+
+    vac = spectrum(tiny_problem(eps=np.ones(27), sig=np.zeros(27)))
+    assert np.abs(vac.imag).max() <= 1e-9 * np.abs(vac).max()
+    var = spectrum(tiny_problem(seed=9, sig=np.zeros(27)))
+    assert np.abs(var.imag).max() >= 1e-4 * np.abs(var).max()
+    assert var.real.min() >= -1e-9 * np.abs(var).max()
 
 
 def test_source_flux_total_and_polarisation():
