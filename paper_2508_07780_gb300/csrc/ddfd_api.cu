@@ -61,9 +61,11 @@ struct ddfd_problem {
   void *snap = nullptr;
   // element-by-element FEM rows (fem_kind = DDFD_FEM_EBE): explicit mesh
   int ebe_rows = 0;
-  int *ebe_row_node = nullptr, *ebe_row_ptr = nullptr, *ebe_inc_tet = nullptr, *ebe_inc_local = nullptr;
-  int *ebe_tet_node = nullptr;
-  void *ebe_tet_grad = nullptr, *ebe_out_r = nullptr, *ebe_out_q = nullptr;
+  int *ebe_row_node = nullptr, *ebe_blk_nodes = nullptr, *ebe_blk_rows = nullptr;
+  EbeBlock *ebe_blocks = nullptr;
+  unsigned char *ebe_blob = nullptr;
+  int ebe_nblocks = 0, ebe_smem = 0;
+  void *ebe_out_r = nullptr, *ebe_out_q = nullptr;
   double *ebe_scale = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
   float *gpart = nullptr;     // FP32: per free node (g_eps, g_sig) sums of the current step block
@@ -363,12 +365,13 @@ void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, 
   EbeParams<T> E;
   E.n_rows = p->ebe_rows;
   E.row_node = p->ebe_row_node;
-  E.row_ptr = p->ebe_row_ptr;
-  E.inc_tet = p->ebe_inc_tet;
-  E.inc_local = p->ebe_inc_local;
-  E.tet_node = p->ebe_tet_node;
-  E.tet_grad = (const T *)p->ebe_tet_grad;
   E.scale = p->ebe_scale;
+  E.n_blocks = p->ebe_nblocks;
+  E.blocks = p->ebe_blocks;
+  E.blob = p->ebe_blob;
+  E.blk_nodes = p->ebe_blk_nodes;
+  E.blk_rows = p->ebe_blk_rows;
+  E.smem = p->ebe_smem;
   E.field = (const T *)field;
   E.s = (const T *)p->kcoef;
   E.cs = p->cs;
@@ -680,6 +683,36 @@ int encode_field_maps(std::string *err, FieldMaps *fm, void *const E[2], void *c
 // Kuhn tetrahedra of every cube of [a, b]^3 as a tet list with per-tet
 // sqrt|K| g (from the inverse of [1 x] in FP64), the incidences of the nodes
 // strictly inside the cube (the rows the FEM updates) and their lumped masses.
+// Packs the element-by-element rows into shared-memory blocks and uploads
+// them with the rows' node offsets and mass scales (both mesh kinds).
+int upload_ebe(ddfd_problem *p, long long rows, long long ntet, const std::vector<int> &tnode,
+               const std::vector<double> &tgrad, const std::vector<int> &rptr, const std::vector<int> &itet,
+               const std::vector<int> &iloc, const std::vector<int> &rnode, const std::vector<double> &scale,
+               const std::vector<double> &rpos) {
+  EbePack pk;
+  std::string m;
+  if (!pack_ebe_blocks(rows, ntet, tnode.data(), tgrad.data(), rptr.data(), itet.data(), iloc.data(), rpos.data(),
+                       (int)p->esz, &pk, &m))
+    return fail(p, DDFD_E_ARG, m);
+  int st;
+  const size_t es = p->esz;
+  if ((st = dalloc_t(p, (size_t)rows, &p->ebe_row_node)) || (st = dalloc_t(p, (size_t)rows, &p->ebe_scale)) ||
+      (st = dalloc_t(p, pk.blocks.size(), &p->ebe_blocks)) || (st = dalloc_t(p, pk.blob.size(), &p->ebe_blob)) ||
+      (st = dalloc_t(p, pk.nodes.size(), &p->ebe_blk_nodes)) || (st = dalloc_t(p, pk.rows.size(), &p->ebe_blk_rows)) ||
+      (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_r)) || (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_q)))
+    return st;
+  CK(cudaMemcpy(p->ebe_row_node, rnode.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_scale, scale.data(), rows * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_blocks, pk.blocks.data(), pk.blocks.size() * sizeof(EbeBlock), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_blob, pk.blob.data(), pk.blob.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_blk_nodes, pk.nodes.data(), pk.nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->ebe_blk_rows, pk.rows.data(), pk.rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+  p->ebe_nblocks = (int)pk.blocks.size();
+  p->ebe_smem = pk.smem;
+  p->ebe_rows = (int)rows;
+  return DDFD_OK;
+}
+
 int build_ebe(ddfd_problem *p) {
   const int a = p->a, b = p->b, n = p->n;
   const int fm = b - a - 1;  // rows per axis
@@ -754,29 +787,16 @@ int build_ebe(ddfd_problem *p) {
         rnode[r] = off(i, j, k);
         scale[r] = p->h * p->h / mass[r];
       }
-  int st;
-  const size_t es = p->esz;
-  if ((st = dalloc_t(p, (size_t)rows, &p->ebe_row_node)) || (st = dalloc_t(p, (size_t)rows + 1, &p->ebe_row_ptr)) ||
-      (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_tet)) || (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_local)) ||
-      (st = dalloc_t(p, (size_t)ntet * 4, &p->ebe_tet_node)) || (st = dalloc(p, (size_t)ntet * 12 * es, &p->ebe_tet_grad)) ||
-      (st = dalloc_t(p, (size_t)rows, &p->ebe_scale)) || (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_r)) ||
-      (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_q)))
-    return st;
-  std::vector<float> tgf;
-  const void *gsrc = tgrad.data();
-  if (p->fp32) {
-    tgf.assign(tgrad.begin(), tgrad.end());
-    gsrc = tgf.data();
-  }
-  CK(cudaMemcpy(p->ebe_row_node, rnode.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_row_ptr, rptr.data(), (rows + 1) * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_inc_tet, itet.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_inc_local, iloc.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_tet_node, tnode.data(), ntet * 4 * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_tet_grad, gsrc, ntet * 12 * es, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_scale, scale.data(), rows * sizeof(double), cudaMemcpyHostToDevice));
-  p->ebe_rows = (int)rows;
-  return DDFD_OK;
+  std::vector<double> rpos((size_t)rows * 3);
+  for (int k = a + 1; k < b; ++k)
+    for (int j = a + 1; j < b; ++j)
+      for (int i = a + 1; i < b; ++i) {
+        const long long r = rowof(i, j, k);
+        rpos[3 * r] = i;
+        rpos[3 * r + 1] = j;
+        rpos[3 * r + 2] = k;
+      }
+  return upload_ebe(p, rows, ntet, tnode, tgrad, rptr, itet, iloc, rnode, scale, rpos);
 }
 
 // Explicit refined FEM mesh (fem_kind = DDFD_FEM_MESH): node coordinates
@@ -897,36 +917,30 @@ int build_mesh(ddfd_problem *p) {
     mfree[f] = mass[rowof((p->f0 + li) + n * ((p->f0 + lj) + (long long)n * (p->f0 + lk)))];
   }
   for (int e = 0; e < p->n_new; ++e) mfree[p->n_free_grid + e] = mass[grid_rows + e];
+  std::vector<double> rpos((size_t)rows * 3);
+  for (long long k = a + 1; k < b; ++k)
+    for (long long j = a + 1; j < b; ++j)
+      for (long long i = a + 1; i < b; ++i) {
+        const long long r = rowof(i + n * (j + n * k));
+        rpos[3 * r] = (double)i;
+        rpos[3 * r + 1] = (double)j;
+        rpos[3 * r + 2] = (double)k;
+      }
+  for (int e = 0; e < p->n_new; ++e)
+    for (int d = 0; d < 3; ++d) rpos[3 * (grid_rows + e) + d] = X[(size_t)e * 3 + d] / p->h;
   int st;
+  if ((st = upload_ebe(p, rows, ntet, tnode, tgrad, rptr, itet, iloc, rnode, scale, rpos))) return st;
   const size_t es = p->esz, xb = 3 * (size_t)std::max(p->n_new, 1) * es;
-  if ((st = dalloc_t(p, (size_t)rows, &p->ebe_row_node)) || (st = dalloc_t(p, (size_t)rows + 1, &p->ebe_row_ptr)) ||
-      (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_tet)) || (st = dalloc_t(p, (size_t)ninc, &p->ebe_inc_local)) ||
-      (st = dalloc_t(p, (size_t)ntet * 4, &p->ebe_tet_node)) || (st = dalloc(p, (size_t)ntet * 12 * es, &p->ebe_tet_grad)) ||
-      (st = dalloc_t(p, (size_t)rows, &p->ebe_scale)) || (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_r)) ||
-      (st = dalloc(p, 3 * (size_t)rows * es, &p->ebe_out_q)) || (st = dalloc_t(p, (size_t)p->n_free, &p->mass_free)) ||
-      (st = dalloc(p, xb, &p->X[0])) || (st = dalloc(p, xb, &p->X[1])) || (st = dalloc(p, xb, &p->xcoef)) ||
+  if ((st = dalloc_t(p, (size_t)p->n_free, &p->mass_free)) || (st = dalloc(p, xb, &p->X[0])) ||
+      (st = dalloc(p, xb, &p->X[1])) || (st = dalloc(p, xb, &p->xcoef)) ||
       (!p->fonly && ((st = dalloc(p, xb, &p->XMu[0])) || (st = dalloc(p, xb, &p->XMu[1])))))
     return st;
-  std::vector<float> tgf;
-  const void *gsrc = tgrad.data();
-  if (p->fp32) {
-    tgf.assign(tgrad.begin(), tgrad.end());
-    gsrc = tgf.data();
-  }
-  CK(cudaMemcpy(p->ebe_row_node, rnode.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_row_ptr, rptr.data(), (rows + 1) * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_inc_tet, itet.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_inc_local, iloc.data(), ninc * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_tet_node, tnode.data(), ntet * 4 * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_tet_grad, gsrc, ntet * 12 * es, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(p->ebe_scale, scale.data(), rows * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(p->mass_free, mfree.data(), p->n_free * sizeof(double), cudaMemcpyHostToDevice));
   for (int q = 0; q < 2; ++q) {
     CK(cudaMemset(p->X[q], 0, xb));
     if (p->XMu[q]) CK(cudaMemset(p->XMu[q], 0, xb));
   }
   CK(cudaMemset(p->xcoef, 0, xb));
-  p->ebe_rows = (int)rows;
   return DDFD_OK;
 }
 
@@ -1200,7 +1214,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
       return bail(DDFD_E_CUDA);
     }
   if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      prepare_step_kernels() != cudaSuccess) {
+      prepare_step_kernels() != cudaSuccess || prepare_ebe_kernels() != cudaSuccess) {
     p->err = "stream creation or kernel attribute setup failed";
     return bail(DDFD_E_CUDA);
   }

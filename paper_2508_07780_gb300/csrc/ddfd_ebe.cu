@@ -1,5 +1,5 @@
 // Element-by-element FEM apply on an explicit tetrahedral mesh of the FEM
-// cube (fem_kind = DDFD_FEM_EBE).
+// cube (fem_kind = DDFD_FEM_EBE and DDFD_FEM_MESH).
 //
 // For every node updated by FEM rows, the P1 stiffness of the stabilized
 // operator is gathered element by element over the node's incident
@@ -9,11 +9,17 @@
 //   adjoint:  (K^T mu)_a = sum_K |K| [ sum_b (g_a . g_b) mu_b ] + s_a (D^T D mu)_a,
 //             (D^T D mu)_a = sum_K |K| g_a sum_b g_b . mu_b
 // with g the P1 gradients (the Laplacian and the Gauss-law term of eq.
-// forward_prob, weak form eq. lagrangian_weak).  Each tet stores its four
-// nodes' offsets in the padded field layout and sqrt|K| g_b (so products of
-// two carry |K|).  The output is scaled to the step kernel's units,
-// R = h^2 M^-1 (K E), and, in the adjoint, also q = h^2 M^-1 (D^T D mu) for the
-// gradient.
+// forward_prob, weak form eq. lagrangian_weak).  Each tet carries
+// sqrt|K| g_b (so products of two carry |K|).  The output is scaled to the
+// step kernel's units, R = h^2 M^-1 (K E), and, in the adjoint, also
+// q = h^2 M^-1 (D^T D mu) for the gradient.
+//
+// Staging: one CTA per block of nearby rows (EbeBlock).  The block's tets
+// arrive as one contiguous blob (16-byte loads), its nodes' values are
+// gathered once into shared memory, the tet divergences
+// sum_b g_b . (s_b E_b) are formed once per tet, and each row then sums its
+// incident tets from shared memory (EBE_TPR threads per row, each summing
+// every EBE_TPR-th incidence, combined in a fixed order).
 #include <cuda_runtime.h>
 
 #include "ddfd_internal.h"
@@ -30,59 +36,185 @@ __device__ __forceinline__ T node_s(const EbeParams<T> &P, int nb) {
   return nb < P.cs ? P.s[nb] : P.xs[nb - P.cs];
 }
 
+// Vector loads from shared memory: 12 gradient values, 4 node values.
+__device__ __forceinline__ void ld_grad(const float *g, float v[12]) {
+  const float4 a = reinterpret_cast<const float4 *>(g)[0], b = reinterpret_cast<const float4 *>(g)[1],
+               c = reinterpret_cast<const float4 *>(g)[2];
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y;
+  v[6] = b.z, v[7] = b.w, v[8] = c.x, v[9] = c.y, v[10] = c.z, v[11] = c.w;
+}
+__device__ __forceinline__ void ld_grad(const double *g, double v[12]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double2 d = reinterpret_cast<const double2 *>(g)[i];
+    v[2 * i] = d.x, v[2 * i + 1] = d.y;
+  }
+}
+__device__ __forceinline__ void ld_node(const float *n, float v[4]) {
+  const float4 a = *reinterpret_cast<const float4 *>(n);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+__device__ __forceinline__ void ld_node(const double *n, double v[4]) {
+  const double2 a = reinterpret_cast<const double2 *>(n)[0], b = reinterpret_cast<const double2 *>(n)[1];
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+
+// Running sum with Kahan compensation: the FP32 rows sum 24 to 60 element
+// terms without FP64 arithmetic (scarce on this part) and keep an error
+// close to one rounding of the total.
+template <typename T>
+struct KSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    if (sizeof(T) == 8) {
+      s += x;
+    } else {
+      const T y = x - c, t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <typename T, bool ADJ>
-__global__ void k_ebe(const EbeParams<T> P) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.n_rows; r += gridDim.x * blockDim.x) {
-    const int i = P.row_node[r];  // padded offset of the row's node
-    double y[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
-    const int e0 = P.row_ptr[r], e1 = P.row_ptr[r + 1];
-    for (int e = e0; e < e1; ++e) {
-      const int t = P.inc_tet[e];
-      const int a = P.inc_local[e];
-      const int *nodes = P.tet_node + 4 * t;
-      const T *g = P.tet_grad + 12 * t;  // sqrt|K| g_b, b = 0..3
-      const T ga0 = g[3 * a + 0], ga1 = g[3 * a + 1], ga2 = g[3 * a + 2];
-      T lap[3] = {T(0), T(0), T(0)}, div = T(0);
+__global__ void __launch_bounds__(EBE_THREADS, 2) k_ebe(const EbeParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const EbeBlock B = P.blocks[blockIdx.x];
+  const int tid = threadIdx.x;
+  // 1. the block's tets and incidences
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(P.blob + B.blob);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm);
+    const int nv = B.bytes >> 4;
+#pragma unroll 4
+    for (int i = tid; i < nv; i += EBE_THREADS) dst[i] = __ldg(src + i);
+  }
+  // 2. the values of its nodes: field components and s
+  T *sN = reinterpret_cast<T *>(sm + B.bytes);
+  T *sD = sN + ((4 * B.nn * (int)sizeof(T) + 15) & ~15) / (int)sizeof(T);
+  for (int i = tid; i < B.nn; i += EBE_THREADS) {
+    const int o = P.blk_nodes[B.node0 + i];
+    T v0, v1, v2, sv;
+    if (o < P.cs) {
+      v0 = P.field[o];
+      v1 = P.field[P.cs + o];
+      v2 = P.field[2 * P.cs + o];
+      sv = ADJ ? T(1) : P.s[o];
+    } else {
+      const long long e = o - P.cs;
+      v0 = P.xfield[e];
+      v1 = P.xfield[P.n_new + e];
+      v2 = P.xfield[2LL * P.n_new + e];
+      sv = ADJ ? T(1) : P.xs[e];
+    }
+    sN[4 * i + 0] = v0;
+    sN[4 * i + 1] = v1;
+    sN[4 * i + 2] = v2;
+    sN[4 * i + 3] = sv;
+  }
+  __syncthreads();
+  const T *sG = reinterpret_cast<const T *>(sm);
+  const uint2 *sT = reinterpret_cast<const uint2 *>(sm + (size_t)B.nt * 12 * sizeof(T));  // 4 x uint16 per tet
+  const uint16_t *sI = reinterpret_cast<const uint16_t *>(sT + B.nt);
+  // 3. per tet: sum_b s_b (g_b . E_b) (forward), sum_b g_b . mu_b (adjoint)
+  for (int t = tid; t < B.nt; t += EBE_THREADS) {
+    T g[12];
+    ld_grad(sG + 12 * t, g);
+    const uint2 nd = sT[t];
+    const int ids[4] = {(int)(nd.x & 0xFFFF), (int)(nd.x >> 16), (int)(nd.y & 0xFFFF), (int)(nd.y >> 16)};
+    T div = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      T v[4];
+      ld_node(sN + 4 * ids[b], v);
+      div += v[3] * (g[3 * b + 0] * v[0] + g[3 * b + 1] * v[1] + g[3 * b + 2] * v[2]);
+    }
+    sD[t] = div;
+  }
+  __syncthreads();
+  // 4. rows: EBE_TPR threads per row, thread j of a row sums incidences j, j + EBE_TPR, ...
+  const int lr = tid / EBE_TPR, j = tid % EBE_TPR;
+  KSum<T> y[3], q[3];
+  if (lr < B.nrows) {
+    for (int e = j; e < B.maxinc; e += EBE_TPR) {
+      const uint16_t code = sI[e * EBE_RB + lr];
+      if (code == EBE_PAD) break;
+      const int t = code >> 2, a = code & 3;
+      T g[12];
+      ld_grad(sG + 12 * t, g);
+      const uint2 nd = sT[t];
+      const int ids[4] = {(int)(nd.x & 0xFFFF), (int)(nd.x >> 16), (int)(nd.y & 0xFFFF), (int)(nd.y >> 16)};
+      // g_a by selection (a dynamic index would put g in local memory)
+      T ga0 = g[0], ga1 = g[1], ga2 = g[2];
+#pragma unroll
+      for (int b = 1; b < 4; ++b)
+        if (a == b) ga0 = g[3 * b + 0], ga1 = g[3 * b + 1], ga2 = g[3 * b + 2];
+      T lap0 = T(0), lap1 = T(0), lap2 = T(0);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int nb = nodes[b];
-        const T gb0 = g[3 * b + 0], gb1 = g[3 * b + 1], gb2 = g[3 * b + 2];
-        const T w = ga0 * gb0 + ga1 * gb1 + ga2 * gb2;
-        const T e0v = node_field(P, nb, 0), e1v = node_field(P, nb, 1), e2v = node_field(P, nb, 2);
-        lap[0] += w * e0v;
-        lap[1] += w * e1v;
-        lap[2] += w * e2v;
-        const T sb = ADJ ? T(1) : node_s(P, nb);
-        div += sb * (gb0 * e0v + gb1 * e1v + gb2 * e2v);
+        T v[4];
+        ld_node(sN + 4 * ids[b], v);
+        const T w = ga0 * g[3 * b + 0] + ga1 * g[3 * b + 1] + ga2 * g[3 * b + 2];
+        lap0 += w * v[0];
+        lap1 += w * v[1];
+        lap2 += w * v[2];
       }
-      y[0] += (double)lap[0];
-      y[1] += (double)lap[1];
-      y[2] += (double)lap[2];
-      q[0] += (double)(ga0 * div);
-      q[1] += (double)(ga1 * div);
-      q[2] += (double)(ga2 * div);
+      const T div = sD[t];
+      y[0].add(lap0);
+      y[1].add(lap1);
+      y[2].add(lap2);
+      q[0].add(ga0 * div);
+      q[1].add(ga1 * div);
+      q[2].add(ga2 * div);
     }
+  }
+  // the row's partial sums, combined in a fixed order (bitwise reproducible)
+  double yr[3], qr[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    yr[c] = y[c].value();
+    qr[c] = q[c].value();
+#pragma unroll
+    for (int m = 1; m < EBE_TPR; m <<= 1) {
+      yr[c] += __shfl_xor_sync(0xffffffffu, yr[c], m);
+      qr[c] += __shfl_xor_sync(0xffffffffu, qr[c], m);
+    }
+  }
+  if (j == 0 && lr < B.nrows) {
+    const int r = P.blk_rows[B.row0 + lr];
     const double sc = P.scale[r];  // h^2 / m_a
-    const double sa = ADJ ? (double)node_s(P, i) : 1.0;
+    const double sa = ADJ ? (double)node_s(P, P.row_node[r]) : 1.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      P.out_r[c * P.n_rows + r] = (T)(sc * (y[c] + sa * q[c]));
-      if (ADJ) P.out_q[c * P.n_rows + r] = (T)(sc * q[c]);
+      P.out_r[c * (long long)P.n_rows + r] = (T)(sc * (yr[c] + sa * qr[c]));
+      if (ADJ) P.out_q[c * (long long)P.n_rows + r] = (T)(sc * qr[c]);
     }
   }
 }
 
 template <typename T>
 void launch_ebe(const EbeParams<T> &P, bool adj, cudaStream_t s) {
-  const int blocks = (P.n_rows + 255) / 256 < 4096 ? (P.n_rows + 255) / 256 : 4096;
+  if (P.n_blocks <= 0) return;
   if (adj)
-    k_ebe<T, true><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(P);
+    k_ebe<T, true><<<P.n_blocks, EBE_THREADS, P.smem, s>>>(P);
   else
-    k_ebe<T, false><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(P);
+    k_ebe<T, false><<<P.n_blocks, EBE_THREADS, P.smem, s>>>(P);
 }
 
 template void launch_ebe<float>(const EbeParams<float> &, bool, cudaStream_t);
 template void launch_ebe<double>(const EbeParams<double> &, bool, cudaStream_t);
+
+cudaError_t prepare_ebe_kernels() {
+  const int lim = EBE_SMEM_BUDGET;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_ebe<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+      (e = cudaFuncSetAttribute(k_ebe<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+      (e = cudaFuncSetAttribute(k_ebe<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+      (e = cudaFuncSetAttribute(k_ebe<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)))
+    return e;
+  return cudaSuccess;
+}
 
 // New nodes of a refined mesh: the update of the step kernels for interior
 // FEM rows, E^{n+1} = E^n + q1 (E^n - E^{n-1}) - q2 tau^2 R (R from k_ebe), the

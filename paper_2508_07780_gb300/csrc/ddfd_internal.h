@@ -133,17 +133,59 @@ void launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s);
 template <typename T, int NB>
 void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s);
 
-// Element-by-element FEM apply over an explicit tetrahedral mesh.
+// Element-by-element FEM apply over an explicit tetrahedral mesh, staged in
+// shared memory block by block.  A block holds up to EBE_RB rows (nearby
+// nodes), every tet incident to them and every node of those tets; one CTA
+// copies the block's tets into shared memory, gathers its nodes' values, and
+// then sums each row over its incident tets from shared memory only.
+constexpr int EBE_RB = 128;                  // rows per block
+constexpr int EBE_TPR = 4;                   // threads per row
+constexpr int EBE_THREADS = EBE_TPR * EBE_RB;
+constexpr int EBE_SMEM_BUDGET = 100 * 1024;  // per block: two CTAs per SM
+constexpr uint16_t EBE_PAD = 0xFFFF;         // unused incidence slot
+
+// One block.  Its blob (16-byte aligned, a multiple of 16 bytes) holds, for
+// its nt tets (nt even; a padding tet has zero gradients), sqrt|K| times the
+// P1 gradients [nt][4][3] (element type T), the tets' local node ids
+// [nt][4] (uint16), and the rows' incidences [maxinc][EBE_RB] (uint16:
+// local tet << 2 | the row's vertex in it, EBE_PAD where a row has fewer).
+struct EbeBlock {
+  long long blob;  // byte offset of the blob
+  int bytes;       // blob size
+  int nt;          // tets
+  int nn;          // nodes (their padded offsets at nodes[node0 ..])
+  int maxinc;      // incidences of the block's busiest row
+  int nrows;       // rows (their indices at rows[row0 ..])
+  int node0, row0;
+};
+
+// Host packer: rows in brick order of their positions, cut greedily into
+// blocks under EBE_RB rows and EBE_SMEM_BUDGET bytes of shared memory.
+// tnode: [ntet][4] padded node offsets; tgrad: [ntet][12] sqrt|K| g (FP64);
+// rptr / itet / iloc: each row's incidences; rpos: [n_rows][3] node
+// positions in units of h; esz: sizeof(T) of the kernel.
+struct EbePack {
+  std::vector<EbeBlock> blocks;
+  std::vector<unsigned char> blob;
+  std::vector<int> nodes, rows;
+  int smem = 0;  // dynamic shared memory of the largest block
+};
+bool pack_ebe_blocks(long long n_rows, long long ntet, const int *tnode, const double *tgrad, const int *rptr,
+                     const int *itet, const int *iloc, const double *rpos, int esz, EbePack *out, std::string *err);
+// Shared-memory bytes of a block with nt tets, nn nodes, maxinc incidences.
+long long ebe_block_smem(long long nt, long long nn, long long maxinc, int esz);
+
 template <typename T>
 struct EbeParams {
   int n_rows;               // FEM-updated nodes
   const int *row_node;      // padded offset of each row's node
-  const int *row_ptr;       // incidences of row r: [row_ptr[r], row_ptr[r+1])
-  const int *inc_tet;       // incident tet
-  const int *inc_local;     // the row's vertex index (0..3) in that tet
-  const int *tet_node;      // [T][4] padded offsets
-  const T *tet_grad;        // [T][4][3] sqrt|K| times the P1 gradients
   const double *scale;      // h^2 / m of each row (lumped P1 mass)
+  int n_blocks;
+  const EbeBlock *blocks;
+  const unsigned char *blob;
+  const int *blk_nodes;     // padded node offsets of the blocks' nodes
+  const int *blk_rows;      // row indices of the blocks' rows
+  int smem;                 // dynamic shared memory per CTA
   const T *field;           // E^n (forward) or mu^k (adjoint), padded, 3 components
   const T *s;               // eps - 1, padded (coefficient channel 0)
   long long cs;             // component stride
@@ -155,6 +197,8 @@ struct EbeParams {
   const T *xs;
   int n_new;
 };
+// Sets the shared-memory limit of the gather kernels (once, before any launch).
+cudaError_t prepare_ebe_kernels();
 template <typename T>
 void launch_ebe(const EbeParams<T> &P, bool adj, cudaStream_t s);
 
