@@ -360,7 +360,7 @@ int capture_slot(const ddfd_problem *p, int step) {
 // The element-by-element rows of the current level (fem_kind = DDFD_FEM_EBE).
 template <typename T>
 void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, int64_t *nk,
-                 const void *xfield = nullptr) {
+                 const void *xfield = nullptr, int *err = nullptr) {
   if (!p->ebe_rows) return;
   EbeParams<T> E;
   E.n_rows = p->ebe_rows;
@@ -371,7 +371,9 @@ void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, 
   E.blob = p->ebe_blob;
   E.blk_nodes = p->ebe_blk_nodes;
   E.blk_rows = p->ebe_blk_rows;
-  E.smem = p->ebe_smem;
+  E.stage_bytes = p->ebe_smem;
+  E.err = err ? err : p->errflag;
+  E.spin_limit = 1u << 22;
   E.field = (const T *)field;
   E.s = (const T *)p->kcoef;
   E.cs = p->cs;
@@ -708,7 +710,7 @@ int upload_ebe(ddfd_problem *p, long long rows, long long ntet, const std::vecto
   CK(cudaMemcpy(p->ebe_blk_nodes, pk.nodes.data(), pk.nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(p->ebe_blk_rows, pk.rows.data(), pk.rows.size() * sizeof(int), cudaMemcpyHostToDevice));
   p->ebe_nblocks = (int)pk.blocks.size();
-  p->ebe_smem = pk.smem;
+  p->ebe_smem = (pk.smem + 127) & ~127;  // one pipeline stage
   p->ebe_rows = (int)rows;
   return DDFD_OK;
 }
@@ -965,7 +967,7 @@ int check_err(ddfd_problem *p) {
   CK(cudaStreamSynchronize(p->stream));
   if (e) {
     CK(cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream));
-    return fail(p, DDFD_E_TIMEOUT, "a step kernel gave up a bounded wait on its TMA pipeline");
+    return fail(p, DDFD_E_TIMEOUT, "a kernel gave up a bounded wait on its TMA copies");
   }
   return DDFD_OK;
 }
@@ -1664,7 +1666,7 @@ int enqueue_batch_forward(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
                        (p->nsnap || p->fonly) ? nullptr : (T *)p->hist + (size_t)(st + 1) * 3 * p->n_free);
     };
     // element-by-element members: their FEM rows of this level first
-    for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->E[ic], false, sm, nk, p->X[ic]);
+    for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->E[ic], false, sm, nk, p->X[ic], b->errflag);
     launch_groups<T>(b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io], fill, sm, nk);
     for (ddfd_problem *p : b->m)
       if (p->n_new) {
@@ -1716,7 +1718,7 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
       }
       int fc = 1, fo = 0;
       for (int st = n0; st < n1; ++st) {
-        for (int i : ck) enqueue_ebe<T>(b->m[i], b->m[i]->E[fc], false, sm, nk, b->m[i]->X[fc]);
+        for (int i : ck) enqueue_ebe<T>(b->m[i], b->m[i]->E[fc], false, sm, nk, b->m[i]->X[fc], b->errflag);
         launch_groups<T>(
             b, false, ck, b->maps.E_halo[fc], b->maps.E_ctr[fo],
             [&](StepParams<T> &P, ddfd_problem *p) {
@@ -1731,7 +1733,7 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
         const long long hk = p->nsnap ? k - n0 : k;
         set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free, Nt);
       };
-      for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk, p->XMu[ic]);
+      for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk, p->XMu[ic], b->errflag);
       launch_groups<T>(b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io], fill, sm, nk);
       for (ddfd_problem *p : b->m)
         if (p->n_new) {
@@ -1808,7 +1810,7 @@ int batch_check_err(ddfd_batch *b) {
   BCK(cudaStreamSynchronize(b->stream));
   if (e) {
     BCK(cudaMemsetAsync(b->errflag, 0, sizeof(int), b->stream));
-    return bfail(b, DDFD_E_TIMEOUT, "a step kernel gave up a bounded wait on its TMA pipeline");
+    return bfail(b, DDFD_E_TIMEOUT, "a kernel gave up a bounded wait on its TMA copies");
   }
   return DDFD_OK;
 }

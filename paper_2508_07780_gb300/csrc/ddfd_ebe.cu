@@ -14,15 +14,16 @@
 // step kernel's units, R = h^2 M^-1 (K E), and, in the adjoint, also
 // q = h^2 M^-1 (D^T D mu) for the gradient.
 //
-// Staging: one CTA per block of nearby rows (EbeBlock).  The block's tets
-// arrive as one contiguous blob (16-byte loads), its nodes' values are
-// gathered once into shared memory, the tet divergences
+// Staging: blocks of nearby rows (EbeBlock), double-buffered in shared
+// memory by a persistent CTA per SM.  A block's tets arrive as one bulk copy,
+// its nodes' values are gathered once into shared memory, the tet divergences
 // sum_b g_b . (s_b E_b) are formed once per tet, and each row then sums its
 // incident tets from shared memory (EBE_TPR threads per row, each summing
 // every EBE_TPR-th incidence, combined in a fixed order).
 #include <cuda_runtime.h>
 
 #include "ddfd_internal.h"
+#include "ddfd_tma.h"
 
 namespace ddfd {
 
@@ -59,160 +60,195 @@ __device__ __forceinline__ void ld_node(const double *n, double v[4]) {
   v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
 }
 
-// Running sum with Kahan compensation: the FP32 rows sum 24 to 60 element
-// terms without FP64 arithmetic (scarce on this part) and keep an error
-// close to one rounding of the total.
-template <typename T>
-struct KSum {
-  T s = T(0), c = T(0);
-  __device__ __forceinline__ void add(T x) {
-    if (sizeof(T) == 8) {
-      s += x;
-    } else {
-      const T y = x - c, t = s + y;
-      c = (t - s) - y;
-      s = t;
-    }
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
+// Starts the copies of block `bi` into stage buffer D: the blob by one bulk
+// copy (thread 0, counted on bar), the node values by per-thread copies.
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(EBE_THREADS, 2) k_ebe(const EbeParams<T> P) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  const EbeBlock B = P.blocks[blockIdx.x];
-  const int tid = threadIdx.x;
-  // 1. the block's tets and incidences
-  {
-    const uint4 *src = reinterpret_cast<const uint4 *>(P.blob + B.blob);
-    uint4 *dst = reinterpret_cast<uint4 *>(sm);
-    const int nv = B.bytes >> 4;
-#pragma unroll 4
-    for (int i = tid; i < nv; i += EBE_THREADS) dst[i] = __ldg(src + i);
+__device__ __forceinline__ EbeBlock ebe_issue(const EbeParams<T> &P, int bi, unsigned char *D, uint64_t *bar) {
+  const EbeBlock N = P.blocks[bi];
+  if (threadIdx.x == 0) {
+    fence_proxy_async_smem();  // earlier reads of this buffer (ordered by the last barrier) come first
+    mbar_expect_tx(bar, (uint32_t)N.bytes);
+    bulk_load(D, P.blob + N.blob, (uint32_t)N.bytes, bar);
   }
-  // 2. the values of its nodes: field components and s
-  T *sN = reinterpret_cast<T *>(sm + B.bytes);
-  T *sD = sN + ((4 * B.nn * (int)sizeof(T) + 15) & ~15) / (int)sizeof(T);
-  for (int i = tid; i < B.nn; i += EBE_THREADS) {
-    const int o = P.blk_nodes[B.node0 + i];
-    T v0, v1, v2, sv;
+  T *sN = reinterpret_cast<T *>(D + N.bytes);
+  for (int i = threadIdx.x; i < N.nn; i += EBE_THREADS) {
+    const int o = P.blk_nodes[N.node0 + i];
+    const T *f0, *f1, *f2, *sv;
     if (o < P.cs) {
-      v0 = P.field[o];
-      v1 = P.field[P.cs + o];
-      v2 = P.field[2 * P.cs + o];
-      sv = ADJ ? T(1) : P.s[o];
+      f0 = P.field + o;
+      f1 = P.field + P.cs + o;
+      f2 = P.field + 2 * P.cs + o;
+      sv = P.s + o;
     } else {
       const long long e = o - P.cs;
-      v0 = P.xfield[e];
-      v1 = P.xfield[P.n_new + e];
-      v2 = P.xfield[2LL * P.n_new + e];
-      sv = ADJ ? T(1) : P.xs[e];
+      f0 = P.xfield + e;
+      f1 = P.xfield + P.n_new + e;
+      f2 = P.xfield + 2LL * P.n_new + e;
+      sv = P.xs + e;
     }
-    sN[4 * i + 0] = v0;
-    sN[4 * i + 1] = v1;
-    sN[4 * i + 2] = v2;
-    sN[4 * i + 3] = sv;
+    if (sizeof(T) == 4) {
+      cp_async4(sN + 4 * i + 0, f0);
+      cp_async4(sN + 4 * i + 1, f1);
+      cp_async4(sN + 4 * i + 2, f2);
+      if (!ADJ) cp_async4(sN + 4 * i + 3, sv);
+    } else {
+      cp_async8(sN + 4 * i + 0, f0);
+      cp_async8(sN + 4 * i + 1, f1);
+      cp_async8(sN + 4 * i + 2, f2);
+      if (!ADJ) cp_async8(sN + 4 * i + 3, sv);
+    }
+    if (ADJ) sN[4 * i + 3] = T(1);
+  }
+  cp_async_commit();
+  return N;
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(EBE_THREADS, 1) k_ebe(const EbeParams<T> P) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ int s_ok;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm);  // one mbarrier per stage
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
   }
   __syncthreads();
-  const T *sG = reinterpret_cast<const T *>(sm);
-  const uint2 *sT = reinterpret_cast<const uint2 *>(sm + (size_t)B.nt * 12 * sizeof(T));  // 4 x uint16 per tet
-  const uint16_t *sI = reinterpret_cast<const uint16_t *>(sT + B.nt);
-  // 3. per tet: sum_b s_b (g_b . E_b) (forward), sum_b g_b . mu_b (adjoint)
-  for (int t = tid; t < B.nt; t += EBE_THREADS) {
-    T g[12];
-    ld_grad(sG + 12 * t, g);
-    const uint2 nd = sT[t];
-    const int ids[4] = {(int)(nd.x & 0xFFFF), (int)(nd.x >> 16), (int)(nd.y & 0xFFFF), (int)(nd.y >> 16)};
-    T div = T(0);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      T v[4];
-      ld_node(sN + 4 * ids[b], v);
-      div += v[3] * (g[3 * b + 0] * v[0] + g[3 * b + 1] * v[1] + g[3 * b + 2] * v[2]);
+  uint32_t parity = 0u;  // bit s: the phase stage s waits for
+  int st = 0;
+  auto stage = [&](int q) { return sm + 128 + (size_t)q * P.stage_bytes; };
+  int bi = blockIdx.x;
+  EbeBlock B;
+  if (bi < P.n_blocks) B = ebe_issue<T, ADJ>(P, bi, stage(0), &bar[0]);
+  for (; bi < P.n_blocks; bi += gridDim.x) {
+    cp_async_wait_all();
+    if (tid == 0) s_ok = mbar_wait_bounded(bar + st, (parity >> st) & 1u, P.spin_limit) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+      // the copy still in flight is this stage's: wait for it (bounded) and stop
+      if (tid == 0) {
+        atomicOr(P.err, 8);
+        mbar_wait_bounded(bar + st, (parity >> st) & 1u, P.spin_limit);
+      }
+      break;
     }
-    sD[t] = div;
-  }
-  __syncthreads();
-  // 4. rows: EBE_TPR threads per row, thread j of a row sums incidences j, j + EBE_TPR, ...
-  const int lr = tid / EBE_TPR, j = tid % EBE_TPR;
-  KSum<T> y[3], q[3];
-  if (lr < B.nrows) {
-    for (int e = j; e < B.maxinc; e += EBE_TPR) {
-      const uint16_t code = sI[e * EBE_RB + lr];
-      if (code == EBE_PAD) break;
-      const int t = code >> 2, a = code & 3;
+    parity ^= 1u << st;
+    EbeBlock next = B;
+    if (bi + (int)gridDim.x < P.n_blocks) next = ebe_issue<T, ADJ>(P, bi + gridDim.x, stage(st ^ 1), bar + (st ^ 1));
+
+    unsigned char *S = stage(st);
+    const T *sG = reinterpret_cast<const T *>(S);
+    const uint2 *sT = reinterpret_cast<const uint2 *>(S + (size_t)B.nt * 12 * sizeof(T));  // 4 x uint16 per tet
+    const uint16_t *sI = reinterpret_cast<const uint16_t *>(sT + B.nt);
+    const T *sN = reinterpret_cast<const T *>(S + B.bytes);
+    T *sD = reinterpret_cast<T *>(S + B.bytes + ((4 * B.nn * (int)sizeof(T) + 15) & ~15));
+    // per tet: sum_b s_b (g_b . E_b) (forward), sum_b g_b . mu_b (adjoint)
+    for (int t = tid; t < B.nt; t += EBE_THREADS) {
       T g[12];
       ld_grad(sG + 12 * t, g);
       const uint2 nd = sT[t];
       const int ids[4] = {(int)(nd.x & 0xFFFF), (int)(nd.x >> 16), (int)(nd.y & 0xFFFF), (int)(nd.y >> 16)};
-      // g_a by selection (a dynamic index would put g in local memory)
-      T ga0 = g[0], ga1 = g[1], ga2 = g[2];
-#pragma unroll
-      for (int b = 1; b < 4; ++b)
-        if (a == b) ga0 = g[3 * b + 0], ga1 = g[3 * b + 1], ga2 = g[3 * b + 2];
-      T lap0 = T(0), lap1 = T(0), lap2 = T(0);
+      T div = T(0);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         T v[4];
         ld_node(sN + 4 * ids[b], v);
-        const T w = ga0 * g[3 * b + 0] + ga1 * g[3 * b + 1] + ga2 * g[3 * b + 2];
-        lap0 += w * v[0];
-        lap1 += w * v[1];
-        lap2 += w * v[2];
+        div += v[3] * (g[3 * b + 0] * v[0] + g[3 * b + 1] * v[1] + g[3 * b + 2] * v[2]);
       }
-      const T div = sD[t];
-      y[0].add(lap0);
-      y[1].add(lap1);
-      y[2].add(lap2);
-      q[0].add(ga0 * div);
-      q[1].add(ga1 * div);
-      q[2].add(ga2 * div);
+      sD[t] = div;
     }
-  }
-  // the row's partial sums, combined in a fixed order (bitwise reproducible)
-  double yr[3], qr[3];
+    __syncthreads();
+    // rows: thread j of a row sums its incidences j, j + EBE_TPR, ... (in T:
+    // at most a few terms each, as the stencil rows do)
+    const int lr = tid / EBE_TPR, j = tid % EBE_TPR;
+    T y[3] = {T(0), T(0), T(0)}, q[3] = {T(0), T(0), T(0)};
+    if (lr < B.nrows) {
+      for (int e = j; e < B.maxinc; e += EBE_TPR) {
+        const uint16_t code = sI[e * EBE_RB + lr];
+        if (code == EBE_PAD) break;
+        const int t = code >> 2, a = code & 3;
+        T g[12];
+        ld_grad(sG + 12 * t, g);
+        const uint2 nd = sT[t];
+        const int ids[4] = {(int)(nd.x & 0xFFFF), (int)(nd.x >> 16), (int)(nd.y & 0xFFFF), (int)(nd.y >> 16)};
+        // g_a by selection (a dynamic index would put g in local memory)
+        T ga0 = g[0], ga1 = g[1], ga2 = g[2];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    yr[c] = y[c].value();
-    qr[c] = q[c].value();
+        for (int b = 1; b < 4; ++b)
+          if (a == b) ga0 = g[3 * b + 0], ga1 = g[3 * b + 1], ga2 = g[3 * b + 2];
+        T lap0 = T(0), lap1 = T(0), lap2 = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          T v[4];
+          ld_node(sN + 4 * ids[b], v);
+          const T w = ga0 * g[3 * b + 0] + ga1 * g[3 * b + 1] + ga2 * g[3 * b + 2];
+          lap0 += w * v[0];
+          lap1 += w * v[1];
+          lap2 += w * v[2];
+        }
+        const T div = sD[t];
+        y[0] += lap0;
+        y[1] += lap1;
+        y[2] += lap2;
+        q[0] += ga0 * div;
+        q[1] += ga1 * div;
+        q[2] += ga2 * div;
+      }
+    }
+    // the row's partial sums, merged by a butterfly (a + b == b + a, so all
+    // lanes of the row hold the same bits; the order is fixed: reproducible)
 #pragma unroll
     for (int m = 1; m < EBE_TPR; m <<= 1) {
-      yr[c] += __shfl_xor_sync(0xffffffffu, yr[c], m);
-      qr[c] += __shfl_xor_sync(0xffffffffu, qr[c], m);
-    }
-  }
-  if (j == 0 && lr < B.nrows) {
-    const int r = P.blk_rows[B.row0 + lr];
-    const double sc = P.scale[r];  // h^2 / m_a
-    const double sa = ADJ ? (double)node_s(P, P.row_node[r]) : 1.0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      P.out_r[c * (long long)P.n_rows + r] = (T)(sc * (yr[c] + sa * qr[c]));
-      if (ADJ) P.out_q[c * (long long)P.n_rows + r] = (T)(sc * qr[c]);
+      for (int c = 0; c < 3; ++c) {
+        y[c] += __shfl_xor_sync(0xffffffffu, y[c], m);
+        q[c] += __shfl_xor_sync(0xffffffffu, q[c], m);
+      }
     }
+    if (j == 0 && lr < B.nrows) {
+      const int r = P.blk_rows[B.row0 + lr];
+      const T sc = (T)P.scale[r];  // h^2 / m_a
+      const T sa = ADJ ? node_s(P, P.row_node[r]) : T(1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        P.out_r[c * (long long)P.n_rows + r] = sc * (y[c] + sa * q[c]);
+        if (ADJ) P.out_q[c * (long long)P.n_rows + r] = sc * q[c];
+      }
+    }
+    st ^= 1;
+    B = next;
   }
 }
+
+static int g_ebe_ctas = 0;  // one CTA per SM
 
 template <typename T>
 void launch_ebe(const EbeParams<T> &P, bool adj, cudaStream_t s) {
   if (P.n_blocks <= 0) return;
+  const int ctas = g_ebe_ctas > 0 ? g_ebe_ctas : 1;
+  const int grid = P.n_blocks < ctas ? P.n_blocks : ctas;
+  const size_t smem = 128 + 2 * (size_t)P.stage_bytes;
   if (adj)
-    k_ebe<T, true><<<P.n_blocks, EBE_THREADS, P.smem, s>>>(P);
+    k_ebe<T, true><<<grid, EBE_THREADS, smem, s>>>(P);
   else
-    k_ebe<T, false><<<P.n_blocks, EBE_THREADS, P.smem, s>>>(P);
+    k_ebe<T, false><<<grid, EBE_THREADS, smem, s>>>(P);
 }
 
 template void launch_ebe<float>(const EbeParams<float> &, bool, cudaStream_t);
 template void launch_ebe<double>(const EbeParams<double> &, bool, cudaStream_t);
 
 cudaError_t prepare_ebe_kernels() {
-  const int lim = EBE_SMEM_BUDGET;
+  const int lim = 128 + 2 * EBE_SMEM_BUDGET;
+  int dev = 0, sms = 0;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_ebe<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaFuncSetAttribute(k_ebe<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
       (e = cudaFuncSetAttribute(k_ebe<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
       (e = cudaFuncSetAttribute(k_ebe<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) ||
       (e = cudaFuncSetAttribute(k_ebe<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)))
     return e;
+  g_ebe_ctas = sms > 0 ? sms : 1;
   return cudaSuccess;
 }
 

@@ -139,11 +139,15 @@ void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s);
 // copies the block's tets into shared memory, gathers its nodes' values, and
 // then sums each row over its incident tets from shared memory only.
 constexpr int EBE_RB = 128;                  // rows per block
-constexpr int EBE_TPR = 4;                   // threads per row
+constexpr int EBE_TPR = 8;                   // threads per row
 constexpr int EBE_THREADS = EBE_TPR * EBE_RB;
-constexpr int EBE_SMEM_BUDGET = 100 * 1024;  // per block: two CTAs per SM
+constexpr int EBE_SMEM_BUDGET = 100 * 1024;  // per block (one of two pipeline stages)
 constexpr uint16_t EBE_PAD = 0xFFFF;         // unused incidence slot
 
+// The kernel is persistent (one CTA per SM) and double-buffered: while it
+// sums one block, the next block's blob arrives by bulk copy and its nodes by
+// per-thread asynchronous copies.
+//
 // One block.  Its blob (16-byte aligned, a multiple of 16 bytes) holds, for
 // its nt tets (nt even; a padding tet has zero gradients), sqrt|K| times the
 // P1 gradients [nt][4][3] (element type T), the tets' local node ids
@@ -185,7 +189,9 @@ struct EbeParams {
   const unsigned char *blob;
   const int *blk_nodes;     // padded node offsets of the blocks' nodes
   const int *blk_rows;      // row indices of the blocks' rows
-  int smem;                 // dynamic shared memory per CTA
+  int stage_bytes;          // shared memory of one pipeline stage (>= every block's)
+  int *err;                 // bit 8: a bounded wait for a block's copy gave up
+  uint32_t spin_limit;      // polls per bounded wait
   const T *field;           // E^n (forward) or mu^k (adjoint), padded, 3 components
   const T *s;               // eps - 1, padded (coefficient channel 0)
   long long cs;             // component stride

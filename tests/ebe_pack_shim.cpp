@@ -38,3 +38,10 @@ extern "C" void ebe_pack_fetch(long long *blocks, unsigned char *blob, int *node
 extern "C" long long ebe_pack_smem(long long nt, long long nn, long long maxinc, int esz) {
   return ddfd::ebe_block_smem(nt, nn, maxinc, esz);
 }
+
+// rows per block, shared-memory budget, padding code
+extern "C" void ebe_pack_consts(int *v) {
+  v[0] = ddfd::EBE_RB;
+  v[1] = ddfd::EBE_SMEM_BUDGET;
+  v[2] = ddfd::EBE_PAD;
+}

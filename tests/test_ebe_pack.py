@@ -24,7 +24,6 @@ from synth.mesh import kuhn_cube, refined_fem_mesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2508_07780_gb300", "csrc")
-RB, BUDGET, PAD = 128, 100 * 1024, 0xFFFF
 
 
 def _cuda_include():
@@ -47,6 +46,9 @@ def lib(tmp_path_factory):
     L = ctypes.CDLL(out)
     L.ebe_pack_smem.restype = ctypes.c_longlong
     L.ebe_pack_smem.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int]
+    v = (ctypes.c_int * 3)()
+    L.ebe_pack_consts(v)
+    L.RB, L.BUDGET, L.PAD = v[0], v[1], v[2]
     return L
 
 
@@ -144,7 +146,8 @@ def direct_rows(m, field, s):
 def emulate(lib, m, esz, field, s):
     blocks, blob, nodes, rows, smem = pack(lib, m, esz)
     ft = np.float32 if esz == 4 else np.float64
-    assert smem <= BUDGET
+    RB, PAD = lib.RB, lib.PAD
+    assert smem <= lib.BUDGET
     seen = np.zeros(m["rows"], np.int64)
     y = np.zeros((m["rows"], 3))
     for blob_off, nbytes, nt, nn, maxinc, nrows, node0, row0 in blocks:
@@ -218,4 +221,4 @@ def test_pack_of_a_refined_mesh_reproduces_the_element_loop(lib, esz):
     tol = 1e-5 if esz == 4 else 1e-13
     assert np.abs(y - ref).max() <= tol * np.abs(ref).max()
     # several blocks, and in FP64 the byte budget (not only the row count) cuts them
-    assert blocks.shape[0] > m["rows"] // RB
+    assert blocks.shape[0] > m["rows"] // lib.RB
