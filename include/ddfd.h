@@ -31,7 +31,9 @@
  *
  * Conventions:
  *   - every call returns a ddfd_status; nothing is thrown across the ABI;
- *   - on error, outputs are untouched and ddfd_last_error() holds a message;
+ *   - on error, outputs are untouched and ddfd_last_error() holds a message
+ *     (one stated exception: ddfd_cg_run hands back the records and the
+ *     iterate of a run that failed part-way);
  *   - the caller owns every buffer it passes; host inputs are copied before
  *     the call returns; device pointers must stay valid until the call
  *     returns (the library synchronises its stream before returning from
