@@ -40,6 +40,16 @@ div(eps E) ~ eps div E is not applied):
             + sum_{n=0}^{Nt-1} m_i mu^n_i . (E^{n+1} - E^{n-1})_i / (2 tau)
 term by term the discrete forms of -int d_t lambda d_t E, int div lambda div E
 and int lambda d_t E; f1 = 0 (eq. model1) removes the lambda(0) f1 term.
+
+Paper-literal variant (gradient_literal): eq. gradeps as printed, with the
+approximation div(eps_bar E) ~ eps_bar div E made under it.  The time terms
+and g_sig are those above; the Gauss-law term becomes the lumped quadrature
+of int phi_i div lambda div E over the tets K around node i (P1 divergences
+are constant on K, int_K phi_i = |K|/4):
+  sum_{n=0}^{Nt-1} sum_{K ni i} |K|/4 (div E^n)_K (div P mu^n)_K
+instead of sum_K |K| (grad phi_i . E^n_i) (div P mu^n)_K.  Summed over every
+node of the tets, the two agree (both are sum_K |K| (div E)_K (div P mu)_K);
+node by node they differ by the dropped grad(eps_bar) . E term.
 """
 from __future__ import annotations
 
@@ -218,6 +228,37 @@ class OracleProblem:
             ge += m * np.sum(mu * (Ep1 - 2.0 * E0 + Em1), axis=0) / tau ** 2
             ge += np.sum(E0 * adj.dtd_free[n], axis=0)
             gs += m * np.sum(mu * (Ep1 - Em1), axis=0) / (2.0 * tau)
+        return ge, gs
+
+    def literal_div_term(self, E: np.ndarray, mu: np.ndarray) -> np.ndarray:
+        """sum_{K ni i} |K|/4 (div E)_K (div P mu)_K at every node (paper-literal
+        Gauss-law term of eq. gradeps for one time level; E, mu: (3, nn))."""
+        op = self.op
+        dE = op.D @ E.ravel()                                   # sqrt|K| (div E)_K
+        dM = op.D @ (op.fem_mask[None, :] * mu).ravel()         # sqrt|K| (div P mu)_K
+        prod = 0.25 * dE * dM
+        out = np.zeros(self.g.nn)
+        for q in range(4):
+            np.add.at(out, op.tets[:, q], prod)
+        return out
+
+    def gradient_literal(self, fwds, adjs):
+        """The paper-literal gradient (module docstring).  Needs every forward
+        level 0..Nt and every adjoint level 0..Nt-1 kept (keep_fields)."""
+        free = self.g.free_nodes
+        m = self.op.m[free]
+        ge = self.gamma_eps * m * (self.op.eps[free] - self.eps0)
+        gs = self.gamma_sig * m * (self.op.sig[free] - self.sig0)
+        Nt = self.n_steps
+        for f, a in zip(fwds, adjs):
+            if any(n not in f.fields for n in range(Nt)) or any(n not in a.fields for n in range(Nt)):
+                raise ValueError("gradient_literal needs the full forward and adjoint fields (keep_fields)")
+            for n in range(Nt):
+                Em1, E0, Ep1 = f.E_free[n], f.E_free[n + 1], f.E_free[n + 2]
+                mu = a.mu_free[n]
+                ge += m * np.sum(mu * (Ep1 - 2.0 * E0 + Em1), axis=0) / self.tau ** 2
+                ge += self.literal_div_term(f.fields[n], a.fields[n])[free]
+                gs += m * np.sum(mu * (Ep1 - Em1), axis=0) / (2.0 * self.tau)
         return ge, gs
 
     def gradient(self, fwds, adjs):
