@@ -337,7 +337,7 @@ def run_ours(args, w, rank, world, local_rank):
     src_dir = w.directions() if world == 1 else shard_directions(world)[rank:rank + 1]
     kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision=w.precision,
               src_dir=src_dir, det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
-              n_snapshots=args.snapshots, stream=stream.cuda_stream)
+              n_snapshots=args.snapshots, grad_variant=args.grad_variant, stream=stream.cuda_stream)
     p = Problem(**kw)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     # observed data: the layers-only model's trace (the inclusions are what
@@ -462,6 +462,8 @@ def run_ours(args, w, rank, world, local_rank):
                        "n_steps": w.n_steps, "n_src": w.n_src, "problems_per_gpu": 1,
                        "e_history": (f"checkpointing, {args.snapshots} snapshots, replayed segments"
                                      if args.snapshots else "full E history on the free nodes"),
+                       "gradient": ("exact derivative of the discrete J" if args.grad_variant == "exact" else
+                                    "paper-literal (Sec. 4, div(eps E) ~ eps div E; E kept on the FEM nodes)"),
                        "device_bytes": int(dev_bytes),
                        "l2": "inputs larger than L2: 2 field levels of 3 x n^3 plus the "
                              "E history on the free nodes, re-streamed every step",
@@ -504,6 +506,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 16-problem workload")
     ap.add_argument("--snapshots", type=int, default=0,
                     help="checkpointing with this many state snapshots instead of the full E history")
+    ap.add_argument("--grad-variant", choices=["exact", "literal"], default="exact",
+                    help="gradient form: the exact derivative of the discrete J (default) or the "
+                         "paper-literal one of Sec. 4")
     args = ap.parse_args()
     w = workload(args.workload)
     if args.precision:

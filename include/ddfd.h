@@ -71,6 +71,7 @@ enum { DDFD_SRC_GAUSS = 0, DDFD_SRC_SINE = 1 };  /* pulse shape, see ddfd_config
 /* FEM apply: Kuhn block stencil / element gather over the Kuhn split /
  * element gather over an explicit, locally refined mesh (mesh_* fields) */
 enum { DDFD_FEM_STENCIL = 0, DDFD_FEM_EBE = 1, DDFD_FEM_MESH = 2 };
+enum { DDFD_GRAD_EXACT = 0, DDFD_GRAD_LITERAL = 1 };  /* gradient form, see ddfd_config */
 enum {
   DDFD_ABS_BOTTOM = 1, DDFD_ABS_TOP = 2, /* top: only after the source phase */
   DDFD_ABS_X0 = 4, DDFD_ABS_X1 = 8, DDFD_ABS_Y0 = 16, DDFD_ABS_Y1 = 32
@@ -125,6 +126,13 @@ typedef struct {
   int64_t mesh_n_tets;
   const int32_t *mesh_tets;      /* [mesh_n_tets][4] */
   void *stream;          /* cudaStream_t for all work, or NULL for the default stream */
+  int32_t grad_variant;  /* DDFD_GRAD_EXACT (default): g is the exact derivative of the
+                            discrete J; DDFD_GRAD_LITERAL: eq. gradeps as printed in Sec. 4,
+                            with div(eps_bar E) ~ eps_bar div E (the Gauss-law term becomes
+                            sum_K |K|/4 (div E)_K (div mu)_K around each free node).  The
+                            literal variant keeps E on every FEM-updated node for every step
+                            and takes neither n_snapshots, forward_only, fem_kind other than
+                            DDFD_FEM_STENCIL, nor batches. */
 } ddfd_config;
 
 /* Fill *cfg with defaults: cfl 0.3, FP64, stencil FEM, 1 normal-incidence

@@ -53,7 +53,7 @@ class ddfd_config(ctypes.Structure):
         ("sig_max", c_double), ("n_snapshots", c_int32), ("cfl_check", c_int32),
         ("mem_budget", c_int64), ("tile_kz", c_int32), ("forward_only", c_int32),
         ("mesh_n_new", c_int32), ("mesh_parents", POINTER(c_int32)), ("mesh_n_tets", c_int64),
-        ("mesh_tets", POINTER(c_int32)), ("stream", c_void_p),
+        ("mesh_tets", POINTER(c_int32)), ("stream", c_void_p), ("grad_variant", c_int32),
     ]
 
 
@@ -243,6 +243,8 @@ def make_config(lib, kw, keep):
             cfg.stream = c_void_p(v)
         elif k == "precision" and isinstance(v, str):
             cfg.precision = DDFD_FP32 if v == "fp32" else DDFD_FP64
+        elif k == "grad_variant" and isinstance(v, str):
+            cfg.grad_variant = {"exact": 0, "literal": 1}[v]
         else:
             setattr(cfg, k, v)
     return cfg

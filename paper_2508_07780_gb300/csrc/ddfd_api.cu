@@ -55,6 +55,7 @@ struct ddfd_problem {
   void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr};
   void *kcoef = nullptr;      // padded full-grid (s, q1, q2), 3 channels
   void *hist = nullptr;       // E on the free nodes: every step, or one replayed segment
+  void *hist_fem = nullptr;   // literal gradient: E on the FEM-updated nodes, every step
   // checkpointing (n_snapshots > 0): state snapshots (E^n, E^{n-1}) at the
   // starts of segments of seg steps; the adjoint replays each segment
   int nsnap = 0, seg = 0;
@@ -162,6 +163,11 @@ int validate(const ddfd_config *c, std::string *m) {
   if (c->precision != DDFD_FP64 && c->precision != DDFD_FP32) return *m = "bad precision", DDFD_E_ARG;
   if (c->fem_kind != DDFD_FEM_STENCIL && c->fem_kind != DDFD_FEM_EBE && c->fem_kind != DDFD_FEM_MESH)
     return *m = "bad fem_kind", DDFD_E_ARG;
+  if (c->grad_variant != DDFD_GRAD_EXACT && c->grad_variant != DDFD_GRAD_LITERAL)
+    return *m = "bad grad_variant", DDFD_E_ARG;
+  if (c->grad_variant == DDFD_GRAD_LITERAL &&
+      (c->fem_kind != DDFD_FEM_STENCIL || c->n_snapshots > 0 || c->forward_only))
+    return *m = "grad_variant DDFD_GRAD_LITERAL takes the stencil FEM, the full history and an adjoint", DDFD_E_ARG;
   if (c->fem_kind == DDFD_FEM_MESH) {
     if (c->mesh_n_new < 0 || c->mesh_n_tets < 1 || !c->mesh_tets || (c->mesh_n_new > 0 && !c->mesh_parents))
       return *m = "fem_kind DDFD_FEM_MESH needs mesh_tets (and mesh_parents for new nodes)", DDFD_E_ARG;
@@ -448,6 +454,12 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
       enqueue_new_step<T>(p, p->X[ic], p->X[io], false, P, sm, nk);
       ++*nk;
       std::swap(ic, io);
+      if (p->hist_fem) {  // E^{st+1} on the FEM-updated nodes, for the literal gradient
+        const size_t nfu = (size_t)(p->b - p->a - 1) * (p->b - p->a - 1) * (p->b - p->a - 1);
+        launch_copy_fem_nodes<T>((const T *)p->E[ic], (T *)p->hist_fem + ((size_t)s * (Nt + 1) + st + 1) * 3 * nfu,
+                                 p->n, p->px, p->cs, p->a, p->b, sm);
+        ++*nk;
+      }
       if (s == 0) {
         const int sl = capture_slot(p, st + 1);
         if (sl >= 0)
@@ -512,6 +524,12 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
         launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
         enqueue_new_step<T>(p, p->XMu[ic], p->XMu[io], true, P, sm, nk);
         ++*nk;
+        if (p->hist_fem) {  // literal gradient: swap the Gauss-law term of step k (mu^k is still in Mu[ic])
+          const size_t nfu = (size_t)(p->b - p->a - 1) * (p->b - p->a - 1) * (p->b - p->a - 1);
+          launch_grad_literal<T>((const T *)p->hist_fem + ((size_t)s * (Nt + 1) + k) * 3 * nfu, (const T *)p->Mu[ic],
+                                 p->gacc, p->n, p->px, p->cs, p->a, p->b, p->tau * p->tau / (p->h * p->h), sm);
+          ++*nk;
+        }
         std::swap(ic, io);
         if (s == 0) {
           const int sl = capture_slot(p, k - 1);
@@ -1267,6 +1285,15 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
       (p->fp32 && (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gpart))))
     return bail(st);
   if (p->nsnap && (st = dalloc(p, (size_t)p->n_src * p->nsnap * 2 * fbytes, &p->snap))) return bail(st);
+  if (cfg->grad_variant == DDFD_GRAD_LITERAL) {
+    const size_t nfu = (size_t)(p->b - p->a - 1) * (p->b - p->a - 1) * (p->b - p->a - 1);
+    const size_t hb = (size_t)p->n_src * (p->Nt + 1) * 3 * nfu * p->esz;
+    if ((st = dalloc(p, hb, &p->hist_fem))) return bail(st);
+    if (cudaMemsetAsync(p->hist_fem, 0, hb, p->stream) != cudaSuccess) {
+      p->err = "cudaMemsetAsync of the FEM-node history failed";
+      return bail(DDFD_E_CUDA);
+    }
+  }
   bool any_oblique = false;
   for (int s = 0; s < p->n_src; ++s) any_oblique |= p->oblique[s] != 0;
   if (any_oblique && (st = dalloc_t(p, delay_host.size(), &p->delay))) return bail(st);
@@ -2126,6 +2153,10 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
     if (st) {
       g_create_err = "member " + std::to_string(i) + ": " + m;
       return st;
+    }
+    if (c.grad_variant != DDFD_GRAD_EXACT) {
+      g_create_err = "member " + std::to_string(i) + ": batches compute the exact gradient only";
+      return DDFD_E_ARG;
     }
     if (c.n != cfgs[0].n || c.n_steps != cfgs[0].n_steps || c.cfl != cfgs[0].cfl ||
         c.precision != cfgs[0].precision) {

@@ -205,6 +205,18 @@ struct EbeParams {
 };
 // Sets the shared-memory limit of the gather kernels (once, before any launch).
 cudaError_t prepare_ebe_kernels();
+
+// Paper-literal gradient (grad_variant = DDFD_GRAD_LITERAL).  copy: E on the
+// FEM-updated nodes (a, b)^3 into dst [3][(b-a-1)^3] (x fastest).  literal:
+// adds, for every free node i, r2/6 sum_{K ni i} (div mu)_K ((div E)_K / 4 -
+// grad phi_i . E_i) (Kuhn tets, divergences with unit gradients, r2 = tau^2/h^2)
+// to the eps accumulator gacc[i]: the literal Gauss-law term replaces the exact
+// one in the units the step kernels accumulate in.
+template <typename T>
+void launch_copy_fem_nodes(const T *E, T *dst, int n, int px, long long cs, int a, int b, cudaStream_t s);
+template <typename T>
+void launch_grad_literal(const T *Efem, const T *mu, double *gacc, int n, int px, long long cs, int a, int b,
+                         double r2, cudaStream_t s);
 template <typename T>
 void launch_ebe(const EbeParams<T> &P, bool adj, cudaStream_t s);
 

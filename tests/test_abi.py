@@ -97,3 +97,23 @@ def test_create_rejects_bad_refined_meshes(lib, mesh_kw, what):
     with pytest.raises(DDFDError) as e:
         Problem(n=13, fem_n=9, n_steps=3, **mesh_kw)
     assert e.value.code == -1 and what in str(e.value), str(e.value)
+
+
+@pytest.mark.parametrize("kw,what", [
+    (dict(grad_variant=2), "bad grad_variant"),
+    (dict(grad_variant="literal", n_snapshots=2), "full history"),
+    (dict(grad_variant="literal", fem_kind=1), "stencil FEM"),
+    (dict(grad_variant="literal", forward_only=1), "adjoint"),
+])
+def test_create_rejects_unsupported_literal_gradients(lib, kw, what):
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    with pytest.raises(DDFDError) as e:
+        Problem(n=13, fem_n=9, n_steps=3, **kw)
+    assert e.value.code == -1 and what in str(e.value), str(e.value)
+
+
+def test_create_batch_rejects_literal_gradients(lib):
+    from paper_2508_07780_gb300 import Batch, DDFDError
+    with pytest.raises(DDFDError) as e:
+        Batch([dict(n=21, fem_n=11, n_steps=3), dict(n=21, fem_n=11, n_steps=3, grad_variant="literal")])
+    assert e.value.code == -1 and "exact gradient only" in str(e.value), str(e.value)
