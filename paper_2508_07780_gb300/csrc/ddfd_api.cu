@@ -66,6 +66,9 @@ struct ddfd_problem {
   EbeBlock *ebe_blocks = nullptr;
   unsigned char *ebe_blob = nullptr;
   int ebe_nblocks = 0, ebe_smem = 0;
+  int *kuhn_list = nullptr;   // explicit-mesh rows taken from the Kuhn block stencil
+  int kuhn_n = 0;
+  double kuhn_B[8][9] = {};   // (D^T D)_{i,i+o} / h of the uniform Kuhn split
   void *ebe_out_r = nullptr, *ebe_out_q = nullptr;
   double *ebe_scale = nullptr;
   double *trace = nullptr, *res = nullptr, *eobs_stage = nullptr, *gacc = nullptr;
@@ -380,6 +383,24 @@ void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, 
   E.stage_bytes = p->ebe_smem;
   E.err = err ? err : p->errflag;
   E.spin_limit = 1u << 22;
+  if (p->kuhn_n) {
+    KuhnRowParams<T> K;
+    K.n_list = p->kuhn_n;
+    K.list = p->kuhn_list;
+    K.row_node = p->ebe_row_node;
+    K.field = (const T *)field;
+    K.s = (const T *)p->kcoef;
+    K.cs = p->cs;
+    K.px = p->px;
+    K.n = p->n;
+    K.out_r = (T *)p->ebe_out_r;
+    K.out_q = (T *)p->ebe_out_q;
+    K.n_rows = p->ebe_rows;
+    for (int o = 0; o < 8; ++o)
+      for (int e = 0; e < 9; ++e) K.B[o][e] = (T)p->kuhn_B[o][e];
+    launch_kuhn_rows<T>(K, adj, sm);
+    ++*nk;
+  }
   E.field = (const T *)field;
   E.s = (const T *)p->kcoef;
   E.cs = p->cs;
@@ -388,8 +409,10 @@ void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, 
   E.xfield = (const T *)xfield;
   E.xs = (const T *)p->xcoef;
   E.n_new = p->n_new;
-  launch_ebe<T>(E, adj, sm);
-  ++*nk;
+  if (p->ebe_nblocks > 0) {
+    launch_ebe<T>(E, adj, sm);
+    ++*nk;
+  }
 }
 
 // The new nodes of a refined mesh, one step (after the rows of enqueue_ebe).
@@ -708,12 +731,29 @@ int encode_field_maps(std::string *err, FieldMaps *fm, void *const E[2], void *c
 int upload_ebe(ddfd_problem *p, long long rows, long long ntet, const std::vector<int> &tnode,
                const std::vector<double> &tgrad, const std::vector<int> &rptr, const std::vector<int> &itet,
                const std::vector<int> &iloc, const std::vector<int> &rnode, const std::vector<double> &scale,
-               const std::vector<double> &rpos) {
+               const std::vector<double> &rpos, const std::vector<unsigned char> *stencil = nullptr) {
+  // rows marked in *stencil take the Kuhn block stencil; the others are gathered
+  std::vector<unsigned char> use;
+  std::vector<int> klist;
+  if (stencil) {
+    use.assign((size_t)rows, 1);
+    for (size_t r = 0; r < stencil->size(); ++r)
+      if ((*stencil)[r]) {
+        use[r] = 0;
+        klist.push_back((int)r);
+      }
+  }
   EbePack pk;
   std::string m;
   if (!pack_ebe_blocks(rows, ntet, tnode.data(), tgrad.data(), rptr.data(), itet.data(), iloc.data(), rpos.data(),
-                       (int)p->esz, &pk, &m))
+                       (int)p->esz, &pk, &m, stencil ? use.data() : nullptr))
     return fail(p, DDFD_E_ARG, m);
+  if (!klist.empty()) {
+    int st;
+    if ((st = dalloc_t(p, klist.size(), &p->kuhn_list))) return st;
+    CK(cudaMemcpy(p->kuhn_list, klist.data(), klist.size() * sizeof(int), cudaMemcpyHostToDevice));
+    p->kuhn_n = (int)klist.size();
+  }
   int st;
   const size_t es = p->esz;
   if ((st = dalloc_t(p, (size_t)rows, &p->ebe_row_node)) || (st = dalloc_t(p, (size_t)rows, &p->ebe_scale)) ||
@@ -948,8 +988,11 @@ int build_mesh(ddfd_problem *p) {
       }
   for (int e = 0; e < p->n_new; ++e)
     for (int d = 0; d < 3; ++d) rpos[3 * (grid_rows + e) + d] = X[(size_t)e * 3 + d] / p->h;
+  // grid rows whose elements are the 24 untouched Kuhn tets take the block stencil
+  std::vector<unsigned char> stencil;
+  kuhn_stencil_rows(grid_rows, n, rptr.data(), itet.data(), p->mesh_tets.data(), &stencil);
   int st;
-  if ((st = upload_ebe(p, rows, ntet, tnode, tgrad, rptr, itet, iloc, rnode, scale, rpos))) return st;
+  if ((st = upload_ebe(p, rows, ntet, tnode, tgrad, rptr, itet, iloc, rnode, scale, rpos, &stencil))) return st;
   const size_t es = p->esz, xb = 3 * (size_t)std::max(p->n_new, 1) * es;
   if ((st = dalloc_t(p, (size_t)p->n_free, &p->mass_free)) || (st = dalloc(p, xb, &p->X[0])) ||
       (st = dalloc(p, xb, &p->X[1])) || (st = dalloc(p, xb, &p->xcoef)) ||
@@ -1247,6 +1290,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
     p->err = "the Kuhn blocks assembled from the tetrahedra differ from the compiled-in table";
     return bail(DDFD_E_CUDA);
   }
+  std::memcpy(p->kuhn_B, kb.B, sizeof(p->kuhn_B));
   std::vector<double> delay_host;
   setup_sources(p, &delay_host);
   const size_t fbytes = 3 * (size_t)p->cs * p->esz;

@@ -221,6 +221,63 @@ __global__ void __launch_bounds__(EBE_THREADS, 1) k_ebe(const EbeParams<T> P) {
   }
 }
 
+// Kuhn stencil rows of an explicit mesh: the same R (and q) as the gather,
+// from the 15-point block stencil of the uniform Kuhn split, R = (6 v_i -
+// sum of the 6 axis neighbours) + sum_o B_o w_{i+o} with w = s E (forward);
+// adjoint R = (6 mu_i - ...) + s_i sum_o B_o mu_{i+o}, q = sum_o B_o mu_{i+o}.
+template <typename T, bool ADJ>
+__global__ void k_kuhn_rows(const KuhnRowParams<T> P) {
+  const long long sx = 1, sy = P.px, sz = (long long)P.px * P.n;
+  const long long off[7] = {sx, sy, sz, sx + sy, sx + sz, sy + sz, sx + sy + sz};
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < P.n_list; q += gridDim.x * blockDim.x) {
+    const int r = P.list[q];
+    const long long o = P.row_node[r];
+    T lap[3], g[3] = {T(0), T(0), T(0)};
+    const T s0 = P.s[o];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T *f = P.field + c * P.cs;
+      lap[c] = T(6) * f[o] - (((((f[o + sx] + f[o - sx]) + f[o + sy]) + f[o - sy]) + f[o + sz]) + f[o - sz]);
+    }
+    {
+      T w[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) w[d] = (ADJ ? T(1) : s0) * P.field[d * P.cs + o];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[c] += P.B[0][3 * c] * w[0] + P.B[0][3 * c + 1] * w[1] + P.B[0][3 * c + 2] * w[2];
+    }
+#pragma unroll
+    for (int b = 0; b < 7; ++b) {
+      const long long up = o + off[b], dn = o - off[b];
+      const T su = ADJ ? T(1) : P.s[up], sd = ADJ ? T(1) : P.s[dn];
+      T w[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) w[d] = su * P.field[d * P.cs + up] + sd * P.field[d * P.cs + dn];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        g[c] += P.B[b + 1][3 * c] * w[0] + P.B[b + 1][3 * c + 1] * w[1] + P.B[b + 1][3 * c + 2] * w[2];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      P.out_r[c * (long long)P.n_rows + r] = lap[c] + (ADJ ? s0 : T(1)) * g[c];
+      if (ADJ) P.out_q[c * (long long)P.n_rows + r] = g[c];
+    }
+  }
+}
+
+template <typename T>
+void launch_kuhn_rows(const KuhnRowParams<T> &P, bool adj, cudaStream_t s) {
+  if (P.n_list <= 0) return;
+  const int blocks = (P.n_list + 255) / 256 < 4096 ? (P.n_list + 255) / 256 : 4096;
+  if (adj)
+    k_kuhn_rows<T, true><<<blocks, 256, 0, s>>>(P);
+  else
+    k_kuhn_rows<T, false><<<blocks, 256, 0, s>>>(P);
+}
+
+template void launch_kuhn_rows<float>(const KuhnRowParams<float> &, bool, cudaStream_t);
+template void launch_kuhn_rows<double>(const KuhnRowParams<double> &, bool, cudaStream_t);
+
 static int g_ebe_ctas = 0;  // one CTA per SM
 
 template <typename T>

@@ -28,8 +28,46 @@ long long ebe_block_smem(long long nt, long long nn, long long maxinc, int esz) 
   return blob_bytes(nt, maxinc, esz) + align16(nn * 4LL * esz) + align16(nt * (long long)esz);
 }
 
+void kuhn_stencil_rows(long long n_grid_rows, int n, const int *rptr, const int *itet, const int *tet_ids,
+                       std::vector<unsigned char> *is_stencil) {
+  const long long n3 = (long long)n * n * n;
+  is_stencil->assign((size_t)n_grid_rows, 0);
+  auto kuhn_tet = [&](long long t) {
+    long long v[4][3];
+    for (int q = 0; q < 4; ++q) {
+      const long long id = tet_ids[4 * t + q];
+      if (id < 0 || id >= n3) return false;  // a new node
+      v[q][0] = id % n;
+      v[q][1] = (id / n) % n;
+      v[q][2] = id / ((long long)n * n);
+    }
+    // order the vertices by coordinate sum; a Kuhn path climbs one axis per step
+    int ord[4] = {0, 1, 2, 3};
+    std::sort(ord, ord + 4, [&](int x, int y) { return v[x][0] + v[x][1] + v[x][2] < v[y][0] + v[y][1] + v[y][2]; });
+    int used = 0;
+    for (int q = 0; q < 3; ++q) {
+      int axis = -1, steps = 0;
+      for (int d = 0; d < 3; ++d) {
+        const long long dd = v[ord[q + 1]][d] - v[ord[q]][d];
+        if (dd == 1) axis = d, ++steps;
+        else if (dd != 0) return false;
+      }
+      if (steps != 1 || (used >> axis) & 1) return false;
+      used |= 1 << axis;
+    }
+    return true;
+  };
+  for (long long r = 0; r < n_grid_rows; ++r) {
+    if (rptr[r + 1] - rptr[r] != 24) continue;
+    bool ok = true;
+    for (int e = rptr[r]; e < rptr[r + 1] && ok; ++e) ok = kuhn_tet(itet[e]);
+    (*is_stencil)[r] = ok ? 1 : 0;
+  }
+}
+
 bool pack_ebe_blocks(long long n_rows, long long ntet, const int *tnode, const double *tgrad, const int *rptr,
-                     const int *itet, const int *iloc, const double *rpos, int esz, EbePack *out, std::string *err) {
+                     const int *itet, const int *iloc, const double *rpos, int esz, EbePack *out, std::string *err,
+                     const unsigned char *use) {
   out->blocks.clear();
   out->blob.clear();
   out->nodes.clear();
@@ -43,8 +81,10 @@ bool pack_ebe_blocks(long long n_rows, long long ntet, const int *tnode, const d
   for (long long i = 0; i < 4 * ntet; ++i)
     tnc[i] = (int)(std::lower_bound(uniq.begin(), uniq.end(), tnode[i]) - uniq.begin());
   // rows in brick order (8 x 4 x 4 spacings, x fastest), then z, y, x inside
-  std::vector<long long> order((size_t)n_rows);
-  std::iota(order.begin(), order.end(), 0LL);
+  std::vector<long long> order;
+  order.reserve((size_t)n_rows);
+  for (long long r = 0; r < n_rows; ++r)
+    if (!use || use[r]) order.push_back(r);
   auto key = [&](long long r) {
     const double *x = rpos + 3 * r;
     return std::make_tuple(std::floor(x[2] / 4.0), std::floor(x[1] / 4.0), std::floor(x[0] / 8.0), x[2], x[1], x[0]);

@@ -175,7 +175,35 @@ struct EbePack {
   int smem = 0;  // dynamic shared memory of the largest block
 };
 bool pack_ebe_blocks(long long n_rows, long long ntet, const int *tnode, const double *tgrad, const int *rptr,
-                     const int *itet, const int *iloc, const double *rpos, int esz, EbePack *out, std::string *err);
+                     const int *itet, const int *iloc, const double *rpos, int esz, EbePack *out, std::string *err,
+                     const unsigned char *use = nullptr);
+// use (may be NULL: every row): rows with use[r] = 0 are left out of the blocks.
+
+// Marks the grid rows (the first n_grid_rows rows) whose incident tets are
+// exactly the 24 tets of the uniform Kuhn split around the node: 24 incident
+// tets, all four vertices grid nodes (ids below n^3, id = i + n (j + n k)), each
+// a path o, o + e_p0, o + e_p0 + e_p1, o + (1,1,1).  Such a row equals the
+// 15-point Kuhn block stencil row.
+void kuhn_stencil_rows(long long n_grid_rows, int n, const int *rptr, const int *itet, const int *tet_ids,
+                       std::vector<unsigned char> *is_stencil);
+
+// Explicit-mesh rows that are Kuhn stencil rows: R (and, in the adjoint, q)
+// from the 15-point block stencil instead of the element gather.
+template <typename T>
+struct KuhnRowParams {
+  int n_list;
+  const int *list;          // row indices
+  const int *row_node;      // padded offset of each row's node
+  const T *field;           // E^n or mu^k, padded, 3 components
+  const T *s;               // eps - 1, padded
+  long long cs;             // component stride
+  int px, n;                // x pitch, nodes per axis
+  T *out_r, *out_q;         // [3][n_rows]
+  int n_rows;
+  T B[8][9];                // (D^T D)_{i,i+o} / h, offsets 0, (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,0,1) (0,1,1) (1,1,1)
+};
+template <typename T>
+void launch_kuhn_rows(const KuhnRowParams<T> &P, bool adj, cudaStream_t s);
 // Shared-memory bytes of a block with nt tets, nn nodes, maxinc incidences.
 long long ebe_block_smem(long long nt, long long nn, long long maxinc, int esz);
 

@@ -8,9 +8,9 @@ static ddfd::EbePack g_pack;
 
 extern "C" int ebe_pack_run(long long n_rows, long long ntet, const int *tnode, const double *tgrad,
                             const int *rptr, const int *itet, const int *iloc, const double *rpos, int esz,
-                            long long *sizes, char *err, int err_len) {
+                            long long *sizes, char *err, int err_len, const unsigned char *use) {
   std::string m;
-  if (!ddfd::pack_ebe_blocks(n_rows, ntet, tnode, tgrad, rptr, itet, iloc, rpos, esz, &g_pack, &m)) {
+  if (!ddfd::pack_ebe_blocks(n_rows, ntet, tnode, tgrad, rptr, itet, iloc, rpos, esz, &g_pack, &m, use)) {
     std::strncpy(err, m.c_str(), err_len - 1);
     err[err_len - 1] = 0;
     return 1;
@@ -44,4 +44,21 @@ extern "C" void ebe_pack_consts(int *v) {
   v[0] = ddfd::EBE_RB;
   v[1] = ddfd::EBE_SMEM_BUDGET;
   v[2] = ddfd::EBE_PAD;
+}
+
+// grid rows that are Kuhn block-stencil rows (1) or gathered (0)
+extern "C" void ebe_kuhn_rows(long long n_grid_rows, int n, const int *rptr, const int *itet, const int *tet_ids,
+                              unsigned char *out) {
+  std::vector<unsigned char> v;
+  ddfd::kuhn_stencil_rows(n_grid_rows, n, rptr, itet, tet_ids, &v);
+  std::memcpy(out, v.data(), v.size());
+}
+
+// (D^T D)_{i,i+o} / h of the uniform Kuhn split, as the library assembles it
+extern "C" int ebe_kuhn_blocks(double *B) {
+  ddfd::KuhnBlocks kb;
+  std::string m;
+  if (!ddfd::build_kuhn_blocks(&kb, &m)) return 1;
+  std::memcpy(B, kb.B, sizeof(kb.B));
+  return 0;
 }

@@ -42,7 +42,8 @@ def lib(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("pack") / "libpack.so")
     subprocess.run([cxx, "-O2", "-std=c++17", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                     "-I", inc, os.path.join(ROOT, "tests", "ebe_pack_shim.cpp"),
-                    os.path.join(CSRC, "ddfd_ebe_pack.cpp"), "-o", out], check=True)
+                    os.path.join(CSRC, "ddfd_ebe_pack.cpp"), os.path.join(CSRC, "ddfd_kuhn.cpp"), "-o", out],
+                   check=True)
     L = ctypes.CDLL(out)
     L.ebe_pack_smem.restype = ctypes.c_longlong
     L.ebe_pack_smem.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int]
@@ -109,16 +110,16 @@ def mesh_arrays(n, fem_n, parents, tets, px):
                 rpos[rowof(i + n * (j + n * k))] = (i, j, k)
     rpos[grid_rows:] = X
     return dict(tnode=tnode, tgrad=tgrad, rptr=rptr, itet=itet, iloc=iloc, rpos=rpos, rows=rows, cs=cs,
-                n_new=n_new)
+                n_new=n_new, grid_rows=grid_rows, tet_ids=np.ascontiguousarray(tets, dtype=np.int32), n=n, px=px)
 
 
-def pack(lib, m, esz):
+def pack(lib, m, esz, use=None):
     p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     sizes = np.zeros(5, np.int64)
     err = ctypes.create_string_buffer(256)
     st = lib.ebe_pack_run(ctypes.c_longlong(m["rows"]), ctypes.c_longlong(m["tnode"].shape[0]), p(m["tnode"]),
                           p(m["tgrad"]), p(m["rptr"]), p(m["itet"]), p(m["iloc"]), p(m["rpos"]), esz, p(sizes),
-                          err, 256)
+                          err, 256, None if use is None else p(use))
     assert st == 0, err.value
     nb, nblob, nn, nr, smem = (int(v) for v in sizes)
     blocks = np.zeros((nb, 8), np.int64)
@@ -143,8 +144,8 @@ def direct_rows(m, field, s):
     return y
 
 
-def emulate(lib, m, esz, field, s):
-    blocks, blob, nodes, rows, smem = pack(lib, m, esz)
+def emulate(lib, m, esz, field, s, use=None):
+    blocks, blob, nodes, rows, smem = pack(lib, m, esz, use)
     ft = np.float32 if esz == 4 else np.float64
     RB, PAD = lib.RB, lib.PAD
     assert smem <= lib.BUDGET
@@ -178,7 +179,7 @@ def emulate(lib, m, esz, field, s):
             ga = G[t, a]
             lap = np.einsum("ic,ibc,ibd->id", ga, G[t], sN[TN[t], :3])
             y[r] = lap.sum(0) + (ga * div[t, None]).sum(0)
-    assert np.all(seen == 1)
+    assert np.array_equal(seen, np.ones(m["rows"], np.int64) if use is None else use.astype(np.int64))
     return y, blocks
 
 
@@ -222,3 +223,82 @@ def test_pack_of_a_refined_mesh_reproduces_the_element_loop(lib, esz):
     assert np.abs(y - ref).max() <= tol * np.abs(ref).max()
     # several blocks, and in FP64 the byte budget (not only the row count) cuts them
     assert blocks.shape[0] > m["rows"] // lib.RB
+
+
+def stencil_rows(lib, m):
+    p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    out = np.zeros(m["grid_rows"], np.uint8)
+    lib.ebe_kuhn_rows(ctypes.c_longlong(m["grid_rows"]), m["n"], p(m["rptr"]), p(m["itet"]), p(m["tet_ids"]), p(out))
+    return out
+
+
+def test_pack_of_a_row_subset_covers_exactly_those_rows(lib):
+    n, fem_n = 17, 11
+    m = mesh_arrays(n, fem_n, np.zeros((0, 2), np.int64), kuhn_cube(n, fem_n), px=20)
+    use = (np.random.default_rng(4).random(m["rows"]) < 0.3).astype(np.uint8)
+    field, s = fields(m, 5)
+    y, _ = emulate(lib, m, 8, field, s, use)
+    ref = direct_rows(m, field, s)
+    sel = use.astype(bool)
+    assert np.abs(y[sel] - ref[sel]).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_kuhn_stencil_rows_are_the_untouched_kuhn_rows(lib):
+    n, fem_n = 25, 17
+    # uniform split: every grid row
+    m = mesh_arrays(n, fem_n, np.zeros((0, 2), np.int64), kuhn_cube(n, fem_n), px=28)
+    assert stencil_rows(lib, m).all()
+    # refined mesh: exactly the rows none of whose tets holds a new node
+    nf = (fem_n - 4) ** 3
+    rng = np.random.default_rng(3)
+    eps = np.full(nf, 4.0)
+    eps[rng.random(nf) < 0.05] = 20.0
+    par, tets = refined_fem_mesh(n, fem_n, eps, np.zeros(nf), beta_eps=0.5, beta_sig=0.0)
+    m = mesh_arrays(n, fem_n, par, tets, px=28)
+    got = stencil_rows(lib, m).astype(bool)
+    want = np.array([not (tets[m["itet"][m["rptr"][r]:m["rptr"][r + 1]]] >= n ** 3).any()
+                     for r in range(m["grid_rows"])])
+    assert np.array_equal(got, want) and 0 < got.sum() < m["grid_rows"]
+    # a cube split along another diagonal: the rows at its corners are gathered
+    a, b, _, _ = box_bounds(n, fem_n)
+    T = kuhn_cube(n, fem_n).copy()
+    c = (a + 3) + n * ((a + 3) + n * (a + 3))          # cube corner
+    i, j, k = T % n, (T // n) % n, T // (n * n)
+    inside = ((i >= a + 3) & (i <= a + 4) & (j >= a + 3) & (j <= a + 4) & (k >= a + 3) & (k <= a + 4)).all(axis=1)
+    T[inside] = (2 * (a + 3) + 1 - i[inside]) + n * (j[inside] + n * k[inside])   # mirrored in x
+    m = mesh_arrays(n, fem_n, np.zeros((0, 2), np.int64), T, px=28)
+    got = stencil_rows(lib, m).astype(bool)
+    corners = [(a + 3 + dx) + n * ((a + 3 + dy) + n * (a + 3 + dz)) for dx in (0, 1) for dy in (0, 1) for dz in (0, 1)]
+    fm = b - a - 1
+    rowid = lambda v: (v % n - a - 1) + fm * ((v // n % n - a - 1) + fm * (v // (n * n) - a - 1))
+    assert not any(got[rowid(v)] for v in corners)
+    assert got.sum() == m["grid_rows"] - 8
+
+
+def test_kuhn_stencil_rows_reproduce_the_element_loop(lib):
+    """The formula of the stencil-row kernel, with the blocks the library
+    assembles, on the untouched rows of a refined mesh."""
+    p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    B = np.zeros((8, 9))
+    assert lib.ebe_kuhn_blocks(p(B)) == 0
+    n, fem_n = 25, 17
+    nf = (fem_n - 4) ** 3
+    rng = np.random.default_rng(3)
+    eps = np.full(nf, 4.0)
+    eps[rng.random(nf) < 0.05] = 20.0
+    par, tets = refined_fem_mesh(n, fem_n, eps, np.zeros(nf), beta_eps=0.5, beta_sig=0.0)
+    m = mesh_arrays(n, fem_n, par, tets, px=28)
+    field, s = fields(m, 6)
+    ref = direct_rows(m, field, s)
+    st = stencil_rows(lib, m)
+    px = m["px"]
+    sx, sy, sz = 1, px, px * n
+    offs = [sx, sy, sz, sx + sy, sx + sz, sy + sz, sx + sy + sz]
+    for r in np.nonzero(st)[0]:
+        i, j, k = (int(v) for v in m["rpos"][r])
+        o = i + px * (j + n * k)
+        lap = 6 * field(o) - sum(field(o + d) + field(o - d) for d in (sx, sy, sz))
+        g = B[0].reshape(3, 3) @ (s(o) * field(o))
+        for b, d in enumerate(offs):
+            g += B[b + 1].reshape(3, 3) @ (s(o + d) * field(o + d) + s(o - d) * field(o - d))
+        assert np.allclose(lap + g, ref[r], rtol=1e-12, atol=1e-12 * np.abs(ref).max())
