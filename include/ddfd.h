@@ -239,6 +239,17 @@ int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t);
 int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps);
 int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out);
 
+/* Failure-detection test hook (not for production runs; the paper has no
+ * counterpart).  fault = 1: the first thread block of the element gather
+ * never starts the bulk copy of its first block of rows, so the mbarrier it
+ * waits on is never completed; its bounded wait gives up after spin_limit
+ * polls (0: the default 1 << 22), it records the timeout and returns, and the
+ * ddfd_forward / ddfd_adjoint that ran it fails with DDFD_E_TIMEOUT.  No copy
+ * is left in flight and no fault is raised, so the handle stays usable.
+ * fault = 0 restores normal operation.  Needs fem_kind DDFD_FEM_EBE or
+ * DDFD_FEM_MESH (DDFD_E_ARG otherwise). */
+int ddfd_test_gather_timeout(ddfd_problem *p, int32_t fault, uint32_t spin_limit);
+
 /* Tile autotuner for the step kernels of one handle.  Times `steps` forward
  * and `steps` adjoint step kernels (CUDA events on the handle's stream) for
  * each candidate z depth of the thread-block tile (32 x 8 x kz nodes; kz in

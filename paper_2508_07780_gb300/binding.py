@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "ddfd_autotune", "ddfd_create_batch", "ddfd_destroy_batch", "ddfd_batch_last_error",
     "ddfd_batch_member", "ddfd_batch_forward", "ddfd_batch_forward_dev", "ddfd_batch_adjoint",
     "ddfd_batch_adjoint_dev", "ddfd_batch_autotune", "ddfd_batch_get_info",
-    "ddfd_cg_params_default", "ddfd_cg_run",
+    "ddfd_cg_params_default", "ddfd_cg_run", "ddfd_test_gather_timeout",
 )
 
 
@@ -157,6 +157,7 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).argtypes = [P, P]
     lib.ddfd_batch_autotune.argtypes = [P, c_int32, POINTER(c_int32)]
     lib.ddfd_batch_get_info.argtypes = [P, POINTER(ddfd_batch_info)]
+    lib.ddfd_test_gather_timeout.argtypes = [P, c_int32, ctypes.c_uint32]
     lib.ddfd_cg_params_default.argtypes = [POINTER(ddfd_cg_params)]
     lib.ddfd_cg_params_default.restype = None
     lib.ddfd_cg_run.argtypes = [P, P, POINTER(ddfd_cg_params), P, P, POINTER(ddfd_cg_iter), POINTER(c_int32),
@@ -382,6 +383,12 @@ class Problem:
         self._check(self._lib.ddfd_gradient_dev(self._h, _ptr(g_eps), _ptr(g_sig)))
 
     # -- test hooks -------------------------------------------------------------
+    def test_gather_timeout(self, fault, spin_limit=0):
+        """ddfd_test_gather_timeout: fault=1 makes the element gather's first
+        bounded wait run out (the next forward/adjoint fails with
+        DDFD_E_TIMEOUT); fault=0 restores normal operation."""
+        self._check(self._lib.ddfd_test_gather_timeout(self._h, int(fault), int(spin_limit)))
+
     def set_capture(self, steps):
         arr = _host(list(steps), np.int32)
         self._check(self._lib.ddfd_set_capture(self._h, len(arr), _ptr(arr) if len(arr) else None))

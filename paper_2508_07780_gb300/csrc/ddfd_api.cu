@@ -66,6 +66,8 @@ struct ddfd_problem {
   EbeBlock *ebe_blocks = nullptr;
   unsigned char *ebe_blob = nullptr;
   int ebe_nblocks = 0, ebe_smem = 0;
+  int test_fault = 0;          // ddfd_test_gather_timeout
+  uint32_t test_spin = 0;
   int *kuhn_list = nullptr;   // explicit-mesh rows taken from the Kuhn block stencil
   int kuhn_n = 0;
   double kuhn_B[8][9] = {};   // (D^T D)_{i,i+o} / h of the uniform Kuhn split
@@ -382,7 +384,8 @@ void enqueue_ebe(ddfd_problem *p, const void *field, bool adj, cudaStream_t sm, 
   E.blk_rows = p->ebe_blk_rows;
   E.stage_bytes = p->ebe_smem;
   E.err = err ? err : p->errflag;
-  E.spin_limit = 1u << 22;
+  E.spin_limit = p->test_spin ? p->test_spin : 1u << 22;
+  E.test_skip_copy = p->test_fault;
   if (p->kuhn_n) {
     KuhnRowParams<T> K;
     K.n_list = p->kuhn_n;
@@ -1516,6 +1519,18 @@ int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t) {
   t->adjoint_loop_ms = p->adj_ms;
   t->forward_step_kernels = p->fwd_kernels;
   t->adjoint_step_kernels = p->adj_kernels;
+  return DDFD_OK;
+}
+
+int ddfd_test_gather_timeout(ddfd_problem *p, int32_t fault, uint32_t spin_limit) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  if (!p->ebe_rows || p->ebe_nblocks <= 0)
+    return fail(p, DDFD_E_ARG, "the timeout test needs an element gather (fem_kind DDFD_FEM_EBE or DDFD_FEM_MESH)");
+  if (fault != 0 && fault != 1) return fail(p, DDFD_E_ARG, "fault must be 0 or 1");
+  p->test_fault = fault;
+  p->test_spin = spin_limit;
+  drop_graphs(p);  // the captured sequences hold the old kernel parameters
   return DDFD_OK;
 }
 

@@ -220,6 +220,7 @@ struct EbeParams {
   int stage_bytes;          // shared memory of one pipeline stage (>= every block's)
   int *err;                 // bit 8: a bounded wait for a block's copy gave up
   uint32_t spin_limit;      // polls per bounded wait
+  int test_skip_copy;       // failure-detection test: CTA 0 never starts its first block's copy
   const T *field;           // E^n (forward) or mu^k (adjoint), padded, 3 components
   const T *s;               // eps - 1, padded (coefficient channel 0)
   long long cs;             // component stride
