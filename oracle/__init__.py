@@ -16,7 +16,9 @@ What it computes, in plain numpy/scipy, FP64, with no blocking or fusion:
     eq. adjoint_prob, derived from the Lagrangian eq. lagrangian_weak;
     solver.adjoint);
   * the gradient with respect to epsilon and sigma (Sec. 4, eq. gradeps, taken
-    as the exact derivative of the discrete functional; solver.gradient);
+    as the exact derivative of the discrete functional; solver.gradient), and
+    the paper-literal form with div(eps_bar E) ~ eps_bar div E
+    (solver.gradient_literal);
   * the leapfrog stability bound by power iteration (cfl.py);
   * the conjugate gradient reconstruction of Sec. 4 (cg.py);
   * all of the above on a locally refined FEM mesh given as explicit
