@@ -217,6 +217,9 @@ typedef struct {
   int64_t device_bytes;        /* bytes allocated by the handle */
   int64_t kernel_launches;     /* kernels launched by the handle so far */
   int64_t forward_steps;       /* forward steps executed so far (replays included) */
+  int64_t generation;          /* incremented by every ddfd_set_coeffs and every forward run
+                                  (single or batched); a caller that keeps results of a run can
+                                  compare it to tell whether the handle's state is still theirs */
 } ddfd_info;
 int ddfd_get_info(const ddfd_problem *p, ddfd_info *info);
 
@@ -381,22 +384,27 @@ int ddfd_cg_run(ddfd_batch *b, const double *const *eobs, const ddfd_cg_params *
  * afford cudaMalloc's latency and implicit synchronisation).  Such callers
  * cannot use ddfd_create, which allocates the field buffers.
  *
- * Computes J = tau/2 sum_{s, n=1..n_steps} z(t_n) sum_d |trace - eobs|^2,
- * the misfit part of eq. tikhonov_functional as ddfd_functional computes it
- * (same z taper, t_n = n tau, T = n_steps tau), and writes it to *J.
+ * Writes to *J the data part of the functional that ddfd_functional
+ * returns with both regularisation weights at zero: half the time step tau
+ * times the sum, over sources s and steps n = 1..n_steps, of the taper
+ * z(t_n) times the squared distance between trace and eobs at step n (all
+ * detectors, all three components); t_n = n tau, and z is the taper of
+ * ddfd_config.z_delta_frac with horizon T = n_steps tau.
  *   trace, eobs: device pointers, [n_src][n_steps + 1][n_det][3] doubles,
  *                owned by the caller (may be NULL when n_det = 0);
  *   J:           device pointer to one double, owned by the caller;
  *   stream:      cudaStream_t (NULL: default stream).  The call is
  *                asynchronous on `stream`: read *J after synchronising it.
  * Scratch: a fixed 512 KB array in the library's device image (one FP64
- * partial per (source, step) row); it requires n_src * (n_steps + 1) <=
- * 65536, else DDFD_E_ARG with a message, and nothing is launched.  The call
- * allocates and frees nothing.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call in the process
- * shares the array and it keeps the last call's contents: calls that overlap
- * on the GPU (other streams, other threads) race and give wrong results.
+ * partial per (source, step) row); it requires 1 <= n_src * (n_steps + 1)
+ * <= 65536, else DDFD_E_ARG with a message, and nothing is launched.  The
+ * call allocates and frees nothing.  The array's device address is looked
+ * up (cudaGetSymbolAddress) with the device current on the first call in
+ * each device context -- the first call on a device, and again after that
+ * device's context was reset; make that first call before any stream
+ * capture.  Every call in the process shares the array and it keeps the
+ * last call's contents: calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong results.
  * Errors: DDFD_E_ARG, DDFD_E_CUDA; the message is ddfd_create_error(). */
 int ddfd_misfit_noalloc(const double *trace, const double *eobs, int32_t n_src, int32_t n_steps,
                         int32_t n_det, double tau, double z_delta_frac, double *J, void *stream);

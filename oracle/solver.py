@@ -137,6 +137,15 @@ class OracleProblem:
         return self.M / self.tau ** 2 + C / (2 * self.tau), self.M / self.tau ** 2 - C / (2 * self.tau)
 
     # ---- forward (O3) ------------------------------------------------------
+    def forward_step(self, n: int, E_prev: np.ndarray, E_cur: np.ndarray, F: np.ndarray,
+                     src: SourceSpec) -> np.ndarray:
+        """One step of the scheme: E^{n+1} from E^{n-1}, E^n and the flux F^n,
+        A+_n E^{n+1} = (2 M_eps / tau^2) E^n - K E^n - A-_n E^{n-1} + F^n."""
+        tau = self.tau
+        Ap, Am = self.coeff(n, src)
+        rhs = (2.0 * self.M / tau ** 2) * E_cur - self.op.apply_K(E_cur) - Am * E_prev + F
+        return rhs / Ap
+
     def forward(self, s: int = 0, keep_fields: Sequence[int] = (),
                 source_override: Optional[Callable[[int], np.ndarray]] = None) -> ForwardResult:
         src = self.sources[s]
@@ -148,10 +157,8 @@ class OracleProblem:
         E_free = np.zeros((Nt + 2, 3, free.size))
         fields = {0: E_cur.copy()} if 0 in keep_fields else {}
         for n in range(Nt):
-            Ap, Am = self.coeff(n, src)
             F = source_override(n) if source_override is not None else self.source_term(n, src)
-            rhs = (2.0 * self.M / tau ** 2) * E_cur - self.op.apply_K(E_cur) - Am * E_prev + F
-            E_next = rhs / Ap
+            E_next = self.forward_step(n, E_prev, E_cur, F, src)
             trace[n + 1] = E_next[:, self.det_nodes].T
             E_free[n + 2] = E_next[:, free]
             if (n + 1) in keep_fields:
@@ -188,6 +195,16 @@ class OracleProblem:
             np.add.at(j[c], self.det_nodes, r[:, c])
         return j
 
+    def adjoint_step(self, k: int, mu_next: np.ndarray, mu_cur: np.ndarray, j: np.ndarray,
+                     src: SourceSpec) -> np.ndarray:
+        """One step of the discrete adjoint: mu^{k-1} from mu^{k+1}, mu^k and j^k,
+        A+_{k-1} mu^{k-1} = (2 M_eps / tau^2) mu^k - K^T mu^k - A-_{k+1} mu^{k+1} - j^k."""
+        tau = self.tau
+        Ap_km1, _ = self.coeff(k - 1, src)
+        _, Am_kp1 = self.coeff(k + 1, src)
+        rhs = (2.0 * self.M / tau ** 2) * mu_cur - self.op.apply_KT(mu_cur) - Am_kp1 * mu_next - j
+        return rhs / Ap_km1
+
     def adjoint(self, s: int, trace: np.ndarray, eobs: np.ndarray,
                 keep_fields: Sequence[int] = (),
                 residual_override: Optional[Callable[[int], np.ndarray]] = None) -> AdjointResult:
@@ -202,11 +219,7 @@ class OracleProblem:
         for k in range(Nt, 0, -1):
             j = residual_override(k) if residual_override is not None else \
                 self.residual_source(k, trace, eobs)
-            Ap_km1, _ = self.coeff(k - 1, src)
-            _, Am_kp1 = self.coeff(k + 1, src)
-            rhs = (2.0 * self.M / tau ** 2) * mu_cur - self.op.apply_KT(mu_cur) \
-                - Am_kp1 * mu_next - j
-            mu_prev = rhs / Ap_km1
+            mu_prev = self.adjoint_step(k, mu_next, mu_cur, j, src)
             mu_free[k - 1] = mu_prev[:, free]
             dtd_free[k - 1] = self.op.apply_DtD_masked(mu_prev)[:, free]
             if (k - 1) in keep_fields:

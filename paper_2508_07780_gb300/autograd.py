@@ -8,6 +8,12 @@ solve and gradient accumulation (Sec. 3 eq. adjoint_prob, Sec. 4 eq. gradeps).
 All arithmetic runs in the CUDA library on torch's current stream (the
 problem must be created with stream=torch.cuda.current_stream().cuda_stream);
 this module only wires the calls.
+
+One handle holds one forward state.  If another loss (or any set_coeffs /
+forward call) has used the handle between this loss's forward and its
+backward, the handle's generation counter has moved on; backward then
+re-runs set_coeffs and the forward from the coefficients this loss saved, so
+that its gradient is the one of its own (eps, sigma).
 """
 from __future__ import annotations
 
@@ -19,17 +25,24 @@ from .binding import Problem
 class DDFDFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, eps, sig, problem: Problem, eobs):
-        problem.set_coeffs_dev(eps.detach().contiguous(), sig.detach().contiguous())
+        e = eps.detach().contiguous()
+        s = sig.detach().contiguous()
+        problem.set_coeffs_dev(e, s)
         problem.forward_dev(None)
         J = problem.functional_dev(eobs)
         ctx.problem = problem
-        ctx.save_for_backward(eobs)
+        ctx.generation = problem.get_info().generation
+        ctx.save_for_backward(eobs, e, s)
         return torch.tensor(J, dtype=torch.float64, device=eps.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        (eobs,) = ctx.saved_tensors
+        eobs, e, s = ctx.saved_tensors
         p = ctx.problem
+        if p.get_info().generation != ctx.generation:
+            # the handle's forward state belongs to a later call: restore ours
+            p.set_coeffs_dev(e, s)
+            p.forward_dev(None)
         p.adjoint_dev(eobs)
         ge = torch.empty(p.n_free, dtype=torch.float64, device=eobs.device)
         gs = torch.empty_like(ge)

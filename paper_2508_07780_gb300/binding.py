@@ -63,6 +63,7 @@ class ddfd_info(ctypes.Structure):
         ("n_src", c_int32), ("n_steps", c_int32), ("a", c_int32), ("b", c_int32),
         ("switch_step", c_int32), ("h", c_double), ("tau", c_double),
         ("device_bytes", c_int64), ("kernel_launches", c_int64), ("forward_steps", c_int64),
+        ("generation", c_int64),
     ]
 
 

@@ -88,6 +88,7 @@ struct ddfd_problem {
   std::vector<int> cap_steps;
   void *capE = nullptr, *capMu = nullptr;
   int state = ST_READY;
+  int64_t generation = 0;     // +1 whenever the coefficients or the forward state change
   int64_t launches = 0, fwd_steps = 0;
   int kz = 16;
   int n_part = 256;
@@ -1071,6 +1072,7 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
     ++p->launches;
   }
   p->state = ST_READY;
+  ++p->generation;
   if (p->cfg.cfl_check) {
     st = cfl_check(p);
     if (st) return st;
@@ -1079,6 +1081,10 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
 }
 
 int forward_impl(ddfd_problem *p, double *trace_out, cudaMemcpyKind kind) {
+  // the run overwrites the trace and the E history: until it has completed,
+  // no earlier forward or adjoint state may be used
+  p->state = ST_READY;
+  ++p->generation;
   int st = run_sequence(p, false);
   if (st) return st;
   if ((st = check_err(p))) return st;
@@ -1134,6 +1140,7 @@ int adjoint_impl(ddfd_problem *p, const double *eobs, bool host) {
   }
   launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
   ++p->launches;
+  p->state = ST_FORWARD;  // the accumulators are overwritten: no earlier gradient survives a failed run
   int st = run_sequence(p, true);
   if (st) return st;
   if ((st = check_err(p))) return st;
@@ -1510,6 +1517,7 @@ int ddfd_get_info(const ddfd_problem *p, ddfd_info *info) {
   info->device_bytes = p->bytes;
   info->kernel_launches = p->launches;
   info->forward_steps = p->fwd_steps;
+  info->generation = p->generation;
   return DDFD_OK;
 }
 
@@ -1951,6 +1959,10 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
 }
 
 int batch_forward_impl(ddfd_batch *b, double *const *trace_out, cudaMemcpyKind kind) {
+  for (ddfd_problem *p : b->m) {
+    p->state = ST_READY;
+    ++p->generation;
+  }
   int st = run_batch_sequence(b, false);
   if (st) return st;
   if ((st = batch_check_err(b))) return st;
@@ -1992,6 +2004,7 @@ int batch_adjoint_impl(ddfd_batch *b, const double *const *eobs, bool host) {
     launch_residual(p->trace, e, p->z, p->Nt, p->n_det, 1, p->tau, p->res, p->part, p->n_part, b->stream);
     ++b->launches;
   }
+  for (ddfd_problem *p : b->m) p->state = ST_FORWARD;
   int st = run_batch_sequence(b, true);
   if (st) return st;
   if ((st = batch_check_err(b))) return st;

@@ -11,6 +11,7 @@
 // (source, time step) row of the trace.  It is part of the library image,
 // so every GPU that loads the library holds it (512 KB) until the process
 // exits; no call allocates or frees anything.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -73,10 +74,48 @@ __global__ void k_misfit_total(const double *rows, int n_rows, double tau, doubl
   if (threadIdx.x == 0) *J = 0.5 * tau * b;
 }
 
-// Device address of the scratch array, resolved once per device with that
-// device current (the array's host-side name is not a device address).
+// Device address of the scratch array.  The array's host-side name is not a
+// device address, so it is resolved with cudaGetSymbolAddress, with the
+// device current, once per device context: the cache entry of a device is
+// keyed on the context's process-unique id (cuCtxGetId), so a context that
+// was reset and re-created (cudaDeviceReset) resolves the address again
+// instead of reusing a stale one.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
 std::mutex g_mu;
-double *g_rows_addr[64] = {nullptr};
+struct RowsAddr {
+  unsigned long long ctx_id = 0;  // 0: not resolved
+  double *addr = nullptr;
+};
+RowsAddr g_rows_addr[64];
+PfnCtxGetCurrent g_ctx_current = nullptr;
+PfnCtxGetId g_ctx_id = nullptr;
+
+int driver_fn(const char *name, void **fn) {
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !*fn) {
+    ddfd::set_thread_error(std::string(name) + " is not available from the driver");
+    return DDFD_E_CUDA;
+  }
+  return DDFD_OK;
+}
+
+// Id of the current context (0 if none is current yet).
+int current_ctx_id(unsigned long long *id) {
+  *id = 0;
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS) {
+    ddfd::set_thread_error("cuCtxGetCurrent failed");
+    return DDFD_E_CUDA;
+  }
+  if (ctx && g_ctx_id(ctx, id) != CUDA_SUCCESS) {
+    ddfd::set_thread_error("cuCtxGetId failed");
+    return DDFD_E_CUDA;
+  }
+  return DDFD_OK;
+}
 
 int rows_address(double **out) {
   int dev = 0;
@@ -90,16 +129,29 @@ int rows_address(double **out) {
     return DDFD_E_CUDA;
   }
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_rows_addr[dev]) {
+  int st;
+  if (!g_ctx_current && ((st = driver_fn("cuCtxGetCurrent", (void **)&g_ctx_current)) != DDFD_OK ||
+                         (st = driver_fn("cuCtxGetId", (void **)&g_ctx_id)) != DDFD_OK)) {
+    g_ctx_current = nullptr;
+    return st;
+  }
+  unsigned long long id = 0;
+  if ((st = current_ctx_id(&id)) != DDFD_OK) return st;
+  RowsAddr &c = g_rows_addr[dev];
+  if (id == 0 || c.ctx_id != id) {
+    // first use on this device or context: resolving the symbol also makes
+    // the device's primary context current if nothing was current yet
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_misfit_rows);
     if (e != cudaSuccess || !p) {
       ddfd::set_thread_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       return DDFD_E_CUDA;
     }
-    g_rows_addr[dev] = (double *)p;
+    if (id == 0 && (st = current_ctx_id(&id)) != DDFD_OK) return st;
+    c.ctx_id = id;
+    c.addr = (double *)p;
   }
-  *out = g_rows_addr[dev];
+  *out = c.addr;
   return DDFD_OK;
 }
 
@@ -112,8 +164,8 @@ extern "C" int ddfd_misfit_noalloc(const double *trace, const double *eobs, int3
     ddfd::set_thread_error("ddfd_misfit_noalloc: bad argument");
     return DDFD_E_ARG;
   }
-  const long long n_rows = (long long)n_src * (n_steps + 1);
-  if (n_rows > kNoallocMaxRows) {
+  const long long n_rows = (long long)n_src * ((long long)n_steps + 1);
+  if (n_rows < 1 || n_rows > kNoallocMaxRows) {
     ddfd::set_thread_error("ddfd_misfit_noalloc: n_src * (n_steps + 1) = " + std::to_string(n_rows) +
                            " exceeds the fixed scratch of " + std::to_string(kNoallocMaxRows) + " rows");
     return DDFD_E_ARG;

@@ -117,3 +117,16 @@ def test_create_batch_rejects_literal_gradients(lib):
     with pytest.raises(DDFDError) as e:
         Batch([dict(n=21, fem_n=11, n_steps=3), dict(n=21, fem_n=11, n_steps=3, grad_variant="literal")])
     assert e.value.code == -1 and "exact gradient only" in str(e.value), str(e.value)
+
+
+@pytest.mark.parametrize("n_src,n_steps", [(1, 2 ** 31 - 1), (65536, 1), (40, 2000)])
+def test_misfit_noalloc_rejects_oversized_traces_before_any_gpu_work(lib, n_src, n_steps):
+    """The row count n_src * (n_steps + 1) is formed in 64 bits (n_steps =
+    INT32_MAX must not wrap to a negative count that passes the size check);
+    anything beyond the fixed scratch is refused with DDFD_E_ARG before the
+    call touches a device, so this runs without a GPU.  The pointers are
+    placeholders that the call never dereferences."""
+    fake = 4096
+    st = lib.ddfd_misfit_noalloc(fake, fake, n_src, n_steps, 4, 1e-3, 0.1, fake, None)
+    assert st == -1
+    assert b"exceeds the fixed scratch" in lib.ddfd_create_error()

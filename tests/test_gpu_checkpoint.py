@@ -79,6 +79,46 @@ def test_autograd_returns_the_oracle_gradient():
     p.close()
 
 
+def test_autograd_two_losses_on_one_handle_keep_their_own_gradients():
+    """A second loss on the same handle before the first one's backward: the
+    first backward must still return the gradient at its own coefficients
+    (the handle's generation counter tells it to restore its forward state)."""
+    torch = pytest.importorskip("torch")
+    from paper_2508_07780_gb300.autograd import ddfd_loss
+    w = workload("tiny")
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream(dev)
+    eps, sig = w.model()
+    e_lay, s_lay = w.model(inclusions=False)
+    rng = np.random.default_rng(3)
+    eobs = torch.tensor(1e-3 * rng.standard_normal((1, w.n_steps + 1, w.det_per_side ** 2, 3)),
+                        dtype=torch.float64, device=dev)
+    want = []
+    for e_np, s_np in ((eps, sig), (e_lay, s_lay)):        # each loss alone, fresh handle
+        q = gpu_problem(w, "fp64", stream=stream.cuda_stream)
+        e = torch.tensor(e_np, dtype=torch.float64, device=dev, requires_grad=True)
+        s = torch.tensor(s_np, dtype=torch.float64, device=dev, requires_grad=True)
+        ddfd_loss(e, s, q, eobs).backward()
+        want.append((e.grad.cpu().numpy(), s.grad.cpu().numpy()))
+        q.close()
+    p = gpu_problem(w, "fp64", stream=stream.cuda_stream)
+    e1 = torch.tensor(eps, dtype=torch.float64, device=dev, requires_grad=True)
+    s1 = torch.tensor(sig, dtype=torch.float64, device=dev, requires_grad=True)
+    e2 = torch.tensor(e_lay, dtype=torch.float64, device=dev, requires_grad=True)
+    s2 = torch.tensor(s_lay, dtype=torch.float64, device=dev, requires_grad=True)
+    loss1 = ddfd_loss(e1, s1, p, eobs)
+    loss2 = ddfd_loss(e2, s2, p, eobs)       # overwrites the handle's forward state
+    loss1.backward()
+    loss2.backward()
+    torch.cuda.synchronize()
+    for got, ref in (((e1, s1), want[0]), ((e2, s2), want[1])):
+        assert np.array_equal(got[0].grad.cpu().numpy(), ref[0])
+        assert np.array_equal(got[1].grad.cpu().numpy(), ref[1])
+    assert not np.array_equal(want[0][0], want[1][0])   # the two gradients do differ
+    assert rel_l2(want[0][0], want[1][0]) > 1e-5
+    p.close()
+
+
 def test_differentiable_301_checkpointed_gradient_vs_finite_differences():
     w = workload("c4_fp32_301")
     eps, sig = w.model()

@@ -4,8 +4,11 @@ configuration the benchmark times, where the oracle cannot run in full:
 * vacuum, normal incidence: the FP32 3-D field equals the separately written
   1-D FP64 textbook scheme (laterally invariant, E_x = E_z = 0), a property
   that holds at any size;
-* the FP32 path against the FP64 path (which matches the oracle to 1e-12 at
-  the sizes the oracle runs) on traces, J, mu and g;
+* the FP32 path against the FP64 path (which matches the oracle at the sizes
+  the oracle runs in full) on traces, fields, J, mu and g, with the
+  benchmark's observed data (the layers-only model's trace);
+* one forward and one adjoint step half way through the run against the
+  oracle's step from the GPU's own state, at every node (FP64 and FP32);
 * the FP64 adjoint gradient against central finite differences of J
   (delta = 1e-4) at seeded free nodes, and the FP32 gradient at the same
   nodes.
@@ -13,7 +16,7 @@ configuration the benchmark times, where the oracle cannot run in full:
 import numpy as np
 import pytest
 
-from helpers import gpu_problem, rel_l2
+from helpers import capture_steps, conditioning, gpu_problem, rel_l2
 from synth import workload
 
 pytestmark = pytest.mark.gpu
@@ -57,43 +60,122 @@ def test_vacuum_201_fp32_equals_1d_scheme():
     p.close()
 
 
-def _path(prec, eobs, keep):
+def _path(prec, eobs, keep_mu, keep_e=(), eobs_fn=None):
     p = gpu_problem(W, prec)
-    p.set_capture(keep)
+    steps = sorted(set(keep_mu) | set(keep_e))
+    p.set_capture(steps)
     eps, sig = W.model()
     p.set_coeffs(eps, sig)
     tr = p.forward()
+    if eobs_fn is not None:
+        eobs = eobs_fn(tr)
     J = p.functional(eobs)
     p.adjoint(eobs)
     ge, gs = p.gradient()
-    mu = {s: p.get_capture(1, i) for i, s in enumerate(keep)}
+    mu = {s: p.get_capture(1, steps.index(s)) for s in keep_mu}
+    E = {s: p.get_capture(0, steps.index(s)) for s in keep_e}
     p.close()
-    return tr, J, ge, gs, mu
+    return dict(trace=tr, J=J, g_eps=ge, g_sig=gs, mu=mu, E=E)
 
 
 @pytest.fixture(scope="module")
 def eobs_201():
-    """Half the layers-only model's FP64 trace: a residual of the size of E."""
+    """The benchmark's observed data: the layers-only model's FP64 trace."""
     p = gpu_problem(W, "fp64")
     e0, s0 = W.model(inclusions=False)
     p.set_coeffs(e0, s0)
     tr = p.forward()
     p.close()
-    return 0.5 * tr
+    return tr
 
 
-def test_fp32_matches_fp64_at_full_size(eobs_201):
-    keep = [0, W.n_steps // 2]
-    t64, J64, ge64, gs64, mu64 = _path("fp64", eobs_201, keep)
-    t32, J32, ge32, gs32, mu32 = _path("fp32", eobs_201, keep)
-    errs = {"trace": rel_l2(t32, t64), "J": abs(J32 - J64) / abs(J64),
-            "g_eps": rel_l2(ge32, ge64), "g_sig": rel_l2(gs32, gs64)}
-    for s in keep:
-        errs[f"mu{s}"] = rel_l2(mu32[s], mu64[s])
-    print("FP32 vs FP64 at 201^3:", errs)
+@pytest.fixture(scope="module")
+def fp64_201(eobs_201):
+    ke, km = capture_steps(W.n_steps)
+    return _path("fp64", eobs_201, km, ke)
+
+
+def _errs(a, b):
+    e = {"trace": rel_l2(a["trace"], b["trace"]), "J": abs(a["J"] - b["J"]) / abs(b["J"]),
+         "g_eps": rel_l2(a["g_eps"], b["g_eps"]), "g_sig": rel_l2(a["g_sig"], b["g_sig"])}
+    for s in a["E"]:
+        e[f"E{s}"] = rel_l2(a["E"][s], b["E"][s])
+    for s in a["mu"]:
+        e[f"mu{s}"] = rel_l2(a["mu"][s], b["mu"][s])
+    return e
+
+
+def test_fp32_matches_fp64_at_full_size(eobs_201, fp64_201):
+    """FP32 against FP64 on the benchmark's own observed data.  Trace, fields,
+    J and g meet the benchmark spec bars (1e-4, 1e-3).  mu is held to 1e-4 times
+    kappa = ||trace|| / ||trace - Eobs|| (about 19 here): the FP32 forward's
+    trace error (~2e-6) becomes ~kappa times that in the residual that drives
+    the adjoint, and at early adjoint steps, whose driving residual is still
+    tiny, it dominates mu.  The next test shows that the adjoint kernel itself
+    meets the plain bar."""
+    ke, km = capture_steps(W.n_steps)
+    b = fp64_201
+    a = _path("fp32", eobs_201, km, ke)
+    kappa = conditioning(b["trace"], eobs_201)
+    errs = _errs(a, b)
+    print(f"FP32 vs FP64 at 201^3, kappa={kappa:.1f}:", " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
     assert errs["trace"] <= 1e-4 and errs["J"] <= 1e-4
-    assert all(errs[f"mu{s}"] <= 1e-4 for s in keep)
+    assert all(errs[f"E{s}"] <= 1e-4 for s in ke)
     assert errs["g_eps"] <= 1e-3 and errs["g_sig"] <= 1e-3
+    assert all(errs[f"mu{s}"] <= 1e-4 * kappa for s in km)
+
+
+def test_fp32_adjoint_from_the_fp64_residual_meets_the_plain_bars(eobs_201, fp64_201):
+    """The FP32 adjoint driven by the FP64 run's residual (the FP32 trace is
+    shifted into the observed data): mu, J and g then carry only the FP32
+    kernels' own rounding, and meet the plain bars."""
+    ke, km = capture_steps(W.n_steps)
+    b = fp64_201
+    a = _path("fp32", eobs_201, km, eobs_fn=lambda tr: eobs_201 + (tr - b["trace"]))
+    errs = {k: v for k, v in _errs(a, dict(b, E={})).items() if k != "trace"}
+    print("FP32 adjoint from the FP64 residual at 201^3:", " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert errs["J"] <= 1e-4 and all(errs[f"mu{s}"] <= 1e-4 for s in km)
+    assert errs["g_eps"] <= 1e-3 and errs["g_sig"] <= 1e-3
+
+
+@pytest.fixture(scope="module")
+def oracle_201():
+    from oracle import SourceSpec
+    from helpers import oracle_problem
+    eps, sig = W.model()
+    return oracle_problem(W, eps, sig, [SourceSpec()])
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_one_step_against_the_oracle_at_full_size(eobs_201, oracle_201, prec, bar):
+    """One forward and one adjoint step of the GPU run at 201^3, in the
+    benchmark's launch configuration, half way through the 2000 steps (the
+    pulse is inside the FEM cube), against the oracle's step applied to the
+    GPU's own state: E^{n+1} from (E^{n-1}, E^n) and mu^{k-1} from
+    (mu^{k+1}, mu^k) and the residual j^k, at every node of the grid.  One
+    step of rounding: 1e-13 in FP64, 1e-6 in FP32 (FP32 fields and step
+    coefficients)."""
+    n = W.n_steps // 2
+    steps = [n - 1, n, n + 1]
+    p = gpu_problem(W, prec)
+    p.set_capture(steps)
+    eps, sig = W.model()
+    p.set_coeffs(eps, sig)
+    tr = p.forward()
+    p.adjoint(eobs_201)
+    E = [p.get_capture(0, i) for i in range(3)]
+    mu = [p.get_capture(1, i) for i in range(3)]
+    p.close()
+    P = oracle_201
+    src = P.sources[0]
+    shape = (3, -1)
+    E_next = P.forward_step(n, E[0].reshape(shape), E[1].reshape(shape), P.source_term(n, src), src)
+    e_fwd = rel_l2(E[2].reshape(shape), E_next)
+    j = P.residual_source(n, tr[0], eobs_201[0])
+    mu_prev = P.adjoint_step(n, mu[2].reshape(shape), mu[1].reshape(shape), j, src)
+    e_adj = rel_l2(mu[0].reshape(shape), mu_prev)
+    print(f"{prec} one step at n={n}: forward {e_fwd:.2e}, adjoint {e_adj:.2e}")
+    assert e_fwd <= bar and e_adj <= bar
 
 
 def test_gradient_matches_central_differences_at_full_size(eobs_201):
