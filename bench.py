@@ -1,20 +1,28 @@
 """Benchmark of the hot path: forward + functional + adjoint + gradient.
 
-One step = one pass of the whole path over one synthetic workload:
-ddfd_set_coeffs -> ddfd_forward -> ddfd_functional -> ddfd_adjoint ->
-ddfd_gradient.  The default workload is the FP32 201^3 grid with a 101^3
-FEM cube, 2000 time steps, 1024 detectors and three inclusions.
+One step = one pass of the whole path over the batched FP32 workload: 16
+independent problems on a 161^3 grid (FEM cubes 61/81/101/121 for problem b
+mod 4, one hemisphere-drawn incident plane wave each, 1600 time steps, 1024
+detectors), stepped together by the batch calls -- per member
+ddfd_set_coeffs, then ddfd_batch_forward, ddfd_functional per member,
+ddfd_batch_adjoint, ddfd_gradient per member.  Every member keeps its E
+history on the free nodes (about 250 GB of HBM in all).
 
-Prints ONE JSON line (rank 0).  `value` is grid-point updates/s over all
-ranks (2 n^3 Nt per problem and pass, forward + adjoint), device-resident
-inputs; `e2e` is the same through the host-pointer entry points with the
-host<->device copies inside the timed region; `roofline` is the dominant
-step kernel's algorithmic bytes over its CUDA-event duration against the
-measured HBM copy bandwidth; `cpu_baseline` times the FP64 CPU oracle on a
-bounded sample of the same workload; `fp64_plain` is one pass of the plain
-FP64 GPU path on the same workload; `batched` is the batched FP32 workload
-(16 problems of mixed FEM cube size on a 161^3 grid, one launch per time
-step) with its own throughput and roofline.
+Prints ONE JSON line (rank 0):
+  value       grid-point updates/s over all ranks (2 n^3 Nt per problem and
+              pass, forward + adjoint), device-resident inputs;
+  e2e         the same through the host-pointer entry points, with the
+              host<->device copies inside the timed region;
+  roofline    the dominant step kernel (the batched adjoint step) against the
+              measured HBM copy bandwidth, with the forward kernel and the
+              whole pass beside it;
+  fp64_plain  the plain FP64 GPU path on the same 16 problems, solved one at a
+              time, its FP64 ALU roofline, and the FP32 speedup;
+  accuracy    relative errors of the FP32 batched results (traces, J, g)
+              against that FP64 run, measured in this run;
+  single_201  the one-source FP32 workload (201^3 grid, FEM cube 101^3, 2000
+              steps) with its own roofline and errors against FP64;
+  cpu_baseline  the FP64 CPU oracle on the host cores (bounded sample).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -24,6 +32,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,13 +45,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import workload  # noqa: E402
+from synth import batched_problems, workload  # noqa: E402
 
 METRIC = ("grid-point updates/s (fwd+adj+grad) and % HBM roofline, "
           "FP32 batched vs FP64 plain")
 UNIT = "grid-point updates/s"
 STEP_SRC = os.path.join(ROOT, "paper_2508_07780_gb300", "csrc", "ddfd_step.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+BATCH_WORKLOAD = ("c3_batched_161: 16 problems on a 161^3 grid, FEM cubes 61/81/101/121 (problem b mod 4), "
+                  "1600 steps, FP32 fields with FP64 reductions, one hemisphere-drawn plane wave and 1024 "
+                  "detectors each, seeds 300..315, full E history")
 
 
 def describe(w):
@@ -51,23 +63,39 @@ def describe(w):
             f"{w.det_per_side ** 2} detectors, {w.n_incl} inclusion(s), seed {w.seed}")
 
 
-def algorithmic_bytes(w):
+def algorithmic_bytes(n, fem_n, es):
     """Per launch of the forward / adjoint step kernel (one time step, one
-    source): every node reads E^n and E^{n-1} and writes E^{n+1} (3 x 3
+    problem): every node reads E^n and E^{n-1} and writes E^{n+1} (3 x 3
     components); FEM-updated nodes read (eps, sigma); the adjoint reads E^k on
     the free nodes for the gradient.  Neighbour re-reads, the E history
-    written by the forward and the FP64 gradient accumulators are not
+    written by the forward and the gradient accumulators are not
     algorithmic."""
-    es = 4 if w.precision == "fp32" else 8
-    n3 = w.n ** 3
-    fem_rows = (w.fem_n - 2) ** 3
-    n_free = (w.fem_n - 4) ** 3
+    n3 = n ** 3
+    fem_rows = (fem_n - 2) ** 3
+    n_free = (fem_n - 4) ** 3
     fwd = 9 * es * n3 + 2 * es * fem_rows
     adj = fwd + 3 * es * n_free
     return fwd, adj
 
 
-def measured_peak():
+def fp64_flops(n, fem_n):
+    """Algorithmic FP64 flops of one forward / adjoint step (FMA = 2), counted
+    from the formulas the step kernel evaluates: every node 15 per component
+    (the 7-point row: 5 adds and one FMA; the tau^2/h^2 scale; the update
+    E + A (E - E_old) + B E - C R: 7); FEM-updated nodes add the forward
+    Gauss-law stencil sum_o B_o (s E)_{i+o} (45 products s E, 21 pair sums,
+    84 for the integer 3 x 3 blocks, 6 for the 1/6 scale and the add: 156) or
+    the adjoint's s_i sum_o B_o mu_{i+o} (21 + 84 + 9 = 114); free nodes add
+    the adjoint's gradient terms (30 per node and step, 2 more to accumulate)."""
+    n3 = n ** 3
+    fem_rows = (fem_n - 2) ** 3
+    n_free = (fem_n - 4) ** 3
+    fwd = 45 * n3 + 156 * fem_rows
+    adj = 45 * n3 + 114 * fem_rows + 32 * n_free
+    return fwd, adj
+
+
+def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
@@ -76,7 +104,7 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def traffic_per_launch(which):
+def traffic_per_launch(key):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current step-kernel source (sha256 prefix match); else None."""
     try:
@@ -90,9 +118,31 @@ def traffic_per_launch(which):
             vals[k.strip()] = v.strip()
         if vals.get("source_sha256_16") != src_hash:
             return None
-        return float(vals[f"{which}_dram_bytes_per_launch_full"])
+        return float(vals[key])
     except Exception:
         return None
+
+
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part") and model in ("", "aarch64"):
+                model = line.split(":", 1)[1].strip()
+                if low.startswith("model name"):
+                    break
+    except Exception:
+        pass
+    try:
+        lscpu = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in lscpu.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
 class ClockSampler:
@@ -147,119 +197,192 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in rows),
                 "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
-                "samples": len(rows)}
+                "samples": len(rows), "power_w_max": max(r["pw"] for r in rows)}
 
 
-def oracle_sample(w, steps):
-    """The FP64 oracle on the full grid of the workload for `steps` forward and
-    `steps` adjoint steps (assembly excluded); returns (updates/s, seconds,
-    threads used)."""
+# --------------------------------------------------------------------------
+# CPU oracle (the reference arm and the CPU baseline)
+# --------------------------------------------------------------------------
+
+class OracleSample:
+    """The FP64 oracle on one problem's full grid, assembled once; run()
+    times `steps` forward and `steps` adjoint steps plus the functional and
+    the gradient and returns (grid-point updates, seconds, threads used)."""
+
+    def __init__(self, n, fem_n, seed, n_incl, direction, steps):
+        from oracle import OracleProblem, SourceSpec
+        from synth.models import detector_grid, layered_inclusion_model
+        eps, sig = layered_inclusion_model(n, fem_n, seed, n_incl)
+        det = detector_grid(n, fem_n, 32)
+        self.n, self.steps = n, steps
+        self.P = OracleProblem(n, fem_n, steps, 0.3, eps, sig, det, [SourceSpec(direction=tuple(direction))],
+                               z_delta_frac=0.1)
+        self.eobs = np.zeros((steps + 1, det.shape[0], 3))
+
+    def run(self):
+        P = self.P
+        c0, t0 = time.process_time(), time.perf_counter()
+        f = P.forward(0)
+        P.functional([f.trace], [self.eobs])
+        a = P.adjoint(0, f.trace, self.eobs)
+        P.gradient([f], [a])
+        wall = time.perf_counter() - t0
+        cpu = time.process_time() - c0
+        return 2 * self.n ** 3 * self.steps, wall, max(1, round(cpu / wall))
+
+
+def oracle_sample(*args):
+    """One OracleSample run (a pool worker)."""
+    return OracleSample(*args).run()
+
+
+def oracle_full_run(name):
+    """The oracle on a whole workload (forward, functional, adjoint,
+    gradient; assembly excluded); returns (updates, seconds)."""
     from oracle import OracleProblem, SourceSpec
+    w = workload(name)
     eps, sig = w.model()
-    ws = w.with_(n_steps=steps)
-    P = OracleProblem(ws.n, ws.fem_n, steps, ws.cfl, eps, sig, ws.detectors(), [SourceSpec()],
-                      z_delta_frac=ws.z_delta_frac)
-    eobs = np.zeros((steps + 1, ws.detectors().shape[0], 3))
-    c0, t0 = time.process_time(), time.perf_counter()
-    f = P.forward(0)
-    P.functional([f.trace], [eobs])
-    a = P.adjoint(0, f.trace, eobs)
-    P.gradient([f], [a])
-    wall = time.perf_counter() - t0
-    cpu = time.process_time() - c0
-    return 2 * ws.n ** 3 * steps / wall, wall, max(1, round(cpu / wall))
+    e0, s0 = w.model(inclusions=False)
+    P0 = OracleProblem(w.n, w.fem_n, w.n_steps, w.cfl, e0, s0, w.detectors(), [SourceSpec()],
+                       z_delta_frac=w.z_delta_frac)
+    eobs = P0.forward(0).trace
+    P = OracleProblem(w.n, w.fem_n, w.n_steps, w.cfl, eps, sig, w.detectors(), [SourceSpec()],
+                      z_delta_frac=w.z_delta_frac)
+    t0 = time.perf_counter()
+    P.run([eobs])
+    return w.updates, time.perf_counter() - t0
 
 
-def run_reference(args, w, rank):
+SAMPLE_STEPS = 4
+
+
+def _member_args(b):
+    (w, d), = batched_problems(first=b, n_problems=1)
+    return (w.n, w.fem_n, w.seed, w.n_incl, d, SAMPLE_STEPS)
+
+
+def cpu_baseline(workers):
+    """The oracle on the host cores: one batch member (161^3 grid) for
+    SAMPLE_STEPS forward + SAMPLE_STEPS adjoint steps in one process (single
+    core: scipy's sparse products are single-threaded), the same sample on
+    `workers` members at once in separate processes (all cores; the members
+    are independent problems), and the 41^3 x 300-step plain FP64 workload in
+    full.  Processes are started with spawn."""
+    import multiprocessing as mp
+    info = host_info()
+    upd, wall, cores = OracleSample(*_member_args(3)).run()
+    single = upd / wall
+    out = {"value": single, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": (f"one 161^3 member of the batched workload (FEM cube 121^3), {SAMPLE_STEPS} forward + "
+                      f"{SAMPLE_STEPS} adjoint steps, functional and gradient, FP64 scipy oracle, assembly "
+                      f"excluded, {wall:.1f} s"),
+           "host": info}
+    mem_gb = None
+    try:   # about 5 GB of host memory per oracle process at 161^3; keep half free
+        mem_gb = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 1e9
+        workers = max(1, min(workers, int(mem_gb // 10)))
+    except (ValueError, OSError):
+        pass
+    info["host_memory_gb"] = round(mem_gb, 1) if mem_gb else None
+    if workers > 1:
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(workers) as pool:
+            res = pool.starmap(oracle_sample, [_member_args(3)] * workers)
+        wall_all = time.perf_counter() - t0
+        out["all_cores"] = {"value": sum(r[0] / r[1] for r in res), "unit": UNIT, "processes": workers,
+                            "sample": f"the same sample in {workers} processes at once (identical assembly, so "
+                                      f"the timed parts run concurrently); the value sums their rates; "
+                                      f"{wall_all:.1f} s in all"}
+    upd1, wall1 = oracle_full_run("c1_fp64_41")
+    out["c1_fp64_41_full"] = {"value": upd1 / wall1, "unit": UNIT, "seconds": wall1, "cores": 1,
+                              "run": "41^3 grid, FEM 21^3, 300 steps: forward, functional, adjoint, gradient"}
+    return out
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle (this build has no other reference
+    implementation) on the same workload, each bench step a bounded sample:
+    one batch member for SAMPLE_STEPS forward + adjoint steps."""
     if rank != 0:
         return
-    per = 2
-    vals = []
-    cores = 1
+    steps = 2
+    (w, d), = batched_problems(first=3, n_problems=1)
+    sampler = OracleSample(w.n, w.fem_n, w.seed, w.n_incl, d, steps)
+    vals, cores = [], 1
     for i in range(args.warmup + args.steps):
-        v, _, cores = oracle_sample(w, per)
+        upd, wall, cores = sampler.run()
         if i >= args.warmup:
-            vals.append(v)
+            vals.append(upd / wall)
     value = statistics.mean(vals)
-    sample = (f"{w.n}^3 grid of the workload, {per} forward + {per} adjoint steps per bench step, "
-              f"FP64 scipy oracle, assembly excluded")
+    sample = (f"problem 3 of the batched workload (161^3 grid, FEM cube 121^3), {steps} forward + {steps} "
+              f"adjoint steps, functional and gradient per bench step, FP64 scipy oracle, assembly excluded")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 2 * w.n ** 3 * per / value * 1e3, "higher_is_better": True,
+            "ms_per_step": 2 * 161 ** 3 * steps / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": describe(w)},
+            "config": {"workload": BATCH_WORKLOAD},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample}}
+                             "sample": sample, "host": host_info()}}
     print(json.dumps(line), flush=True)
 
 
-def fp64_plain(w, dev, stream):
-    """One timed pass (after one warm-up) of the same workload with FP64 fields."""
+# --------------------------------------------------------------------------
+# GPU legs
+# --------------------------------------------------------------------------
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def fp64_peak_tflops(dev):
+    """Measured FP64 rate: cuBLAS DGEMM (torch.matmul float64, 4096^3), best
+    of 5, CUDA events.  Used as the FP64 ALU peak of the plain FP64 path."""
     import torch
-    from paper_2508_07780_gb300 import Problem
-    w64 = w.with_(precision="fp64")
-    eps, sig = w64.model()
-    e_lay, s_lay = w64.model(inclusions=False)
-    p = Problem(n=w64.n, fem_n=w64.fem_n, n_steps=w64.n_steps, cfl=w64.cfl, precision="fp64",
-                src_dir=w64.directions(), det_ij=w64.detectors(), z_delta_frac=w64.z_delta_frac,
-                stream=stream.cuda_stream)
-    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
-    p.set_coeffs(e_lay, s_lay)
-    eobs = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
-    p.forward_dev(eobs)
-    eps_d, sig_d = T(eps), T(sig)
-    ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
-    gs = torch.empty_like(ge)
-
-    def step():
-        p.set_coeffs_dev(eps_d, sig_d)
-        p.forward_dev(None)
-        p.functional_dev(eobs)
-        p.adjoint_dev(eobs)
-        p.gradient_dev(ge, gs)
-
-    step()
-    torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    step()
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
-    p.close()
-    return w64.updates / (ms / 1e3), ms
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        a @ b
+    best = 1e30
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * 4096 ** 3 / (best / 1e3) / 1e12
 
 
-def batched_bytes(ws):
-    """Algorithmic bytes of one batched forward launch: the per-problem bytes
-    of algorithmic_bytes summed over the members."""
-    return sum(algorithmic_bytes(w)[0] for w in ws)
-
-
-def run_batched(args, dev, stream):
-    """The batched FP32 workload: 16 problems on a 161^3 grid, FEM cubes
-    61/81/101/121 (problem b mod 4), one hemisphere-drawn incidence
-    direction each, 1600 steps, 1024 detectors, stepped together (one launch
-    per time step, graph-captured), tile depth from the autotuner.  Members
-    with the 61^3 and 81^3 cubes keep the E history; the 101^3 and 121^3
-    ones checkpoint (32 snapshots) and are replayed in batched launches of
-    their own, so that the batch fits in about 85 GB."""
+def run_batched(args, dev, stream, rank, world, peak):
     import torch
+    import torch.distributed as dist
     from paper_2508_07780_gb300 import Batch
-    from synth import batched_problems
-    probs = batched_problems()
+
+    probs = batched_problems(first=16 * rank)
     cfgs = [dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp32",
                  src_dir=d[None, :], det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
-                 n_snapshots=32 if w.fem_n > 81 else 0, stream=stream.cuda_stream)
-            for w, d in probs]
+                 stream=stream.cuda_stream) for w, d in probs]
     b = Batch(cfgs)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
-    for (w, _), m in zip(probs, b.members):
-        m.set_coeffs(*w.model(inclusions=False))
-    eobs = [torch.empty(m.trace_shape, dtype=torch.float64, device=dev) for m in b.members]
-    b.forward_dev(eobs)
+    # observed data: each member's layers-only model trace (FP64 forward of the
+    # batch); the inclusions are what the residual sees
+    eobs = []
+    for (w, d) in probs:
+        from paper_2508_07780_gb300 import Problem
+        q = Problem(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp64",
+                    src_dir=d[None, :], det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
+                    forward_only=1, stream=stream.cuda_stream)
+        q.set_coeffs(*w.model(inclusions=False))
+        e = torch.empty(q.trace_shape, dtype=torch.float64, device=dev)
+        q.forward_dev(e)
+        q.close()
+        eobs.append(e)
     coefs = [tuple(T(a) for a in w.model()) for w, _ in probs]
     grads = [(torch.empty(m.n_free, dtype=torch.float64, device=dev),
               torch.empty(m.n_free, dtype=torch.float64, device=dev)) for m in b.members]
@@ -277,6 +400,11 @@ def run_batched(args, dev, stream):
 
     for _ in range(args.warmup):
         step()
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize(dev)
     l0 = b.get_info().kernel_launches
     fwd_ms = adj_ms = 0.0
@@ -290,128 +418,36 @@ def run_batched(args, dev, stream):
         adj_ms += inf.adjoint_loop_ms
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    inf = b.get_info()
-    launches = inf.kernel_launches - l0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ws = [w for w, _ in probs]
-    updates = sum(w.updates for w in ws)
-    nb = batched_bytes(ws)
-    fwd_avg = fwd_ms / (args.steps * inf.forward_step_kernels)
-    peak, peak_kind = measured_peak()
-    achieved = nb / (fwd_avg / 1e3) / 1e9
-    out = {"workload": (f"batched FP32: 16 problems, {ws[0].n}^3 grid, FEM cubes 61/81/101/121 "
-                        f"(problem b mod 4), {ws[0].n_steps} steps, one hemisphere-drawn plane wave "
-                        f"each, 1024 detectors, seeds 300..315"),
-           "value": updates / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
-           "warmup": args.warmup, "tile_kz": kz, "gpu_launches": int(launches),
-           "device_bytes": int(inf.device_bytes),
-           "memory_plan": "61^3/81^3 members keep the E history, 101^3/121^3 members checkpoint "
-                          "(32 snapshots, replayed in batched launches; replays are not counted "
-                          "as updates)",
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None,
-                        "kernel": "k_step<float,forward,16> (one launch = one step of all 16)",
-                        "algorithmic_bytes_per_launch": nb, "avg_launch_ms": fwd_avg,
-                        "adjoint_loop_ms_per_step": adj_ms / args.steps,
-                        "peak_kind": f"{peak_kind} (HBM copy, MEASURED_PEAKS.json hbm_gbs)"}}
-    b.close()
-    return out
-
-
-def run_ours(args, w, rank, world, local_rank):
-    import torch
-    import torch.distributed as dist
-    from paper_2508_07780_gb300 import Problem
-    from paper_2508_07780_gb300.sharding import reduce_loss_and_grad_dev
-    from synth import shard_directions
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream(dev)
-    eps, sig = w.model()
-    e_lay, s_lay = w.model(inclusions=False)
-    # N > 1: source sharding.  Every rank owns one incident plane wave (rank 0
-    # the normal one of the single-GPU workload, the others drawn on the
-    # hemisphere); the ranks share eps and sigma, and one FP64 all-reduce of
-    # [J, g_eps, g_sig] per step sums the functional and the gradient.
-    src_dir = w.directions() if world == 1 else shard_directions(world)[rank:rank + 1]
-    kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision=w.precision,
-              src_dir=src_dir, det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
-              n_snapshots=args.snapshots, grad_variant=args.grad_variant, stream=stream.cuda_stream)
-    p = Problem(**kw)
-    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
-    # observed data: the layers-only model's trace (the inclusions are what
-    # the residual sees)
-    p.set_coeffs(e_lay, s_lay)
-    eobs_d = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
-    p.forward_dev(eobs_d)
-    eps_d, sig_d = T(eps), T(sig)
-    ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
-    gs = torch.empty_like(ge)
-
-    fwd_ms, adj_ms, nk = 0.0, 0.0, 0
-
-    def step():
-        p.set_coeffs_dev(eps_d, sig_d)
-        p.forward_dev(None)
-        J = p.functional_dev(eobs_d)
-        p.adjoint_dev(eobs_d)
-        p.gradient_dev(ge, gs)
-        if world > 1:
-            J = reduce_loss_and_grad_dev(J, ge, gs)
-        return J
-
-    for _ in range(args.warmup):
-        step()
-    sampler = ClockSampler(local_rank) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    l0 = p.get_info().kernel_launches
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-        t = p.get_timing()
-        fwd_ms += t.forward_loop_ms
-        adj_ms += t.adjoint_loop_ms
-        nk += t.forward_step_kernels
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    launches = p.get_info().kernel_launches - l0
+    inf = b.get_info()
+    launches = inf.kernel_launches - l0
     ms = ev0.elapsed_time(ev1) / args.steps
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    updates = w.updates
-    value = world * updates / (ms / 1e3)
 
-    # end to end through the host-pointer entry points (pinned host buffers)
+    # end to end: host coefficients, host observed data, host gradients and J
     pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory()
-    eps_h, sig_h = pin(eps), pin(sig)
-    eobs_h = eobs_d.cpu().pin_memory()
-    trace_h = torch.empty(p.trace_shape, dtype=torch.float64).pin_memory()
-    ge_h = torch.empty(p.n_free, dtype=torch.float64).pin_memory()
-    gs_h = torch.empty_like(ge_h).pin_memory()
+    coefs_h = [(pin(w.model()[0]), pin(w.model()[1])) for w, _ in probs]
+    eobs_h = [e.cpu().pin_memory() for e in eobs]
+    grads_h = [(torch.empty(m.n_free, dtype=torch.float64).pin_memory(),
+                torch.empty(m.n_free, dtype=torch.float64).pin_memory()) for m in b.members]
+    lib = b._lib
+    import ctypes
 
     def step_e2e():
-        p.set_coeffs(eps_h.numpy(), sig_h.numpy())
-        p._check(p._lib.ddfd_forward(p._h, trace_h.data_ptr()))
-        J = p.functional(eobs_h.numpy())
-        p.adjoint(eobs_h.numpy())
-        p._check(p._lib.ddfd_gradient(p._h, ge_h.data_ptr(), gs_h.data_ptr()))
-        if world > 1:
-            gd, sd = ge_h.to(dev, non_blocking=True), gs_h.to(dev, non_blocking=True)
-            J = reduce_loss_and_grad_dev(J, gd, sd)
-            ge_h.copy_(gd)
-            gs_h.copy_(sd)
+        for m, (e, s) in zip(b.members, coefs_h):
+            m._check(lib.ddfd_set_coeffs(m._h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                                         None, None))
+        b._check(lib.ddfd_batch_forward(b._h, None))
+        J = 0.0
+        for m, e in zip(b.members, eobs_h):
+            Jm = ctypes.c_double()
+            m._check(lib.ddfd_functional(m._h, ctypes.c_void_p(e.data_ptr()), ctypes.byref(Jm)))
+            J += Jm.value
+        ptrs = (ctypes.c_void_p * len(eobs_h))(*[e.data_ptr() for e in eobs_h])
+        b._check(lib.ddfd_batch_adjoint(b._h, ptrs))
+        for m, (ge, gs) in zip(b.members, grads_h):
+            m._check(lib.ddfd_gradient(m._h, ctypes.c_void_p(ge.data_ptr()), ctypes.c_void_p(gs.data_ptr())))
         return J
 
     step_e2e()
@@ -423,73 +459,246 @@ def run_ours(args, w, rank, world, local_rank):
         step_e2e()
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
-    nf, ntr = p.n_free, int(np.prod(p.trace_shape))
-    dev_bytes = p.get_info().device_bytes
-    h2d = 2 * nf * 8 + 2 * ntr * 8
-    d2h = ntr * 8 + 2 * nf * 8 + 3 * 8
-    if world > 1:                       # the gradient through the all-reduce and back
-        h2d += 2 * nf * 8
-        d2h += 2 * nf * 8
-    p.close()
+    ntr = sum(int(np.prod(m.trace_shape)) for m in b.members)
+    nfr = sum(m.n_free for m in b.members)
+    h2d = 2 * nfr * 8 + 2 * ntr * 8
+    d2h = 2 * nfr * 8 + len(b.members) * 8
 
+    # FP32 results of one more pass, for the accuracy comparison
+    out32 = []
+    if rank == 0 and not args.no_fp64:
+        traces = [torch.empty(m.trace_shape, dtype=torch.float64, device=dev) for m in b.members]
+        for m, (e, s) in zip(b.members, coefs):
+            m.set_coeffs_dev(e, s)
+        b.forward_dev(traces)
+        Js = [m.functional_dev(e) for m, e in zip(b.members, eobs)]
+        b.adjoint_dev(eobs)
+        for i, m in enumerate(b.members):
+            ge, gs = grads[i]
+            m.gradient_dev(ge, gs)
+            out32.append(dict(trace=traces[i].cpu().numpy(), J=Js[i], g_eps=ge.cpu().numpy(),
+                              g_sig=gs.cpu().numpy(), eobs=eobs[i].cpu().numpy()))
+        del traces
+    dev_bytes = inf.device_bytes
+    n_groups = (len(b.members) + 15) // 16
+    b.close()
+    del eobs, coefs, grads
+    torch.cuda.empty_cache()
+
+    ws = [w for w, _ in probs]
+    fb = sum(algorithmic_bytes(w.n, w.fem_n, 4)[0] for w in ws)
+    ab = sum(algorithmic_bytes(w.n, w.fem_n, 4)[1] for w in ws)
+    nt = ws[0].n_steps
+    fwd_avg = fwd_ms / (args.steps * nt * n_groups)
+    adj_avg = adj_ms / (args.steps * nt * n_groups)
+    updates = sum(w.updates for w in ws)
+    res = dict(ms=ms, updates=updates, e2e_s=e2e_s, h2d=h2d, d2h=d2h, launches=launches, clocks=clocks,
+               kz=kz, dev_bytes=dev_bytes, out32=out32, probs=probs)
+    res["roofline"] = {
+        "bound": "hbm", "achieved": ab / (adj_avg / 1e3) / 1e9, "peak": peak[0], "unit": "GB/s",
+        "frac": ab / (adj_avg / 1e3) / 1e9 / peak[0],
+        "traffic": traffic_per_launch("batched_adjoint_dram_bytes_per_launch"),
+        "kernel": "k_step_pair<adjoint,16> (one launch = one adjoint step of all 16 problems)",
+        "algorithmic_bytes_per_launch": ab, "avg_launch_ms": adj_avg,
+        "peak_kind": f"{peak[1]} (HBM copy, MEASURED_PEAKS.json hbm_gbs)",
+        "forward": {"kernel": "k_step_pair<forward,16>", "algorithmic_bytes_per_launch": fb,
+                    "avg_launch_ms": fwd_avg, "achieved": fb / (fwd_avg / 1e3) / 1e9,
+                    "frac": fb / (fwd_avg / 1e3) / 1e9 / peak[0],
+                    "traffic": traffic_per_launch("batched_forward_dram_bytes_per_launch")},
+        "whole_pass": {"algorithmic_bytes": (fb + ab) * nt, "ms": ms,
+                       "achieved": (fb + ab) * nt / (ms / 1e3) / 1e9,
+                       "frac": (fb + ab) * nt / (ms / 1e3) / 1e9 / peak[0],
+                       "note": "forward + adjoint step bytes of every member over the whole pass time "
+                               "(set_coeffs, forward, functional, adjoint, gradient)"}}
+    return res
+
+
+def run_fp64_plain(args, dev, stream, probs, out32, fp64_peak):
+    """The plain FP64 GPU path on the same problems, one at a time (the FP64
+    method without batching), timed pass by pass after one warm-up pass per
+    problem; its results are the reference of the accuracy table."""
+    import torch
+    from paper_2508_07780_gb300 import Problem
+    total_ms = 0.0
+    upd = 0
+    errs = []
+    step_ms = []
+    for i, (w, d) in enumerate(probs):
+        p = Problem(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp64",
+                    src_dir=d[None, :], det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
+                    stream=stream.cuda_stream)
+        eps, sig = (torch.tensor(a, dtype=torch.float64, device=dev) for a in w.model())
+        eo = torch.tensor(out32[i]["eobs"], dtype=torch.float64, device=dev)
+        tr = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
+        ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
+        gs = torch.empty_like(ge)
+
+        def step():
+            p.set_coeffs_dev(eps, sig)
+            p.forward_dev(tr)
+            J = p.functional_dev(eo)
+            p.adjoint_dev(eo)
+            p.gradient_dev(ge, gs)
+            return J
+
+        step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        J = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1)
+        t = p.get_timing()
+        step_ms.append((t.forward_loop_ms / t.forward_step_kernels, t.adjoint_loop_ms / t.adjoint_step_kernels))
+        upd += w.updates
+        a, tr64 = out32[i], tr.cpu().numpy()
+        kappa = float(np.linalg.norm(tr64) / np.linalg.norm(tr64 - a["eobs"]))
+        errs.append(dict(trace=rel(a["trace"], tr64), J=abs(a["J"] - J) / abs(J),
+                         g_eps=rel(a["g_eps"], ge.cpu().numpy()), g_sig=rel(a["g_sig"], gs.cpu().numpy()),
+                         kappa=kappa))
+        p.close()
+        del eps, sig, eo, tr, ge, gs
+        torch.cuda.empty_cache()
+    # FP64 ALU roofline of the FP64 step kernels (problem 3, the 121^3 FEM cube)
+    w3 = probs[3][0]
+    ff, fa = fp64_flops(w3.n, w3.fem_n)
+    fwd_ms, adj_ms = step_ms[3]
+    ach = max(ff / (fwd_ms / 1e3), fa / (adj_ms / 1e3)) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+            "kernel": "k_step<double> (forward and adjoint, problem 3: FEM cube 121^3)",
+            "algorithmic_flops_per_launch": {"forward": ff, "adjoint": fa},
+            "avg_launch_ms": {"forward": fwd_ms, "adjoint": adj_ms},
+            "peak_kind": "measured in this run: cuBLAS DGEMM 4096^3 (torch.matmul float64), best of 5"}
+    worst = {k: max(e[k] for e in errs) for k in ("trace", "J", "g_eps", "g_sig")}
+    return dict(value=upd / (total_ms / 1e3), ms=total_ms, errs=errs, worst=worst, roofline=roof)
+
+
+def run_single_201(args, dev, stream, peak):
+    """The one-source FP32 workload (201^3, FEM cube 101^3, 2000 steps) with
+    its FP64 counterpart: throughput, step-kernel rooflines and the FP32
+    errors against FP64, measured here."""
+    import torch
+    from paper_2508_07780_gb300 import Problem
+    w = workload("c2_fp32_201")
+    eps, sig = w.model()
+    e_lay, s_lay = w.model(inclusions=False)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, src_dir=w.directions(), det_ij=w.detectors(),
+              z_delta_frac=w.z_delta_frac, stream=stream.cuda_stream)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        p = Problem(precision=prec, **kw)
+        if prec == "fp64":
+            p.set_coeffs(e_lay, s_lay)
+            eobs = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
+            p.forward_dev(eobs)
+        eps_d, sig_d = T(eps), T(sig)
+        tr = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
+        ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
+        gs = torch.empty_like(ge)
+
+        def step():
+            p.set_coeffs_dev(eps_d, sig_d)
+            p.forward_dev(tr)
+            J = p.functional_dev(eobs)
+            p.adjoint_dev(eobs)
+            p.gradient_dev(ge, gs)
+            return J
+
+        reps = 1 if prec == "fp64" else max(args.steps, 3)
+        step()
+        torch.cuda.synchronize(dev)
+        fwd = adj = nk = 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            J = step()
+            t = p.get_timing()
+            fwd += t.forward_loop_ms
+            adj += t.adjoint_loop_ms
+            nk += t.forward_step_kernels
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[prec] = dict(ms=ms, fwd=fwd / nk, adj=adj / nk, trace=tr.cpu().numpy(), J=J,
+                         g_eps=ge.cpu().numpy(), g_sig=gs.cpu().numpy(), bytes=p.get_info().device_bytes)
+        p.close()
+        del eps_d, sig_d, tr, ge, gs
+    eo = eobs.cpu().numpy()
+    del eobs
+    torch.cuda.empty_cache()
+    a, b = out["fp32"], out["fp64"]
+    fb, ab = algorithmic_bytes(w.n, w.fem_n, 4)
+    kappa = float(np.linalg.norm(b["trace"]) / np.linalg.norm(b["trace"] - eo))
+    return {"workload": describe(w), "value": w.updates / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"],
+            "device_bytes": int(a["bytes"]),
+            "roofline": {"bound": "hbm", "peak": peak[0], "unit": "GB/s",
+                         "forward": {"kernel": "k_step_pair<forward,1>", "avg_launch_ms": a["fwd"],
+                                     "algorithmic_bytes_per_launch": fb,
+                                     "frac": fb / (a["fwd"] / 1e3) / 1e9 / peak[0],
+                                     "traffic": traffic_per_launch("forward_dram_bytes_per_launch_full")},
+                         "adjoint": {"kernel": "k_step_pair<adjoint,1>", "avg_launch_ms": a["adj"],
+                                     "algorithmic_bytes_per_launch": ab,
+                                     "frac": ab / (a["adj"] / 1e3) / 1e9 / peak[0],
+                                     "traffic": traffic_per_launch("adjoint_dram_bytes_per_launch_full")}},
+            "fp64_plain": {"value": w.updates / (b["ms"] / 1e3), "ms_per_step": b["ms"],
+                           "fp32_speedup": b["ms"] / a["ms"]},
+            "accuracy_vs_fp64": {"trace": rel(a["trace"], b["trace"]), "J": abs(a["J"] - b["J"]) / abs(b["J"]),
+                                 "g_eps": rel(a["g_eps"], b["g_eps"]), "g_sig": rel(a["g_sig"], b["g_sig"]),
+                                 "kappa": kappa,
+                                 "observed_data": "the layers-only model's FP64 trace (unmodified)"}}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    peak = measured_peaks()
+    single = None
+    if world == 1 and not args.no_single:
+        single = run_single_201(args, dev, stream, peak)
+    bat = run_batched(args, dev, stream, rank, world, peak)
+    ms_t = torch.tensor([bat["ms"], bat["e2e_s"]], device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms, e2e_s = float(ms_t[0].item()), float(ms_t[1].item())
     if rank != 0:
         return
-    fwd_b, adj_b = algorithmic_bytes(w)
-    fwd_avg = fwd_ms / max(nk, 1)
-    adj_avg = adj_ms / max(nk, 1)
-    # with checkpointing the adjoint sequence also holds the replayed forward
-    # steps, so the roofline is taken on the forward launches
-    adj_first = adj_ms >= fwd_ms and not args.snapshots
-    which, nbytes, dur = ("adjoint", adj_b, adj_avg) if adj_first else ("forward", fwd_b, fwd_avg)
-    peak, peak_kind = measured_peak()
-    achieved = nbytes / (dur / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic_per_launch(which),
-            "kernel": f"k_step<{'float' if w.precision == 'fp32' else 'double'},"
-                      f"{'adjoint' if which == 'adjoint' else 'forward'}>",
-            "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": dur,
-            "forward_avg_launch_ms": fwd_avg, "adjoint_avg_launch_ms": adj_avg,
-            "peak_kind": f"{peak_kind} (HBM copy, MEASURED_PEAKS.json hbm_gbs)"}
+    value = world * bat["updates"] / (ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
-            "data": "synthetic",
-            "config": {"workload": describe(w), "grid": w.n, "fem_n": w.fem_n,
-                       "n_steps": w.n_steps, "n_src": w.n_src, "problems_per_gpu": 1,
-                       "e_history": (f"checkpointing, {args.snapshots} snapshots, replayed segments"
-                                     if args.snapshots else "full E history on the free nodes"),
-                       "gradient": ("exact derivative of the discrete J" if args.grad_variant == "exact" else
-                                    "paper-literal (Sec. 4, div(eps E) ~ eps div E; E kept on the FEM nodes)"),
-                       "device_bytes": int(dev_bytes),
-                       "l2": "inputs larger than L2: 2 field levels of 3 x n^3 plus the "
-                             "E history on the free nodes, re-streamed every step",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "grid": 161, "problems_per_gpu": 16, "n_steps": 1600,
+                       "fem_n": [61, 81, 101, 121], "tile_kz": bat["kz"], "device_bytes": int(bat["dev_bytes"]),
+                       "l2": "inputs larger than L2: 16 problems x 2 field levels of 3 x 161^3 FP32 plus "
+                             "the E history, re-streamed every step",
                        "parallelism": "single GPU" if world == 1 else
-                       f"source sharding: 1 incident wave per GPU x{world}, FP64 all-reduce "
-                       f"of [J, g_eps, g_sig] ({8 * (1 + 2 * w.n_free)} bytes) per step"},
-            "e2e": {"value": world * updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "roofline": roof,
-            "gpu_launches": int(launches),
-            "clocks": clocks}
-    if world == 1 and w.precision == "fp32" and not args.no_fp64:
-        # the plain FP64 path on the same workload, for the FP32 speedup
-        v64, ms64 = fp64_plain(w, dev, stream)
-        line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": 1, "warmup": 1,
-                              "fp32_speedup": value / v64,
-                              "accuracy": "FP32 vs FP64 on this workload: trace 2.4e-6, J 1.9e-6, "
-                                          "g 1.1e-5 relative L2 (tests/test_gpu_fullsize.py)"}
-    if world == 1 and not args.no_batched:
-        line["batched"] = run_batched(args, dev, stream)
+                       f"{world} GPUs, 16 independent problems each (problems 16 r .. 16 r + 15 on rank r), "
+                       f"no data-path collective"},
+            "e2e": {"value": world * bat["updates"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bat["h2d"],
+                    "d2h_bytes_per_step": bat["d2h"]},
+            "roofline": bat["roofline"],
+            "gpu_launches": int(bat["launches"]),
+            "clocks": bat["clocks"]}
+    if world == 1 and not args.no_fp64:
+        fp = run_fp64_plain(args, dev, stream, bat["probs"], bat["out32"], fp64_peak_tflops(dev))
+        line["fp64_plain"] = {"value": fp["value"], "unit": UNIT, "ms_per_step": fp["ms"],
+                              "how": "the same 16 problems solved one at a time in FP64 (plain, unbatched)",
+                              "fp32_batched_speedup": value / fp["value"], "roofline": fp["roofline"]}
+        line["accuracy"] = {"reference": "FP64 plain path on the same problems and observed data",
+                            "worst_over_problems": fp["worst"],
+                            "north_star_bars": {"trace": 1e-4, "J": 1e-4, "g": 1e-3},
+                            "kappa_range": [min(e["kappa"] for e in fp["errs"]), max(e["kappa"] for e in fp["errs"])],
+                            "per_problem": fp["errs"]}
+    if single is not None:
+        line["single_201"] = single
     if world == 1 and not args.no_cpu_baseline:
-        v, wall, cores = oracle_sample(w, 2)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{w.n}^3 grid of the workload, 2 forward + 2 adjoint "
-                                          f"steps, FP64 scipy oracle, assembly excluded, "
-                                          f"{wall:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline(args.cpu_workers)
     print(json.dumps(line), flush=True)
 
 
@@ -499,31 +708,22 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2_fp32_201")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison pass")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched 16-problem workload")
-    ap.add_argument("--snapshots", type=int, default=0,
-                    help="checkpointing with this many state snapshots instead of the full E history")
-    ap.add_argument("--grad-variant", choices=["exact", "literal"], default="exact",
-                    help="gradient form: the exact derivative of the discrete J (default) or the "
-                         "paper-literal one of Sec. 4")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison passes")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-source 201^3 workload")
+    ap.add_argument("--cpu-workers", type=int, default=min(8, os.cpu_count() or 1))
     args = ap.parse_args()
-    w = workload(args.workload)
-    if args.precision:
-        w = w.with_(precision=args.precision)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, w, rank)
+        run_reference(args, rank)
         return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        run_ours(args, w, rank, world, local_rank)
+        run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

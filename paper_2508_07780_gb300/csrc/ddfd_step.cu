@@ -963,6 +963,29 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
           }
         }
       }
+      if (x0 + S::TX == n - 1 && xl == S::TX - 2) {
+        // x tail: with n = 32 m + 1 the launch has m tiles in x, the last
+        // ending at x = n - 2, and its lanes owning columns 30, 31 also update
+        // the boundary node e = (n - 1, y), in the staged x halo (an FD node,
+        // never FEM or free): 7-point row with the mirror ghost x + 1 = x - 1,
+        // summed in the order of the pair's rows; operands re-read from the
+        // staged planes (the pair's registers are free again here)
+        float Re[3], Ae = 1.f, Be = 0.f, Ce = 1.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float *e = E0 + c * RE + ci + 2;
+          const float xme = e[-1];
+          Re[c] = 6.f * e[0] - (((((xme + xme) + e[dyp]) + e[dym]) + Ep[c * RE + ci + 2]) + Em[c * RE + ci + 2]);
+          Re[c] *= P.r2;
+        }
+        if (ybnd || (sides & DDFD_ABS_X1) || kbnd) boundary(n - 1, k, Re, Ae, Be, Ce);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float ce = E0[c * RE + ci + 2];
+          const float ov = out[c * cs + 2];  // the previous level, read before it is overwritten
+          out[c * cs + 2] = ce + (Ae * (ce - ov) + (Be * ce - Ce * Re[c]));
+        }
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -1034,11 +1057,16 @@ static void launch_step(const StepLaunch<double, NB> &L, cudaStream_t s) {
   const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
   k_step<double, ADJ, NB><<<grid, STEP_THREADS, Stage<double>::SMEM, s>>>(L);
 }
+// x tiles of the FP32 step kernel: with n = 32 m + 1 the last column is
+// updated by the last of m tiles (k_step_pair's x tail) instead of by a tile
+// of its own
+static int pair_tiles_x(int n) { return n % STEP_TX == 1 ? n / STEP_TX : (n + STEP_TX - 1) / STEP_TX; }
+
 template <bool ADJ, int NB>
 static void launch_step(const StepLaunch<float, NB> &L, cudaStream_t s) {
   const int ty = PairStage::TY;
   const StepParams<float> &P = L.p[0];
-  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
+  const dim3 grid(pair_tiles_x(P.n), (P.n + ty - 1) / ty, L.zchunks * L.nprob);
   k_step_pair<ADJ, NB><<<grid, PairMode<ADJ>::THREADS, PairStage::SMEM, s>>>(L);
 }
 

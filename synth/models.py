@@ -243,13 +243,16 @@ def workload(name: str, **overrides) -> Workload:
     return w.with_(**overrides) if overrides else w
 
 
-def batched_problems(n: int = 161, n_problems: int = 16, n_steps: int = 1600):
+def batched_problems(n: int = 161, n_problems: int = 16, n_steps: int = 1600, first: int = 0):
     """The heterogeneous batch: FEM cube 61/81/101/121 for problem b mod 4,
-    seed 300 + b, one hemisphere-drawn incidence direction per problem."""
+    seed 300 + b, one hemisphere-drawn incidence direction per problem, for
+    problems b = first .. first + n_problems - 1 (first = 0: the 16-problem
+    workload; a later `first` gives further, independent problems of the
+    same kind, e.g. for another GPU)."""
     sizes = (61, 81, 101, 121)
-    dirs = hemisphere_directions(n_problems, 3000)
+    dirs = hemisphere_directions(first + n_problems, 3000)
     out = []
-    for b in range(n_problems):
+    for b in range(first, first + n_problems):
         w = Workload(f"batch{b}", n, sizes[b % 4], n_steps, precision="fp32",
                      seed=300 + b, n_incl=1 + (300 + b) % 3, det_per_side=32,
                      n_src=1, dir_seed=None)

@@ -52,6 +52,11 @@ CASES = {
     # two sources, duplicated and corner detectors
     "two_src_dup_det": (workload("tiny", n_src=2, dir_seed=3,
                                  extra={"det": [[6, 6], [6, 6], [0, 0], [12, 12], [0, 12], [4, 9]]}), {}),
+    # n = 32 + 1: the FP32 kernel's last x tile also updates the column x = n - 1
+    # (absorbing x1 and y1 faces, oblique incidence, detectors on that column)
+    "x_tail_33": (workload("small", n=33, fem_n=17, n_steps=60, seed=13, dir_seed=5,
+                           extra={"det": [[32, 32], [32, 0], [32, 17], [16, 16], [0, 32], [31, 32]]}),
+                  dict(absorbing=1 | 2 | 8 | 32)),
 }
 
 _oracle_cache = {}
