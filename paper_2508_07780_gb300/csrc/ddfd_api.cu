@@ -51,7 +51,71 @@ int dalloc(ddfd_problem *p, size_t bytes, void **out) {
     return fail(p, DDFD_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
   }
   p->allocs.push_back(*out);
+  p->alloc_bytes.push_back(bytes);
   p->bytes += (int64_t)bytes;
+  return DDFD_OK;
+}
+
+void dfree(ddfd_problem *p, void *ptr) {
+  for (size_t q = 0; q < p->allocs.size(); ++q)
+    if (p->allocs[q] == ptr) {
+      cudaFree(ptr);
+      p->bytes -= (int64_t)p->alloc_bytes[q];
+      p->allocs.erase(p->allocs.begin() + q);
+      p->alloc_bytes.erase(p->alloc_bytes.begin() + q);
+      return;
+    }
+}
+
+std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz) {
+  const int n = ps[0]->n;
+  const bool f32 = ps[0]->fp32 != 0;
+  const int gx = step_tiles_x(n, f32), gy = step_tiles_y(n, f32), gz = (n + kz - 1) / kz;
+  // nodes of [z0, z1) inside [first, last]
+  auto ov = [](int lo, int hi, int first, int last) {
+    return (long long)std::max(0, std::min(hi, last + 1) - std::max(lo, first));
+  };
+  // whole z slabs (one problem's tiles of one z chunk) are ordered, so that
+  // tiles that share halos still run side by side
+  struct Slab {
+    long long cost;
+    int q, zc;
+  };
+  std::vector<Slab> v;
+  for (size_t q = 0; q < ps.size(); ++q) {
+    const ddfd_problem *p = ps[q];
+    const long long fem2 = (long long)(p->b - p->a - 1) * (p->b - p->a - 1), fre2 = (long long)p->nf * p->nf;
+    for (int zc = 0; zc < gz; ++zc) {
+      const int z0 = zc * kz, z1 = std::min(z0 + kz, n);
+      Slab sl;
+      sl.cost = (long long)n * n * (z1 - z0) + 2 * fem2 * ov(z0, z1, p->a + 1, p->b - 1) +
+                fre2 * ov(z0, z1, p->f0, p->f0 + p->nf - 1);
+      sl.q = (int)q;
+      sl.zc = zc;
+      v.push_back(sl);
+    }
+  }
+  std::stable_sort(v.begin(), v.end(), [](const Slab &l, const Slab &r) { return l.cost > r.cost; });
+  std::vector<int> out;
+  out.reserve(v.size() * gx * gy);
+  for (const Slab &sl : v)
+    for (int ty = 0; ty < gy; ++ty)
+      for (int tx = 0; tx < gx; ++tx) out.push_back(pack_step_item(tx, ty, sl.zc, sl.q));
+  return out;
+}
+
+int build_items(ddfd_problem *p) {
+  if (p->n > 1024 || (p->n + p->kz - 1) / p->kz > 512) return DDFD_OK;  // beyond the item packing: grid order
+  const std::vector<int> it = step_item_order({p}, p->kz);
+  if (p->items) {
+    dfree(p, p->items);
+    p->items = nullptr;
+    p->items_kz = 0;
+  }
+  int st = dalloc_t(p, it.size(), &p->items);
+  if (st) return st;
+  CK(cudaMemcpy(p->items, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice));
+  p->items_kz = p->kz;
   return DDFD_OK;
 }
 
@@ -866,7 +930,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
     p->err = std::string("create: ") + cudaGetErrorString(cudaGetLastError());
     return bail(DDFD_E_CUDA);
   }
-  if ((st = build_maps(p))) return bail(st);
+  if ((st = build_maps(p)) || (st = build_items(p))) return bail(st);
   if (cfg->fem_kind == DDFD_FEM_EBE && (st = build_ebe(p))) return bail(st);
   if (cfg->fem_kind == DDFD_FEM_MESH && (st = build_mesh(p))) return bail(st);
   // vacuum coefficients

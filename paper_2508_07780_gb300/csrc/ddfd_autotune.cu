@@ -141,6 +141,7 @@ int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out) {
   p->kz = best ? best : p->kz;
   p->state = ST_READY;
   drop_graphs(p);
+  if (!st) st = build_items(p);
   const size_t fbytes = 3 * (size_t)p->cs * p->esz;
   for (int q = 0; q < 2; ++q) {
     CK(cudaMemsetAsync(p->E[q], 0, fbytes, p->stream));
@@ -167,7 +168,9 @@ int ddfd_batch_autotune(ddfd_batch *b, int32_t steps, int32_t *tile_kz_out) {
     p->kz = b->kz;
     p->state = ST_READY;
     drop_graphs(p);
+    if (!st && (st = build_items(p))) b->err = p->err;
   }
+  if (!st) st = build_batch_items(b);
   const size_t slab = 3 * (size_t)b->cs * b->esz * b->m.size();
   for (int q = 0; q < 2; ++q) {
     BCK(cudaMemsetAsync(b->E[q], 0, slab, b->stream));

@@ -22,6 +22,40 @@ std::vector<int> all_members(const ddfd_batch *b) {
   return v;
 }
 
+int build_batch_items(ddfd_batch *b) {
+  for (std::vector<int *> *v : {&b->items_all, &b->items_ck}) {
+    for (int *t : *v) {
+      cudaFree(t);
+      b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)t));
+    }
+    v->clear();
+  }
+  b->items_kz = 0;
+  if (b->n > 1024 || (b->n + b->kz - 1) / b->kz > 512) return DDFD_OK;  // beyond the item packing: grid order
+  std::vector<int> ck;
+  for (size_t i = 0; i < b->m.size(); ++i)
+    if (b->m[i]->nsnap) ck.push_back((int)i);
+  const std::vector<int> all = all_members(b);
+  const std::pair<const std::vector<int> *, std::vector<int *> *> lists[2] = {{&all, &b->items_all},
+                                                                             {&ck, &b->items_ck}};
+  for (const auto &lt : lists)
+    for (size_t g0 = 0; g0 < lt.first->size(); g0 += BATCH_MAX) {
+      std::vector<const ddfd_problem *> ps;
+      for (size_t g = g0; g < std::min(g0 + BATCH_MAX, lt.first->size()); ++g) ps.push_back(b->m[(*lt.first)[g]]);
+      const std::vector<int> it = step_item_order(ps, b->kz);
+      int *d = nullptr;
+      if (cudaMalloc((void **)&d, it.size() * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, DDFD_E_OOM, "cudaMalloc of a dispatch table failed");
+      }
+      b->allocs.push_back(d);
+      lt.second->push_back(d);
+      BCK(cudaMemcpy(d, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+  b->items_kz = b->kz;
+  return DDFD_OK;
+}
+
 }  // namespace host
 }  // namespace ddfd
 
@@ -55,7 +89,7 @@ int enqueue_batch_forward(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
     };
     // element-by-element members: their FEM rows of this level first
     for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->E[ic], false, sm, nk, p->X[ic], b->errflag);
-    launch_groups<T>(b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io], fill, sm, nk);
+    launch_groups<T>(b, false, all, b->maps.E_halo[ic], b->maps.E_ctr[io], fill, sm, nk, &b->items_all);
     for (ddfd_problem *p : b->m)
       if (p->n_new) {
         StepParams<T> P = base_params<T>(p);
@@ -112,7 +146,7 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
             [&](StepParams<T> &P, ddfd_problem *p) {
               set_forward_step(P, p, 0, st, p->E[fc], p->E[fo], (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free);
             },
-            sm, nk);
+            sm, nk, &b->items_ck);
         std::swap(fc, fo);
       }
     }
@@ -122,7 +156,7 @@ int enqueue_batch_adjoint(ddfd_batch *b, cudaStream_t sm, int64_t *nk) {
         set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + (size_t)hk * 3 * p->n_free, Nt);
       };
       for (ddfd_problem *p : b->m) enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk, p->XMu[ic], b->errflag);
-      launch_groups<T>(b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io], fill, sm, nk);
+      launch_groups<T>(b, true, all, b->maps.M_halo[ic], b->maps.M_ctr[io], fill, sm, nk, &b->items_all);
       for (ddfd_problem *p : b->m)
         if (p->n_new) {
           StepParams<T> P = base_params<T>(p);
@@ -400,6 +434,7 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
     if (st) return bail(st, "member " + std::to_string(i) + ": " + thread_error());
     b->m.push_back(p);
   }
+  if (build_batch_items(b)) return bail(DDFD_E_OOM, b->err);
   *out = b;
   return DDFD_OK;
 }

@@ -53,6 +53,7 @@ struct ddfd_problem {
   size_t esz = 8;
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
+  std::vector<size_t> alloc_bytes;  // size of each allocation, in the order of allocs
   int64_t bytes = 0;
   void *E[2] = {nullptr, nullptr}, *Mu[2] = {nullptr, nullptr};
   void *kcoef = nullptr;      // padded full-grid (s, q1, q2), 3 channels
@@ -93,6 +94,8 @@ struct ddfd_problem {
   int64_t generation = 0;     // +1 whenever the coefficients or the forward state change
   int64_t launches = 0, fwd_steps = 0;
   int kz = 16;
+  int *items = nullptr;       // dispatch order of the step launches (heaviest tiles first), for items_kz
+  int items_kz = 0;
   int n_part = 256;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double fwd_ms = 0.0, adj_ms = 0.0;
@@ -133,6 +136,11 @@ struct ddfd_batch {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double fwd_ms = 0.0, adj_ms = 0.0;
   int64_t fwd_kernels = 0, adj_kernels = 0;
+  // dispatch orders of the batched step launches (heaviest tiles first), for
+  // items_kz: one table per group of BATCH_MAX members of all members, and of
+  // the checkpointing members (their replays)
+  std::vector<int *> items_all, items_ck;
+  int items_kz = 0;
   // conjugate gradient work space (FP64, free nodes): 14 vectors, partial
   // sums, the 6 reduced scalars
   double *cg = nullptr;
@@ -171,8 +179,21 @@ int bfail(ddfd_batch *b, int code, const std::string &m);
       return bfail(b, DDFD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
   } while (0)
 
-// Device allocation against the handle's budget (freed with the handle).
+// Device allocation against the handle's budget (freed with the handle);
+// dfree releases one such allocation early.
 int dalloc(ddfd_problem *p, size_t bytes, void **out);
+void dfree(ddfd_problem *p, void *ptr);
+
+// Dispatch order of one step launch over the problems `ps` (stacked in that
+// order) with z depth kz: whole z slabs (one problem's tiles of one z chunk,
+// in grid order within the slab) sorted by an estimate of their work, heaviest
+// first (node count, plus twice the FEM rows and once the free nodes they
+// hold), ties in grid order.
+std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz);
+// (Re)builds p->items for p->kz.
+int build_items(ddfd_problem *p);
+// (Re)builds the batch's tables for b->kz.
+int build_batch_items(ddfd_batch *b);
 template <typename X>
 int dalloc_t(ddfd_problem *p, size_t count, X **out) {
   void *v = nullptr;
@@ -295,6 +316,7 @@ StepLaunch<T, 1> single_launch(const StepParams<T> &P, const CUtensorMap &cur, c
   L.q = p->mQ;
   L.nprob = 1;
   L.zchunks = (p->n + P.kz - 1) / P.kz;
+  L.items = P.kz == p->items_kz ? p->items : nullptr;
   L.p[0] = P;
   return L;
 }
@@ -377,10 +399,12 @@ void enqueue_new_step(ddfd_problem *p, const void *cur, void *old, bool adj, con
 }
 
 // One batched step launch per group of BATCH_MAX members; fill(P, p) sets the
-// per-step scalars of member p.
+// per-step scalars of member p; tables (may be NULL): the groups' dispatch
+// orders, used when built for the batch's current kz.
 template <typename T, typename Fill>
 void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const CUtensorMap &cur,
-                   const CUtensorMap &old, Fill fill, cudaStream_t sm, int64_t *nk) {
+                   const CUtensorMap &old, Fill fill, cudaStream_t sm, int64_t *nk,
+                   const std::vector<int *> *tables = nullptr) {
   for (size_t g0 = 0; g0 < idx.size(); g0 += BATCH_MAX) {
     StepLaunch<T, BATCH_MAX> L;
     std::memset(&L, 0, sizeof(L));
@@ -390,6 +414,8 @@ void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const C
     L.q = b->maps.Q;
     L.nprob = (int)std::min<size_t>(BATCH_MAX, idx.size() - g0);
     L.zchunks = (b->n + b->kz - 1) / b->kz;
+    L.items = (tables && b->kz == b->items_kz && g0 / BATCH_MAX < tables->size()) ? (*tables)[g0 / BATCH_MAX]
+                                                                                  : nullptr;
     for (int g = 0; g < L.nprob; ++g) {
       ddfd_problem *p = b->m[idx[g0 + g]];
       StepParams<T> P = base_params<T>(p);

@@ -121,8 +121,23 @@ struct StepLaunch {
   CUtensorMap cur, old, s, q;
   int nprob;
   int zchunks;
+  // optional dispatch order: block b of a 1-D grid takes the tile items[b],
+  // packed by pack_step_item (heaviest tiles first, so that the last wave is
+  // made of light ones); NULL: a 3-D grid of (tile x, tile y, z chunk +
+  // zchunks x problem)
+  const int *items;
   StepParams<T> p[NB];
 };
+
+// Tiles per axis of the step kernels' launch grid (FP32: 32 x 16 tiles,
+// with n = 32 m + 1 covered by m x tiles; FP64: 32 x 8 tiles).
+int step_tiles_x(int n, bool fp32);
+int step_tiles_y(int n, bool fp32);
+// One dispatch item: tile x (< 32), tile y (< 128), z chunk (< 512), problem
+// of the launch (< 16).
+__host__ __device__ inline int pack_step_item(int tx, int ty, int zc, int prob) {
+  return tx | (ty << 5) | (zc << 12) | (prob << 21);
+}
 
 // Sets the dynamic shared-memory limit of every step-kernel instance (once,
 // before any launch or capture).

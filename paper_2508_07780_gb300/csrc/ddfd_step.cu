@@ -1,12 +1,20 @@
 // Explicit step kernels of the hybrid FE/FD scheme (forward and adjoint).
 //
-// Work decomposition: one CTA owns a 32 x 8 (x, y) tile and a chunk of kz
-// consecutive z planes; one thread per (x, y) column.  The planes of the
-// current field (with a one-node halo in y and a 16-byte-aligned halo in x),
-// the centre tile of the previous level, and (on tiles that touch the FEM
-// cube) the coefficient planes are staged into shared memory by TMA tile
-// loads through a ring of RING stages guarded by mbarriers, so that
-// several planes are in flight per CTA while the previous ones are computed.
+// Work decomposition: one CTA owns an (x, y) tile and a chunk of kz
+// consecutive z planes, which it marches through plane by plane.
+//   - FP32 (k_step_pair): 32 x 16 tiles, 8 compute warps; each thread owns
+//     two x-adjacent nodes, whose arithmetic runs in packed FP32 (one
+//     instruction for both nodes); on a grid of n = 32 m + 1 nodes the last
+//     tile also updates the column x = n - 1.
+//   - FP64 (k_step): 32 x 8 tiles, one node per thread, 8 compute warps and
+//     a producer warp.
+// The planes of the current field (with a one-node halo in y and a
+// 16-byte-aligned halo in x), the centre tile of the previous level, and (on
+// tiles that touch the FEM cube) the coefficient planes are staged into
+// shared memory by TMA tile loads through a ring of stages guarded by
+// mbarriers, so that several planes are in flight per CTA while the previous
+// ones are computed.  A launch may carry a dispatch order (StepLaunch::items):
+// whole z slabs of tiles, heaviest first.
 //
 // Per node and step:
 //   FD part (every node): 7-point Laplacian with ghost-node (mirror) Neumann
@@ -225,15 +233,50 @@ __device__ __forceinline__ void produce_planes(const CUtensorMap *mcur, const CU
     mbar_wait_bounded(&bar[q % S::RING], (uint32_t)((q / S::RING) & 1), spin);
 }
 
+// Tiles per axis of the launch grid (device side of step_tiles_x / _y).  x
+// tiles of the FP32 step kernel: with n = 32 m + 1 the last column is updated
+// by the last of m tiles (k_step_pair's x tail) instead of by a tile of its own.
+__host__ __device__ constexpr int tiles_pair_x(int n) { return n % STEP_TX == 1 ? n / STEP_TX : (n + STEP_TX - 1) / STEP_TX; }
+template <typename T>
+__device__ __forceinline__ int step_tiles_dev_x(int n) {
+  return sizeof(T) == 4 ? tiles_pair_x(n) : (n + STEP_TX - 1) / STEP_TX;
+}
+template <typename T>
+__device__ __forceinline__ int step_tiles_dev_y(int n) {
+  return (n + StepTile<T>::TY - 1) / StepTile<T>::TY;
+}
+
+// Tile of this CTA: (problem of the launch, tile x, tile y, z chunk), from the
+// launch's dispatch order if it has one, else from the 3-D grid.
+struct CtaTile {
+  int prob, tx, ty, zc;
+};
+template <typename LT>
+__device__ __forceinline__ CtaTile cta_tile(const LT &L) {
+  CtaTile t;
+  if (L.items) {
+    const int it = L.items[blockIdx.x];
+    t.tx = it & 31;
+    t.ty = (it >> 5) & 127;
+    t.zc = (it >> 12) & 511;
+    t.prob = it >> 21;
+  } else {
+    t.tx = (int)blockIdx.x;
+    t.ty = (int)blockIdx.y;
+    t.prob = (int)blockIdx.z / L.zchunks;
+    t.zc = (int)blockIdx.z - t.prob * L.zchunks;
+  }
+  return t;
+}
+
 template <typename T, bool ADJ, int NB>
 __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
     k_step(const __grid_constant__ StepLaunch<T, NB> L) {
   using S = Stage<T>;
-  // problem of this CTA (uniform) and its z chunk
-  const int prob = NB == 1 ? 0 : (int)blockIdx.z / L.zchunks;
-  const int zc = NB == 1 ? (int)blockIdx.z : (int)blockIdx.z - prob * L.zchunks;
-  const int zchunks = NB == 1 ? (int)gridDim.z : L.zchunks;
-  const StepParams<T> &P = L.p[prob];
+  // problem of this CTA (uniform), its tile and z chunk
+  const CtaTile ct = cta_tile(L);
+  const int zc = ct.zc, zchunks = L.zchunks;
+  const StepParams<T> &P = L.p[NB == 1 ? 0 : ct.prob];
   constexpr int RE = S::ROWS * S::BXW;  // component stride of a staged plane
   constexpr int BW = S::BXW;
   // 128-byte aligned stage base, computed in the shared window so that the
@@ -246,9 +289,9 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   const int tid = threadIdx.x;
 
   if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
-    const long long nb = (long long)gridDim.x * gridDim.y * zchunks * blockDim.x;
-    long long t = ((long long)blockIdx.x + gridDim.x * ((long long)blockIdx.y + gridDim.y * zc)) *
-                      blockDim.x + tid;
+    const int gx = step_tiles_dev_x<T>(n), gy = step_tiles_dev_y<T>(n);
+    const long long nb = (long long)gx * gy * zchunks * blockDim.x;
+    long long t = ((long long)ct.tx + gx * ((long long)ct.ty + (long long)gy * zc)) * blockDim.x + tid;
     for (; t < 3LL * P.n_det; t += nb) {
       const int d = (int)(t / 3), c = (int)(t - 3LL * d);
       P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
@@ -258,7 +301,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   const int tx = tid & 31, ty = tid >> 5;
   // one CTA per (tile, z chunk): planes k0-1 .. k1 are staged, plane index
   // p = kk - (k0 - 1) in slot p % RING
-  const int x0 = blockIdx.x * STEP_TX, y0 = blockIdx.y * S::TY;
+  const int x0 = ct.tx * STEP_TX, y0 = ct.ty * S::TY;
   const int k0 = zc * P.kz;
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
@@ -514,98 +557,105 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
 
 __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 
-// acc + w v for a compile-time weight (0 and +-1 cost nothing extra).
-__device__ __forceinline__ float wacc(float acc, int w, float v) {
+// Packed FP32 (sm_100+): one instruction for the two nodes of a pair.  These
+// round exactly like the scalar operations; a - b is written fma(b, -1, a),
+// which is exact in its negation.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+#define kOne f2(1.f)
+#define kZero f2(0.f)
+#define kM1 f2(-1.f)
+#define kM6 f2(-6.f)
+#define kSixth f2(1.f / 6.f)
+#define kMSixth f2(-1.f / 6.f)
+
+// acc + w v for a compile-time weight (0 and +-1 cost no multiply).
+__device__ __forceinline__ float2 wacc2(float2 acc, int w, float2 v) {
   if (w == 0) return acc;
-  if (w == 1) return acc + v;
-  if (w == -1) return acc - v;
-  return fmaf((float)w, v, acc);
+  if (w == 1) return add2(acc, v);
+  if (w == -1) return fma2(v, kM1, acc);
+  return fma2(f2((float)w), v, acc);
 }
 
-// Input component d of the two 15-point block stencils of the pair (a at x,
-// b at x+1): the centre values and the 7 (+o, -o) pair sums, added as
-// out_c += B_o[c][d] * (...), B = kb / 6 applied by the caller.
-__device__ __forceinline__ void block_acc_pair(int d, float v0a, const float pa[7], float v0b, const float pb[7],
-                                               float oa[3], float ob[3]) {
+// Input component d of the pair's two 15-point block stencils (a at x, b at
+// x+1): the centre values and the 7 (+o, -o) pair sums, added as
+// out_c += B_o[c][d] * (...), B = kb / 6 applied by the caller; both nodes
+// share the weights.
+__device__ __forceinline__ void block_acc2(int d, float2 v0, const float2 ps[7], float2 out[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float ua = wacc(oa[c], kb(0, c * 3 + d), v0a);
-    float ub = wacc(ob[c], kb(0, c * 3 + d), v0b);
+    float2 u = wacc2(out[c], kb(0, c * 3 + d), v0);
 #pragma unroll
-    for (int p = 0; p < 7; ++p) {
-      ua = wacc(ua, kb(p + 1, c * 3 + d), pa[p]);
-      ub = wacc(ub, kb(p + 1, c * 3 + d), pb[p]);
-    }
-    oa[c] = ua;
-    ob[c] = ub;
+    for (int p = 0; p < 7; ++p) u = wacc2(u, kb(p + 1, c * 3 + d), ps[p]);
+    out[c] = u;
   }
 }
 
-// Values of one input component at the 22 positions the pair's two stencils
-// touch, plane k (row y: x-1..x+2; row y+1: x..x+2; row y-1: x-1..x+1), plane
-// k+1 (rows y, y+1: x..x+2) and plane k-1 (rows y, y-1: x-1..x+1), reduced to
-// the pair sums of each node.  f(position value, s index) returns the stencil
-// operand: s E in the forward, mu in the adjoint.
-struct PairVals {
-  float c0, c1, m, p2;            // plane k, row y: x, x+1, x-1, x+2
-  float yp0, yp1, yp2;            // plane k, row y+1: x, x+1, x+2
-  float ym0, ym1, ymm;            // plane k, row y-1: x, x+1, x-1
-  float pc0, pc1, pp2;            // plane k+1, row y: x, x+1, x+2
-  float pyp0, pyp1, pyp2;         // plane k+1, row y+1: x, x+1, x+2
-  float mc0, mc1, mm;             // plane k-1, row y: x, x+1, x-1
-  float mym0, mym1, mymm;         // plane k-1, row y-1: x, x+1, x-1
+// The 22 positions the pair's two stencils touch, as 11 pairs: plane k (row y:
+// x-1..x+2; row y+1: x..x+2; row y-1: x-1..x+1), plane k+1 (rows y, y+1:
+// x..x+2) and plane k-1 (rows y, y-1: x-1..x+1).
+struct PairVals2 {
+  float2 c;         // plane k, row y: x, x+1
+  float2 yp, ym;    // plane k, rows y+1 and y-1: x, x+1
+  float2 pc, mc;    // planes k+1 and k-1, row y: x, x+1
+  float2 py, my;    // plane k+1 row y+1, plane k-1 row y-1: x, x+1
+  float2 mp;        // plane k, row y: x-1, x+2
+  float2 e9;        // plane k: row y+1 x+2, row y-1 x-1
+  float2 e10;       // plane k+1: row y x+2, row y+1 x+2
+  float2 e11;       // plane k-1: row y x-1, row y-1 x-1
+  __device__ __forceinline__ void mul(const PairVals2 &s) {
+    c = mul2(c, s.c);
+    yp = mul2(yp, s.yp);
+    ym = mul2(ym, s.ym);
+    pc = mul2(pc, s.pc);
+    mc = mul2(mc, s.mc);
+    py = mul2(py, s.py);
+    my = mul2(my, s.my);
+    mp = mul2(mp, s.mp);
+    e9 = mul2(e9, s.e9);
+    e10 = mul2(e10, s.e10);
+    e11 = mul2(e11, s.e11);
+  }
 };
 
-__device__ __forceinline__ void pair_sums(const PairVals &v, float pa[7], float pb[7]) {
-  // offsets (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,0,1) (0,1,1) (1,1,1)
-  pa[0] = v.c1 + v.m;
-  pa[1] = v.yp0 + v.ym0;
-  pa[2] = v.pc0 + v.mc0;
-  pa[3] = v.yp1 + v.ymm;
-  pa[4] = v.pc1 + v.mm;
-  pa[5] = v.pyp0 + v.mym0;
-  pa[6] = v.pyp1 + v.mymm;
-  pb[0] = v.p2 + v.c0;
-  pb[1] = v.yp1 + v.ym1;
-  pb[2] = v.pc1 + v.mc1;
-  pb[3] = v.yp2 + v.ym0;
-  pb[4] = v.pp2 + v.mc0;
-  pb[5] = v.pyp1 + v.mym1;
-  pb[6] = v.pyp2 + v.mym0;
+// Pair sums of the offsets (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,0,1) (0,1,1)
+// (1,1,1): x is node a's v_{i+o} + v_{i-o}, y node b's.
+__device__ __forceinline__ void pair_sums2(const PairVals2 &v, float2 ps[7]) {
+  ps[0] = add2(make_float2(v.c.y, v.mp.y), make_float2(v.mp.x, v.c.x));
+  ps[1] = add2(v.yp, v.ym);
+  ps[2] = add2(v.pc, v.mc);
+  ps[3] = add2(make_float2(v.yp.y, v.e9.x), make_float2(v.e9.y, v.ym.x));
+  ps[4] = add2(make_float2(v.pc.y, v.e10.x), make_float2(v.e11.x, v.mc.x));
+  ps[5] = add2(v.py, v.my);
+  ps[6] = add2(make_float2(v.py.y, v.e10.y), make_float2(v.e11.y, v.my.x));
 }
 
-// Field values of component d at the 22 positions; the ones the Laplacian
-// already loaded are passed in (cen, above, below, rows y-1 and y+1 at x,x+1,
-// x-1 and x+2 on plane k).
-__device__ __forceinline__ PairVals pair_field(const float *e0, const float *ep, const float *em, int ci, float2 cen,
-                                               float2 ab, float2 bl, float2 ym, float2 yp, float xm, float xp2) {
+// Values of one component at the 22 positions; the ones the Laplacian already
+// loaded are passed in (centre, planes k +- 1, rows y -+ 1, x-1 and x+2).
+__device__ __forceinline__ PairVals2 pair_vals(const float *e0, const float *ep, const float *em, int ci,
+                                               float2 cen, float2 ab, float2 bl, float2 ym, float2 yp, float xm,
+                                               float xp2) {
   constexpr int BW = PairStage::BXW;
-  PairVals v;
-  v.c0 = cen.x;
-  v.c1 = cen.y;
-  v.m = xm;
-  v.p2 = xp2;
-  v.yp0 = yp.x;
-  v.yp1 = yp.y;
-  v.yp2 = e0[ci + BW + 2];
-  v.ym0 = ym.x;
-  v.ym1 = ym.y;
-  v.ymm = e0[ci - BW - 1];
-  v.pc0 = ab.x;
-  v.pc1 = ab.y;
-  v.pp2 = ep[ci + 2];
-  const float2 py = ld2(ep + ci + BW);
-  v.pyp0 = py.x;
-  v.pyp1 = py.y;
-  v.pyp2 = ep[ci + BW + 2];
-  v.mc0 = bl.x;
-  v.mc1 = bl.y;
-  v.mm = em[ci - 1];
-  const float2 my = ld2(em + ci - BW);
-  v.mym0 = my.x;
-  v.mym1 = my.y;
-  v.mymm = em[ci - BW - 1];
+  PairVals2 v;
+  v.c = cen;
+  v.yp = yp;
+  v.ym = ym;
+  v.pc = ab;
+  v.mc = bl;
+  v.py = ld2(ep + ci + BW);
+  v.my = ld2(em + ci - BW);
+  v.mp = make_float2(xm, xp2);
+  v.e9 = make_float2(e0[ci + BW + 2], e0[ci - BW - 1]);
+  v.e10 = make_float2(ep[ci + 2], ep[ci + BW + 2]);
+  v.e11 = make_float2(em[ci - 1], em[ci - BW - 1]);
   return v;
+}
+
+// The s = eps - 1 plane of a stage.
+__device__ __forceinline__ const float *S0f(const unsigned char *stage) {
+  return (const float *)(stage + PairStage::S_OFF);
 }
 
 // Staging: the forward CTA has no producer warp: thread 0 stages the first
@@ -625,10 +675,9 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
   constexpr bool PW = PairMode<ADJ>::PRODUCER_WARP;
   using S = PairStage;
   constexpr int RE = S::RE, BW = S::BXW, TXY = S::TXY;
-  const int prob = NB == 1 ? 0 : (int)blockIdx.z / L.zchunks;
-  const int zc = NB == 1 ? (int)blockIdx.z : (int)blockIdx.z - prob * L.zchunks;
-  const int zchunks = NB == 1 ? (int)gridDim.z : L.zchunks;
-  const StepParams<float> &P = L.p[prob];
+  const CtaTile ct = cta_tile(L);
+  const int zc = ct.zc, zchunks = L.zchunks;
+  const StepParams<float> &P = L.p[NB == 1 ? 0 : ct.prob];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint64_t *bar = (uint64_t *)(smem + S::RING * S::BYTES);  // "full": plane landed
@@ -640,16 +689,16 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
   const int tid = threadIdx.x;
 
   if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
-    const long long nb = (long long)gridDim.x * gridDim.y * zchunks * blockDim.x;
-    long long t = ((long long)blockIdx.x + gridDim.x * ((long long)blockIdx.y + gridDim.y * zc)) *
-                      blockDim.x + tid;
+    const int gx = step_tiles_dev_x<float>(n), gy = step_tiles_dev_y<float>(n);
+    const long long nb = (long long)gx * gy * zchunks * blockDim.x;
+    long long t = ((long long)ct.tx + gx * ((long long)ct.ty + (long long)gy * zc)) * blockDim.x + tid;
     for (; t < 3LL * P.n_det; t += nb) {
       const int d = (int)(t / 3), c = (int)(t - 3LL * d);
       P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
     }
   }
 
-  const int x0 = blockIdx.x * S::TX, y0 = blockIdx.y * S::TY;
+  const int x0 = ct.tx * S::TX, y0 = ct.ty * S::TY;
   const int k0 = zc * P.kz;
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
@@ -747,6 +796,7 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
     }
   };
 
+  const float2 R2 = make_float2(P.r2, P.r2);
   int wq = 0, wslot = 0;   // planes waited so far, slot of the next wait
   uint32_t wphase = 0;     // parity of the next wait
   int sm1 = 0, s0 = 1, sp1 = 2;  // slots of planes p-1, p, p+1 (p = k - k0 + 1)
@@ -788,8 +838,12 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
       ab[c] = ld2(Ep + c * RE + ci);
     }
     if (live_a) {
-      float Ra[3], Rb[3], xm[3], xp2[3];
-      float2 ym[3], yp[3];
+      // The pair's arithmetic runs in packed FP32 (x: node a, y: node b).  Q
+      // holds -R, so that every subtraction is a multiply-add with a constant
+      // (exact negations); a boundary node converts to R for the scalar
+      // boundary terms.
+      float2 Q[3], ym[3], yp[3];
+      float xm[3], xp2[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float *e = E0 + c * RE + ci;
@@ -800,19 +854,18 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
         const float xma = ex0 ? cen[c].y : xm[c];   // ghost x-1 = x+1 at x = 0
         const float xpa = exa ? xm[c] : cen[c].y;   // ghost x+1 = x-1 at x = n-1
         const float xpb = exb ? cen[c].x : xp2[c];
-        Ra[c] = 6.f * cen[c].x - (((((xpa + xma) + yp[c].x) + ym[c].x) + ab[c].x) + below[c].x);
-        Rb[c] = 6.f * cen[c].y - (((((xpb + cen[c].x) + yp[c].y) + ym[c].y) + ab[c].y) + below[c].y);
+        float2 sn = add2(make_float2(xpa, xpb), make_float2(xma, cen[c].x));
+        sn = add2(add2(add2(add2(sn, yp[c]), ym[c]), ab[c]), below[c]);
+        Q[c] = fma2(kM6, cen[c], sn);  // (neighbour sum) - 6 E
       }
-      float Aa = 1.f, Ab = 1.f, Ba = 0.f, Bb = 0.f, Ca = 1.f, Cb = 1.f;
-      float sxa[3] = {0.f, 0.f, 0.f}, sxb[3] = {0.f, 0.f, 0.f};
+      float2 A2 = kOne, B2 = kZero, C2 = kOne;
+      float2 SX[3] = {kZero, kZero, kZero};
       const bool fre_a = free_a && kfree, fre_b = free_b && kfree;
-      if (colfem && kfem) {
+      const bool fem_pair = colfem && kfem;
+      if (fem_pair) {
         const float *Q0 = (const float *)(b0 + S::Q_OFF);
-        const float2 q1 = ld2(Q0 + oi), q2 = ld2(Q0 + TXY + oi);
-        Aa = q1.x;
-        Ab = q1.y;
-        Ca = q2.x;
-        Cb = q2.y;
+        A2 = ld2(Q0 + oi);
+        C2 = ld2(Q0 + TXY + oi);
         if (P.ebe_r) {
           // element-by-element rows computed by k_ebe for this step
           const int fm = P.b - P.a - 1;
@@ -820,104 +873,82 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             if (fem_a) {
-              Ra[c] = P.ebe_r[c * P.ebe_rows + row];
-              if (ADJ) sxa[c] = P.ebe_q[c * P.ebe_rows + row];
+              Q[c].x = -P.ebe_r[c * P.ebe_rows + row];
+              if (ADJ) SX[c].x = P.ebe_q[c * P.ebe_rows + row];
             }
             if (fem_b) {
-              Rb[c] = P.ebe_r[c * P.ebe_rows + row + 1];
-              if (ADJ) sxb[c] = P.ebe_q[c * P.ebe_rows + row + 1];
+              Q[c].y = -P.ebe_r[c * P.ebe_rows + row + 1];
+              if (ADJ) SX[c].y = P.ebe_q[c * P.ebe_rows + row + 1];
             }
           }
         } else if (!ADJ) {
           // forward: sum_o B_o (s E)_{i+o} for both nodes
-          const float *S0 = (const float *)(b0 + S::S_OFF);
-          const float *Sp = (const float *)(bp1 + S::S_OFF);
-          const float *Sm = (const float *)(bm1 + S::S_OFF);
-          PairVals s;
-          {
-            const float2 c2 = ld2(S0 + ci), y2 = ld2(S0 + ci + BW), m2 = ld2(S0 + ci - BW);
-            const float2 pc = ld2(Sp + ci), py = ld2(Sp + ci + BW);
-            const float2 mc = ld2(Sm + ci), my = ld2(Sm + ci - BW);
-            s.c0 = c2.x;
-            s.c1 = c2.y;
-            s.m = S0[ci - 1];
-            s.p2 = S0[ci + 2];
-            s.yp0 = y2.x;
-            s.yp1 = y2.y;
-            s.yp2 = S0[ci + BW + 2];
-            s.ym0 = m2.x;
-            s.ym1 = m2.y;
-            s.ymm = S0[ci - BW - 1];
-            s.pc0 = pc.x;
-            s.pc1 = pc.y;
-            s.pp2 = Sp[ci + 2];
-            s.pyp0 = py.x;
-            s.pyp1 = py.y;
-            s.pyp2 = Sp[ci + BW + 2];
-            s.mc0 = mc.x;
-            s.mc1 = mc.y;
-            s.mm = Sm[ci - 1];
-            s.mym0 = my.x;
-            s.mym1 = my.y;
-            s.mymm = Sm[ci - BW - 1];
-          }
-          float oa[3] = {0.f, 0.f, 0.f}, ob[3] = {0.f, 0.f, 0.f};
+          const PairVals2 sv = pair_vals(S0f(b0), S0f(bp1), S0f(bm1), ci, ld2(S0f(b0) + ci), ld2(S0f(bp1) + ci),
+                                         ld2(S0f(bm1) + ci), ld2(S0f(b0) + ci - BW), ld2(S0f(b0) + ci + BW),
+                                         S0f(b0)[ci - 1], S0f(b0)[ci + 2]);
+          float2 O[3] = {kZero, kZero, kZero};
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            PairVals v = pair_field(E0 + d * RE, Ep + d * RE, Em + d * RE, ci, cen[d], ab[d], below[d], ym[d],
+            PairVals2 v = pair_vals(E0 + d * RE, Ep + d * RE, Em + d * RE, ci, cen[d], ab[d], below[d], ym[d],
                                     yp[d], xm[d], xp2[d]);
-            v.c0 *= s.c0; v.c1 *= s.c1; v.m *= s.m; v.p2 *= s.p2;
-            v.yp0 *= s.yp0; v.yp1 *= s.yp1; v.yp2 *= s.yp2;
-            v.ym0 *= s.ym0; v.ym1 *= s.ym1; v.ymm *= s.ymm;
-            v.pc0 *= s.pc0; v.pc1 *= s.pc1; v.pp2 *= s.pp2;
-            v.pyp0 *= s.pyp0; v.pyp1 *= s.pyp1; v.pyp2 *= s.pyp2;
-            v.mc0 *= s.mc0; v.mc1 *= s.mc1; v.mm *= s.mm;
-            v.mym0 *= s.mym0; v.mym1 *= s.mym1; v.mymm *= s.mymm;
-            float pa[7], pb[7];
-            pair_sums(v, pa, pb);
-            block_acc_pair(d, v.c0, pa, v.c1, pb, oa, ob);
+            v.mul(sv);
+            float2 Ps[7];
+            pair_sums2(v, Ps);
+            block_acc2(d, v.c, Ps, O);
           }
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            Ra[c] += oa[c] * (1.f / 6.f);
-            Rb[c] += ob[c] * (1.f / 6.f);
-          }
+          for (int c = 0; c < 3; ++c) Q[c] = fma2(O[c], kMSixth, Q[c]);
         } else {
           // adjoint: s_i sum_o B_o mu_{i+o}; the sums are kept for the gradient
-          const float2 s0v = ld2((const float *)(b0 + S::S_OFF) + ci);
+          const float2 s0v = ld2(S0f(b0) + ci);
           if (s0v.x != 0.f || s0v.y != 0.f || fre_a || fre_b) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-              const PairVals v = pair_field(E0 + d * RE, Ep + d * RE, Em + d * RE, ci, cen[d], ab[d], below[d],
+              const PairVals2 v = pair_vals(E0 + d * RE, Ep + d * RE, Em + d * RE, ci, cen[d], ab[d], below[d],
                                             ym[d], yp[d], xm[d], xp2[d]);
-              float pa[7], pb[7];
-              pair_sums(v, pa, pb);
-              block_acc_pair(d, v.c0, pa, v.c1, pb, sxa, sxb);
+              float2 Ps[7];
+              pair_sums2(v, Ps);
+              block_acc2(d, v.c, Ps, SX);
             }
+            const float2 ns0 = mul2(s0v, kM1);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              sxa[c] *= (1.f / 6.f);
-              sxb[c] *= (1.f / 6.f);
-              Ra[c] += s0v.x * sxa[c];
-              Rb[c] += s0v.y * sxb[c];
+              SX[c] = mul2(SX[c], kSixth);
+              Q[c] = fma2(ns0, SX[c], Q[c]);
             }
           }
         }
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Ra[c] *= P.r2;
-        Rb[c] *= P.r2;
+      for (int c = 0; c < 3; ++c) Q[c] = mul2(Q[c], R2);
+      const bool bnd_pa = bnd_a || kbnd, bnd_pb = live_b && (bnd_b || kbnd);
+      if (bnd_pa || bnd_pb) {
+        float Rn[3];
+        if (bnd_pa) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Rn[c] = -Q[c].x;
+          boundary(x, k, Rn, A2.x, B2.x, C2.x);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Q[c].x = -Rn[c];
+        }
+        if (bnd_pb) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Rn[c] = -Q[c].y;
+          boundary(x + 1, k, Rn, A2.y, B2.y, C2.y);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Q[c].y = -Rn[c];
+        }
       }
-      if (bnd_a || kbnd) boundary(x, k, Ra, Aa, Ba, Ca);
-      if (live_b && (bnd_b || kbnd)) boundary(x + 1, k, Rb, Ab, Bb, Cb);
       const float *O0 = (const float *)(b0 + S::O_OFF);
+      const bool plain = !fem_pair && !bnd_pa && !bnd_pb;  // A = 1, B = 0, C = 1
       float2 od[3], nw[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         od[c] = ld2(O0 + c * TXY + oi);
-        nw[c].x = cen[c].x + (Aa * (cen[c].x - od[c].x) + (Ba * cen[c].x - Ca * Ra[c]));
-        nw[c].y = cen[c].y + (Ab * (cen[c].y - od[c].y) + (Bb * cen[c].y - Cb * Rb[c]));
+        const float2 dv = fma2(od[c], kM1, cen[c]);  // E^n - E^{n-1}
+        // E^{n+1} = E^n + A (E^n - E^{n-1}) + B E^n - C R, with R = -Q
+        nw[c] = plain ? add2(cen[c], add2(dv, Q[c]))
+                      : add2(cen[c], add2(mul2(A2, dv), fma2(C2, Q[c], mul2(B2, cen[c]))));
         if (live_b)
           *reinterpret_cast<float2 *>(out + c * cs) = nw[c];
         else
@@ -943,7 +974,7 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
             for (int c = 0; c < 3; ++c) {
               const float hv = __ldg(P.hist_r + c * P.n_free + f);
               const float nv = h ? nw[c].y : nw[c].x, cv = h ? cen[c].y : cen[c].x, ov = h ? od[c].y : od[c].x;
-              const float sv = h ? sxb[c] : sxa[c];
+              const float sv = h ? SX[c].y : SX[c].x;
               ge += hv * ((nv - 2.f * cv + ov) + P.r2 * sv);
               gs += hv * (nv - ov);
             }
@@ -1050,24 +1081,27 @@ cudaError_t prepare_step_kernels() {
   return cudaSuccess;
 }
 
-template <bool ADJ, int NB>
-static void launch_step(const StepLaunch<double, NB> &L, cudaStream_t s) {
-  const int ty = Stage<double>::TY;
-  const StepParams<double> &P = L.p[0];
-  const dim3 grid((P.n + STEP_TX - 1) / STEP_TX, (P.n + ty - 1) / ty, L.zchunks * L.nprob);
-  k_step<double, ADJ, NB><<<grid, STEP_THREADS, Stage<double>::SMEM, s>>>(L);
+int step_tiles_x(int n, bool fp32) { return fp32 ? tiles_pair_x(n) : (n + STEP_TX - 1) / STEP_TX; }
+int step_tiles_y(int n, bool fp32) {
+  const int ty = fp32 ? StepTile<float>::TY : StepTile<double>::TY;
+  return (n + ty - 1) / ty;
 }
-// x tiles of the FP32 step kernel: with n = 32 m + 1 the last column is
-// updated by the last of m tiles (k_step_pair's x tail) instead of by a tile
-// of its own
-static int pair_tiles_x(int n) { return n % STEP_TX == 1 ? n / STEP_TX : (n + STEP_TX - 1) / STEP_TX; }
+
+// Launch grid: 1-D over the dispatch items, or the 3-D tile grid.
+template <typename T, int NB>
+static dim3 step_grid(const StepLaunch<T, NB> &L) {
+  const int gx = step_tiles_x(L.p[0].n, sizeof(T) == 4), gy = step_tiles_y(L.p[0].n, sizeof(T) == 4);
+  if (L.items) return dim3((unsigned)(gx * gy * L.zchunks * L.nprob));
+  return dim3(gx, gy, L.zchunks * L.nprob);
+}
 
 template <bool ADJ, int NB>
+static void launch_step(const StepLaunch<double, NB> &L, cudaStream_t s) {
+  k_step<double, ADJ, NB><<<step_grid(L), STEP_THREADS, Stage<double>::SMEM, s>>>(L);
+}
+template <bool ADJ, int NB>
 static void launch_step(const StepLaunch<float, NB> &L, cudaStream_t s) {
-  const int ty = PairStage::TY;
-  const StepParams<float> &P = L.p[0];
-  const dim3 grid(pair_tiles_x(P.n), (P.n + ty - 1) / ty, L.zchunks * L.nprob);
-  k_step_pair<ADJ, NB><<<grid, PairMode<ADJ>::THREADS, PairStage::SMEM, s>>>(L);
+  k_step_pair<ADJ, NB><<<step_grid(L), PairMode<ADJ>::THREADS, PairStage::SMEM, s>>>(L);
 }
 
 template <typename T, int NB>
