@@ -120,45 +120,26 @@ def test_autograd_two_losses_on_one_handle_keep_their_own_gradients():
 
 
 def test_differentiable_301_checkpointed_gradient_vs_finite_differences():
+    """The differentiable 301^3 / 4000-step workload with 32 snapshots: the
+    FP32 and FP64 checkpointed adjoint gradients against central differences
+    of the FP64 functional (delta = 1e-4) at free nodes drawn uniformly
+    (seeded), for eps and sigma, with the per-node bars of
+    paper_2508_07780_gb300.fdcheck; observed data: the layers-only model's
+    trace.  Two nodes per coefficient here (each costs four FP64 forward
+    runs of 4000 steps); `python -m paper_2508_07780_gb300.fdcheck` runs the
+    same check at 20 nodes."""
+    from paper_2508_07780_gb300.fdcheck import check_gradient
     w = workload("c4_fp32_301")
-    eps, sig = w.model()
-    # observed data: half the layers-only model's trace (FP64)
-    p64 = gpu_problem(w, "fp64", n_snapshots=32)
-    e0, s0 = w.model(inclusions=False)
-    p64.set_coeffs(e0, s0)
-    eobs = 0.5 * p64.forward()
     p32 = gpu_problem(w, "fp32", n_snapshots=32)
-    p32.set_coeffs(eps, sig)
+    p32.set_coeffs(*w.model())
     p32.forward(want_trace=False)
-    p32.functional(eobs)
-    p32.adjoint(eobs)
-    ge32, gs32 = p32.gradient()
     info = p32.get_info()
     full_history = (w.n_steps + 1) * 3 * w.n_free * 4
     assert info.device_bytes < 0.3 * full_history       # snapshots instead of all time levels
-    assert info.forward_steps == 2 * w.n_steps
     p32.close()
-    rng = np.random.default_rng(4)
-    delta = 1e-4
-
-    def J_at(e, s):
-        p64.set_coeffs(e, s)
-        p64.forward(want_trace=False)
-        return p64.functional(eobs)
-
-    for which, g in (("eps", ge32), ("sig", gs32)):
-        scale = np.abs(g).max()
-        strong = np.nonzero(np.abs(g) > 0.1 * scale)[0]
-        i = rng.choice(strong)
-        vals = []
-        for sign in (+1, -1):
-            e2, s2 = eps.copy(), sig.copy()
-            if which == "eps":
-                e2[i] += sign * delta
-            else:
-                s2[i] += sign * delta
-            vals.append(J_at(e2, s2))
-        fd = (vals[0] - vals[1]) / (2 * delta)
-        print(f"301^3 {which}[{i}]: adjoint FP32 {g[i]:.6e}  FD FP64 {fd:.6e}")
-        assert abs(g[i] - fd) <= 1e-3 * scale
-    p64.close()
+    rep = check_gradient(w, n_nodes=2, seed=4)
+    for r in rep["rows"]:
+        print(f"301^3 {r['coef']}[{r['node']}]: FD {r['fd']:.6e}  FP32 {r['fp32']['g']:.6e} "
+              f"({r['fp32']['err'] / r['fp32']['bar']:.2f} of bar)  FP64 {r['fp64']['g']:.6e} "
+              f"({r['fp64']['err'] / r['fp64']['bar']:.2f} of bar)")
+    assert rep["ok"], rep["rows"]
