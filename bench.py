@@ -364,7 +364,7 @@ def run_batched(args, dev, stream, rank, world, peak):
     import torch.distributed as dist
     from paper_2508_07780_gb300 import Batch
 
-    probs = batched_problems(first=16 * rank)
+    probs = batched_problems(first=16 * rank, n_steps=args.batch_steps)
     cfgs = [dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp32",
                  src_dir=d[None, :], det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
                  stream=stream.cuda_stream) for w, d in probs]
@@ -581,7 +581,7 @@ def run_single_201(args, dev, stream, peak):
     errors against FP64, measured here."""
     import torch
     from paper_2508_07780_gb300 import Problem
-    w = workload("c2_fp32_201")
+    w = workload("c2_fp32_201", n_steps=args.single_steps)
     eps, sig = w.model()
     e_lay, s_lay = w.model(inclusions=False)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
@@ -632,7 +632,8 @@ def run_single_201(args, dev, stream, peak):
     torch.cuda.empty_cache()
     a, b = out["fp32"], out["fp64"]
     fb, ab = algorithmic_bytes(w.n, w.fem_n, 4)
-    kappa = float(np.linalg.norm(b["trace"]) / np.linalg.norm(b["trace"] - eo))
+    rn = float(np.linalg.norm(b["trace"] - eo))
+    kappa = float(np.linalg.norm(b["trace"]) / rn) if rn > 0 else None
     return {"workload": describe(w), "value": w.updates / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"],
             "device_bytes": int(a["bytes"]),
             "roofline": {"bound": "hbm", "peak": peak[0], "unit": "GB/s",
@@ -646,7 +647,8 @@ def run_single_201(args, dev, stream, peak):
                                      "traffic": traffic_per_launch("adjoint_dram_bytes_per_launch_full")}},
             "fp64_plain": {"value": w.updates / (b["ms"] / 1e3), "ms_per_step": b["ms"],
                            "fp32_speedup": b["ms"] / a["ms"]},
-            "accuracy_vs_fp64": {"trace": rel(a["trace"], b["trace"]), "J": abs(a["J"] - b["J"]) / abs(b["J"]),
+            "accuracy_vs_fp64": {"trace": rel(a["trace"], b["trace"]),
+                                 "J": abs(a["J"] - b["J"]) / abs(b["J"]) if b["J"] != 0 else None,
                                  "g_eps": rel(a["g_eps"], b["g_eps"]), "g_sig": rel(a["g_sig"], b["g_sig"]),
                                  "kappa": kappa,
                                  "observed_data": "the layers-only model's FP64 trace (unmodified)"}}
@@ -673,7 +675,9 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "grid": 161, "problems_per_gpu": 16, "n_steps": 1600,
+            "config": {"workload": BATCH_WORKLOAD if args.batch_steps == 1600 else
+                       BATCH_WORKLOAD.replace("1600 steps", f"{args.batch_steps} steps (profiling run)"),
+                       "grid": 161, "problems_per_gpu": 16, "n_steps": args.batch_steps,
                        "fem_n": [61, 81, 101, 121], "tile_kz": bat["kz"], "device_bytes": int(bat["dev_bytes"]),
                        "l2": "inputs larger than L2: 16 problems x 2 field levels of 3 x 161^3 FP32 plus "
                              "the E history, re-streamed every step",
@@ -712,6 +716,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison passes")
     ap.add_argument("--no-single", action="store_true", help="skip the single-source 201^3 workload")
     ap.add_argument("--cpu-workers", type=int, default=min(8, os.cpu_count() or 1))
+    ap.add_argument("--single-steps", type=int, default=2000,
+                    help="time steps of the single-source 201^3 workload (2000; fewer only for profiler captures)")
+    ap.add_argument("--batch-steps", type=int, default=1600,
+                    help="time steps of the batched workload (1600; fewer only for profiler captures: "
+                         "every step launch does the same work at any step count)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
