@@ -654,6 +654,88 @@ def run_single_201(args, dev, stream, peak):
                                  "observed_data": "the layers-only model's FP64 trace (unmodified)"}}
 
 
+def run_ebe(args, dev, stream, peak):
+    """The element-by-element FEM apply: the 201^3 workload with its 101^3
+    FEM cube gathered over the explicit Kuhn tetrahedra (fem_kind
+    DDFD_FEM_EBE), and a 241^3 grid whose 61^3 FEM cube is refined once
+    around the inclusion (fem_kind DDFD_FEM_MESH: gathered rows next to
+    refined elements and the new nodes, the untouched Kuhn rows on the block
+    stencil).  One source each, FP32, a forward + adjoint pass after a warm-up
+    pass; the gather's roofline from ddfd_time_gather (CUDA events, 20
+    launches each way).  The observed data is the same handle's trace of the
+    layers-only model: these legs measure speed (accuracy: the tests)."""
+    import torch
+    from paper_2508_07780_gb300 import Problem
+    from synth import box_bounds, detector_grid, layered_inclusion_model
+    from synth.mesh import extend_to_new_nodes, refined_fem_mesh
+    out = {}
+    legs = [("ebe_201", 201, 101, 2000, 0.3, None)]
+    if not args.no_refined:
+        legs.append(("refined_241", 241, 61, 2880, 0.25, "refine"))
+    for name, n, fem_n, nt, cfl, kind in legs:
+        t0 = time.perf_counter()
+        eps, sig = layered_inclusion_model(n, fem_n, 2 if n == 201 else 5, 3 if n == 201 else 1)
+        e0, s0 = layered_inclusion_model(n, fem_n, 2 if n == 201 else 5, 0)
+        kw = dict(n=n, fem_n=fem_n, n_steps=nt, cfl=cfl, precision="fp32", det_ij=detector_grid(n, fem_n, 32),
+                  stream=stream.cuda_stream)
+        extra = {}
+        if kind == "refine":
+            _, _, f0, f1 = box_bounds(n, fem_n)
+            nfr = f1 - f0 + 1
+            par, tets = refined_fem_mesh(n, fem_n, eps, sig, beta_eps=0.8, beta_sig=0.0,
+                                         region=(f0 + int(0.3 * nfr), f0 + int(0.7 * nfr)))
+            eps, sig = extend_to_new_nodes(n, fem_n, par, eps, sig)
+            e0, s0 = extend_to_new_nodes(n, fem_n, par, e0, s0)
+            p = Problem(fem_kind=2, mesh=(par, tets), **kw)
+            extra = {"new_nodes": int(par.shape[0]), "tets": int(tets.shape[0])}
+        else:
+            p = Problem(fem_kind=1, **kw)
+            extra = {"tets": 6 * (fem_n - 1) ** 3}
+        setup_s = time.perf_counter() - t0
+        p.set_coeffs(e0, s0)
+        eobs = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
+        p.forward_dev(eobs)
+        T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+        e_d, s_d = T(eps), T(sig)
+        ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
+        gs = torch.empty_like(ge)
+
+        def step():
+            p.set_coeffs_dev(e_d, s_d)
+            p.forward_dev(None)
+            p.functional_dev(eobs)
+            p.adjoint_dev(eobs)
+            p.gradient_dev(ge, gs)
+
+        step()
+        torch.cuda.synchronize(dev)
+        e0_ = torch.cuda.Event(enable_timing=True)
+        e1_ = torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        for _ in range(2):
+            step()
+        e1_.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0_.elapsed_time(e1_) / 2
+        fms, ams, fb, ab = p.time_gather(20)
+        p.close()
+        del eobs, e_d, s_d, ge, gs
+        torch.cuda.empty_cache()
+        updates = 2 * n ** 3 * nt
+        out[name] = {"workload": f"{n}^3 grid, FEM cube {fem_n}^3" + (" refined once around the inclusion"
+                                                                       if kind else " as explicit Kuhn tets")
+                     + f", {nt} steps, FP32, one source", **extra,
+                     "value": updates / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "setup_s": setup_s,
+                     "gather_roofline": {
+                         "bound": "hbm", "peak": peak[0], "unit": "GB/s",
+                         "kernels": "k_ebe" + (" + k_kuhn_rows" if kind else ""),
+                         "forward": {"ms": fms, "algorithmic_bytes": fb, "achieved": fb / (fms / 1e3) / 1e9,
+                                     "frac": fb / (fms / 1e3) / 1e9 / peak[0]},
+                         "adjoint": {"ms": ams, "algorithmic_bytes": ab, "achieved": ab / (ams / 1e3) / 1e9,
+                                     "frac": ab / (ams / 1e3) / 1e9 / peak[0]}}}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -701,6 +783,8 @@ def run_ours(args, rank, world, local_rank):
                             "per_problem": fp["errs"]}
     if single is not None:
         line["single_201"] = single
+    if world == 1 and not args.no_ebe:
+        line["element_gather"] = run_ebe(args, dev, stream, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_workers)
     print(json.dumps(line), flush=True)
@@ -715,6 +799,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison passes")
     ap.add_argument("--no-single", action="store_true", help="skip the single-source 201^3 workload")
+    ap.add_argument("--no-ebe", action="store_true", help="skip the element-gather legs")
+    ap.add_argument("--no-refined", action="store_true", help="skip the refined-mesh element-gather leg")
     ap.add_argument("--cpu-workers", type=int, default=min(8, os.cpu_count() or 1))
     ap.add_argument("--single-steps", type=int, default=2000,
                     help="time steps of the single-source 201^3 workload (2000; fewer only for profiler captures)")

@@ -242,6 +242,22 @@ int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t);
 int ddfd_set_capture(ddfd_problem *p, int32_t count, const int32_t *steps);
 int ddfd_get_capture(ddfd_problem *p, int32_t kind, int32_t idx, double *out);
 
+/* Device time of one step's element-apply launches (fem_kind DDFD_FEM_EBE or
+ * DDFD_FEM_MESH): the element gather, and for refined meshes the rows taken
+ * from the block stencil, run `reps` >= 1 times in the forward form and in
+ * the adjoint form on the handle's current fields, timed with CUDA events on
+ * its stream.  *fwd_ms, *adj_ms (may be NULL) receive the average per step
+ * (adj_ms 0 for forward_only handles); *fwd_bytes, *adj_bytes (may be NULL)
+ * the algorithmic bytes of those launches: each gathered tet's four node ids
+ * and twelve gradient values, each of its nodes' values once (field and s
+ * forward, field adjoint), each row's outputs (R forward; R and q adjoint),
+ * and for stencil rows their own node values and outputs.  The launches only
+ * overwrite the gather's row scratch, so the handle's state is unchanged.
+ * Errors: DDFD_E_ARG (no element gather, reps < 1), DDFD_E_TIMEOUT,
+ * DDFD_E_CUDA.  The paper has no counterpart (a measurement aid). */
+int ddfd_time_gather(ddfd_problem *p, int32_t reps, double *fwd_ms, double *adj_ms, int64_t *fwd_bytes,
+                     int64_t *adj_bytes);
+
 /* Failure-detection test hook (not for production runs; the paper has no
  * counterpart).  fault = 1: the first thread block of the element gather
  * never starts the bulk copy of its first block of rows, so the mbarrier it

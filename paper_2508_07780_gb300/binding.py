@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "ddfd_autotune", "ddfd_create_batch", "ddfd_destroy_batch", "ddfd_batch_last_error",
     "ddfd_batch_member", "ddfd_batch_forward", "ddfd_batch_forward_dev", "ddfd_batch_adjoint",
     "ddfd_batch_adjoint_dev", "ddfd_batch_autotune", "ddfd_batch_get_info",
-    "ddfd_cg_params_default", "ddfd_cg_run", "ddfd_test_gather_timeout",
+    "ddfd_cg_params_default", "ddfd_cg_run", "ddfd_test_gather_timeout", "ddfd_time_gather",
 )
 
 
@@ -159,6 +159,7 @@ def load_library(path: str = LIB_PATH):
     lib.ddfd_batch_autotune.argtypes = [P, c_int32, POINTER(c_int32)]
     lib.ddfd_batch_get_info.argtypes = [P, POINTER(ddfd_batch_info)]
     lib.ddfd_test_gather_timeout.argtypes = [P, c_int32, ctypes.c_uint32]
+    lib.ddfd_time_gather.argtypes = [P, c_int32, P, P, P, P]
     lib.ddfd_cg_params_default.argtypes = [POINTER(ddfd_cg_params)]
     lib.ddfd_cg_params_default.restype = None
     lib.ddfd_cg_run.argtypes = [P, P, POINTER(ddfd_cg_params), P, P, POINTER(ddfd_cg_iter), POINTER(c_int32),
@@ -384,6 +385,15 @@ class Problem:
         self._check(self._lib.ddfd_gradient_dev(self._h, _ptr(g_eps), _ptr(g_sig)))
 
     # -- test hooks -------------------------------------------------------------
+    def time_gather(self, reps=20):
+        """ddfd_time_gather: (forward ms, adjoint ms, forward bytes, adjoint
+        bytes) of one step's element-apply launches."""
+        f, a = c_double(), c_double()
+        fb, ab = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.ddfd_time_gather(self._h, int(reps), ctypes.byref(f), ctypes.byref(a),
+                                               ctypes.byref(fb), ctypes.byref(ab)))
+        return f.value, a.value, fb.value, ab.value
+
     def test_gather_timeout(self, fault, spin_limit=0):
         """ddfd_test_gather_timeout: fault=1 makes the element gather's first
         bounded wait run out (the next forward/adjoint fails with

@@ -1053,6 +1053,40 @@ int ddfd_get_timing(const ddfd_problem *p, ddfd_timing *t) {
   return DDFD_OK;
 }
 
+int ddfd_time_gather(ddfd_problem *p, int32_t reps, double *fwd_ms, double *adj_ms, int64_t *fwd_bytes,
+                     int64_t *adj_bytes) {
+  if (!p) return DDFD_E_ARG;
+  p->err.clear();
+  if (!p->ebe_rows) return fail(p, DDFD_E_ARG, "the handle has no element gather (fem_kind DDFD_FEM_EBE or DDFD_FEM_MESH)");
+  if (reps < 1) return fail(p, DDFD_E_ARG, "reps must be >= 1");
+  float ms[2] = {0.0f, 0.0f};
+  for (int adj = 0; adj < 2; ++adj) {
+    if (adj && !p->Mu[1]) break;  // forward_only: no adjoint fields
+    int64_t nk = 0;
+    const void *f = adj ? p->Mu[1] : p->E[1];
+    const void *xf = adj ? p->XMu[1] : p->X[1];
+    CK(cudaEventRecord(p->ev[0], p->stream));
+    for (int r = 0; r < reps; ++r) {
+      if (p->fp32)
+        enqueue_ebe<float>(p, f, adj != 0, p->stream, &nk, xf);
+      else
+        enqueue_ebe<double>(p, f, adj != 0, p->stream, &nk, xf);
+    }
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(p->ev[1], p->stream));
+    CK(cudaEventSynchronize(p->ev[1]));
+    CK(cudaEventElapsedTime(&ms[adj], p->ev[0], p->ev[1]));
+    p->launches += nk;
+  }
+  const int st = check_err(p);
+  if (st) return st;
+  if (fwd_ms) *fwd_ms = ms[0] / reps;
+  if (adj_ms) *adj_ms = ms[1] / reps;
+  if (fwd_bytes) *fwd_bytes = p->ebe_bytes_fwd;
+  if (adj_bytes) *adj_bytes = p->ebe_bytes_adj;
+  return DDFD_OK;
+}
+
 int ddfd_test_gather_timeout(ddfd_problem *p, int32_t fault, uint32_t spin_limit) {
   if (!p) return DDFD_E_ARG;
   p->err.clear();

@@ -31,6 +31,27 @@ int upload_ebe(ddfd_problem *p, long long rows, long long ntet, const std::vecto
         klist.push_back((int)r);
       }
   }
+  {
+    // algorithmic bytes: the tets incident to gathered rows and their nodes, once each
+    std::vector<unsigned char> tmark((size_t)ntet, 0);
+    long long grows = 0, nt_used = 0;
+    for (long long r = 0; r < rows; ++r) {
+      if (stencil && !use[r]) continue;
+      ++grows;
+      for (int q = rptr[r]; q < rptr[r + 1]; ++q) tmark[itet[q]] = 1;
+    }
+    std::vector<int> nodes;
+    for (long long t = 0; t < ntet; ++t)
+      if (tmark[t]) {
+        ++nt_used;
+        for (int q = 0; q < 4; ++q) nodes.push_back(tnode[t * 4 + q]);
+      }
+    std::sort(nodes.begin(), nodes.end());
+    const long long nn_used = std::unique(nodes.begin(), nodes.end()) - nodes.begin();
+    const long long es = (long long)p->esz, kr = (long long)klist.size();
+    p->ebe_bytes_fwd = nt_used * (16 + 12 * es) + nn_used * 4 * es + grows * 3 * es + kr * 7 * es;
+    p->ebe_bytes_adj = nt_used * (16 + 12 * es) + nn_used * 3 * es + grows * 6 * es + kr * 10 * es;
+  }
   EbePack pk;
   std::string m;
   if (!pack_ebe_blocks(rows, ntet, tnode.data(), tgrad.data(), rptr.data(), itet.data(), iloc.data(), rpos.data(),

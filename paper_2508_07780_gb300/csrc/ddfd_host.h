@@ -69,6 +69,10 @@ struct ddfd_problem {
   ddfd::EbeBlock *ebe_blocks = nullptr;
   unsigned char *ebe_blob = nullptr;
   int ebe_nblocks = 0, ebe_smem = 0;
+  // algorithmic bytes of one step's element-apply launches (forward, adjoint):
+  // each gathered tet's node ids and gradients, each of its nodes' values once,
+  // each row's outputs; stencil rows their own node values and outputs
+  int64_t ebe_bytes_fwd = 0, ebe_bytes_adj = 0;
   int test_fault = 0;          // ddfd_test_gather_timeout
   uint32_t test_spin = 0;
   int *kuhn_list = nullptr;   // explicit-mesh rows taken from the Kuhn block stencil

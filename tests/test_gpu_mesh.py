@@ -179,3 +179,35 @@ def test_cg_on_refined_mesh_matches_the_oracle():
         for k in ("J", "J_data", "gnorm_eps", "gnorm_sig", "alpha_eps", "beta_eps", "step_eps", "step_sig"):
             assert g[k] == pytest.approx(r[k], rel=1e-8, abs=1e-30), (g["iter"], k)
     assert rel_l2(eps - el, eo - el) <= 1e-8 and rel_l2(sig - sl, so - sl) <= 1e-8
+
+
+def test_time_gather_reports_times_and_bytes_and_keeps_the_state():
+    """ddfd_time_gather on an element-gather handle: positive times and the
+    algorithmic bytes of the launches; the forward state survives it (the
+    adjoint afterwards gives the gradient of a run without it); a stencil
+    handle is refused."""
+    from paper_2508_07780_gb300 import DDFDError, Problem
+    w = workload("small", n=25, fem_n=13, n_steps=40, seed=12)
+    eps, sig = w.model()
+    kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp32", det_ij=w.detectors(),
+              z_delta_frac=w.z_delta_frac, fem_kind=1)
+    res = []
+    for timed in (False, True):
+        p = Problem(**kw)
+        p.set_coeffs(eps, sig)
+        tr = p.forward()
+        if timed:
+            fms, ams, fb, ab = p.time_gather(5)
+            assert fms > 0 and ams > 0
+            # 10,164 of the 10,368 Kuhn tets of the 12^3 cubes touch a FEM row (the
+            # others have every vertex on the cube's faces): ids and gradients at least
+            assert fb >= 10164 * (16 + 48) and ab > fb
+        p.adjoint(0.5 * tr)
+        res.append(p.gradient())
+        p.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    q = Problem(n=13, fem_n=9, n_steps=3)
+    with pytest.raises(DDFDError) as e:
+        q.time_gather(2)
+    assert e.value.code == -1
+    q.close()
