@@ -586,7 +586,7 @@ def run_single_201(args, dev, stream, peak):
     e_lay, s_lay = w.model(inclusions=False)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, src_dir=w.directions(), det_ij=w.detectors(),
-              z_delta_frac=w.z_delta_frac, stream=stream.cuda_stream)
+              z_delta_frac=w.z_delta_frac, grad_variant=args.grad_variant, stream=stream.cuda_stream)
     out = {}
     for prec in ("fp64", "fp32"):
         p = Problem(precision=prec, **kw)
@@ -634,7 +634,7 @@ def run_single_201(args, dev, stream, peak):
     fb, ab = algorithmic_bytes(w.n, w.fem_n, 4)
     rn = float(np.linalg.norm(b["trace"] - eo))
     kappa = float(np.linalg.norm(b["trace"]) / rn) if rn > 0 else None
-    return {"workload": describe(w), "value": w.updates / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"],
+    return {"workload": describe(w), "gradient": args.grad_variant, "value": w.updates / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"],
             "device_bytes": int(a["bytes"]),
             "roofline": {"bound": "hbm", "peak": peak[0], "unit": "GB/s",
                          "forward": {"kernel": "k_step_pair<forward,1>", "avg_launch_ms": a["fwd"],
@@ -800,6 +800,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison passes")
     ap.add_argument("--no-single", action="store_true", help="skip the single-source 201^3 workload")
     ap.add_argument("--no-ebe", action="store_true", help="skip the element-gather legs")
+    ap.add_argument("--grad-variant", choices=["exact", "literal"], default="exact",
+                    help="gradient form of the single-source leg: the exact derivative of the discrete J "
+                         "(default) or the paper-literal one of Sec. 4")
     ap.add_argument("--no-refined", action="store_true", help="skip the refined-mesh element-gather leg")
     ap.add_argument("--cpu-workers", type=int, default=min(8, os.cpu_count() or 1))
     ap.add_argument("--single-steps", type=int, default=2000,
