@@ -67,10 +67,11 @@ void dfree(ddfd_problem *p, void *ptr) {
     }
 }
 
-std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz) {
+std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int *n_full) {
   const int n = ps[0]->n;
   const bool f32 = ps[0]->fp32 != 0;
   const int gx = step_tiles_x(n, f32), gy = step_tiles_y(n, f32), gz = (n + kz - 1) / kz;
+  const int ty_rows = f32 ? StepTile<float>::TY : StepTile<double>::TY;
   // nodes of [z0, z1) inside [first, last]
   auto ov = [](int lo, int hi, int first, int last) {
     return (long long)std::max(0, std::min(hi, last + 1) - std::max(lo, first));
@@ -96,17 +97,38 @@ std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, in
     }
   }
   std::stable_sort(v.begin(), v.end(), [](const Slab &l, const Slab &r) { return l.cost > r.cost; });
-  std::vector<int> out;
+  // does tile (tx, ty) of chunk [z0, z1) hold a node strictly inside the FEM
+  // cube or a free node (the x tail column n - 1 is neither)
+  auto full = [&](const ddfd_problem *p, int tx, int ty, int z0, int z1) {
+    const int x0 = tx * STEP_TX, x1 = x0 + STEP_TX - 1, y0 = ty * ty_rows, y1 = y0 + ty_rows - 1;
+    auto box = [&](int lo, int hi) {
+      return lo <= hi && x0 <= hi && x1 >= lo && y0 <= hi && y1 >= lo && z0 <= hi && z1 - 1 >= lo;
+    };
+    return box(p->a + 1, p->b - 1) || box(p->f0, p->f0 + p->nf - 1);
+  };
+  std::vector<int> out, lean;
   out.reserve(v.size() * gx * gy);
-  for (const Slab &sl : v)
+  for (const Slab &sl : v) {
+    const ddfd_problem *p = ps[sl.q];
+    const int z0 = sl.zc * kz, z1 = std::min(z0 + kz, n);
     for (int ty = 0; ty < gy; ++ty)
-      for (int tx = 0; tx < gx; ++tx) out.push_back(pack_step_item(tx, ty, sl.zc, sl.q));
+      for (int tx = 0; tx < gx; ++tx) {
+        const int it = pack_step_item(tx, ty, sl.zc, sl.q);
+        if (!f32 || full(p, tx, ty, z0, z1))
+          out.push_back(it);
+        else
+          lean.push_back(it);
+      }
+  }
+  *n_full = (int)out.size();
+  out.insert(out.end(), lean.begin(), lean.end());
   return out;
 }
 
 int build_items(ddfd_problem *p) {
   if (p->n > 1024 || (p->n + p->kz - 1) / p->kz > 512) return DDFD_OK;  // beyond the item packing: grid order
-  const std::vector<int> it = step_item_order({p}, p->kz);
+  int n_full = 0;
+  const std::vector<int> it = step_item_order({p}, p->kz, &n_full);
   if (p->items) {
     dfree(p, p->items);
     p->items = nullptr;
@@ -116,7 +138,33 @@ int build_items(ddfd_problem *p) {
   if (st) return st;
   CK(cudaMemcpy(p->items, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice));
   p->items_kz = p->kz;
+  p->items_nfull = n_full;
   return DDFD_OK;
+}
+
+int enqueue_det_sources(ddfd_problem *p, cudaStream_t s) {
+  if (!p->rsrc) return 0;
+  launch_det_sources(p->res, p->Nt, p->n_det, p->n_src, p->n_unode, p->uptr, p->det_list, p->uij, p->n,
+                     p->tau * p->tau, 1.0 / (p->h * p->h * p->h), p->rsrc, s);
+  return 1;
+}
+
+int make_fork(StepFork *f) {
+  if (cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    drop_fork(f);
+    return DDFD_E_CUDA;
+  }
+  return DDFD_OK;
+}
+
+void drop_fork(StepFork *f) {
+  if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+  if (f->ev_join) cudaEventDestroy(f->ev_join);
+  if (f->side) cudaStreamDestroy(f->side);
+  *f = StepFork();
 }
 
 uint32_t faces_at(const ddfd_problem *p, int s, long long step) {
@@ -282,9 +330,8 @@ int enqueue_forward(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
                        (p->nsnap || p->fonly) ? nullptr
                                               : (T *)p->hist + ((size_t)s * (Nt + 1) + st + 1) * 3 * p->n_free);
       enqueue_ebe<T>(p, p->E[ic], false, sm, nk, p->X[ic]);
-      launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
+      *nk += launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm, &p->fork);
       enqueue_new_step<T>(p, p->X[ic], p->X[io], false, P, sm, nk);
-      ++*nk;
       std::swap(ic, io);
       if (p->hist_fem) {  // E^{st+1} on the FEM-updated nodes, for the literal gradient
         const size_t nfu = (size_t)(p->b - p->a - 1) * (p->b - p->a - 1) * (p->b - p->a - 1);
@@ -342,8 +389,7 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
           // (the trace is written again with the same values)
           set_forward_step(F, p, s, st, p->E[fc], p->E[fo], (T *)p->hist + (size_t)(st + 1 - n0) * 3 * p->n_free);
           enqueue_ebe<T>(p, p->E[fc], false, sm, nk);
-          launch_forward_step(single_launch(F, p->mE_halo[fc], p->mE_ctr[fo], p), sm);
-          ++*nk;
+          *nk += launch_forward_step(single_launch(F, p->mE_halo[fc], p->mE_ctr[fo], p), sm, &p->fork);
           std::swap(fc, fo);
         }
         hbase = (const T *)p->hist;
@@ -353,9 +399,8 @@ int enqueue_adjoint(ddfd_problem *p, cudaStream_t sm, int64_t *nk) {
       for (int k = n1; k >= n0 + 1; --k) {
         set_adjoint_step(P, p, s, k, p->Mu[ic], p->Mu[io], hbase + (size_t)(k - n0) * 3 * p->n_free, Nt);
         enqueue_ebe<T>(p, p->Mu[ic], true, sm, nk, p->XMu[ic]);
-        launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
+        *nk += launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm, &p->fork);
         enqueue_new_step<T>(p, p->XMu[ic], p->XMu[io], true, P, sm, nk);
-        ++*nk;
         if (p->hist_fem) {  // literal gradient: swap the Gauss-law term of step k (mu^k is still in Mu[ic])
           const size_t nfu = (size_t)(p->b - p->a - 1) * (p->b - p->a - 1) * (p->b - p->a - 1);
           launch_grad_literal<T>((const T *)p->hist_fem + ((size_t)s * (Nt + 1) + k) * 3 * nfu, (const T *)p->Mu[ic],
@@ -680,6 +725,7 @@ int adjoint_impl(ddfd_problem *p, const double *eobs, bool host) {
   }
   launch_residual(p->trace, e, p->z, p->Nt, p->n_det, p->n_src, p->tau, p->res, p->part, p->n_part, p->stream);
   ++p->launches;
+  p->launches += enqueue_det_sources(p, p->stream);
   p->state = ST_FORWARD;  // the accumulators are overwritten: no earlier gradient survives a failed run
   int st = run_sequence(p, true);
   if (st) return st;
@@ -818,7 +864,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
       p->err = "cudaEventCreate failed";
       return bail(DDFD_E_CUDA);
     }
-  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess || make_fork(&p->fork) ||
       prepare_step_kernels() != cudaSuccess || prepare_ebe_kernels() != cudaSuccess) {
     p->err = "stream creation or kernel attribute setup failed";
     return bail(DDFD_E_CUDA);
@@ -870,6 +916,25 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
       (st = dalloc_t(p, (size_t)std::max(p->n_det, 1), &p->det_list)) ||
       (p->fp32 && (st = dalloc_t(p, 2 * (size_t)p->n_free, &p->gpart))))
     return bail(st);
+  // detector nodes: the distinct top nodes that carry detectors, in node order
+  std::vector<int> dslot((size_t)p->n * p->n, -1), uptr(1, 0), uij;
+  {
+    std::vector<int> cnt((size_t)p->n * p->n, 0);
+    for (int d = 0; d < p->n_det; ++d) cnt[p->det_ij[2 * d] + (size_t)p->n * p->det_ij[2 * d + 1]]++;
+    for (int q = 0; q < p->n * p->n; ++q)
+      if (cnt[q]) {
+        dslot[q] = (int)uij.size() / 2;
+        uij.push_back(q % p->n);
+        uij.push_back(q / p->n);
+        uptr.push_back(uptr.back() + cnt[q]);
+      }
+    p->n_unode = (int)uij.size() / 2;
+  }
+  if (p->fp32 && !p->fonly && p->n_unode > 0 &&
+      ((st = dalloc_t(p, dslot.size(), &p->det_slot)) || (st = dalloc_t(p, uptr.size(), &p->uptr)) ||
+       (st = dalloc_t(p, uij.size(), &p->uij)) ||
+       (st = dalloc_t(p, (size_t)p->n_src * (p->Nt + 1) * p->n_unode * 3, &p->rsrc))))
+    return bail(st);
   if (p->nsnap && (st = dalloc(p, (size_t)p->n_src * p->nsnap * 2 * fbytes, &p->snap))) return bail(st);
   if (cfg->grad_variant == DDFD_GRAD_LITERAL) {
     const size_t nfu = (size_t)(p->b - p->a - 1) * (p->b - p->a - 1) * (p->b - p->a - 1);
@@ -912,6 +977,9 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   if (h2d(p->z, zt.data(), zt.size() * sizeof(double)) || h2d(p->det_node, dnode.data(), dnode.size() * sizeof(int)) ||
       h2d(p->det_ptr, dptr.data(), dptr.size() * sizeof(int)) ||
       h2d(p->det_list, dlist.data(), dlist.size() * sizeof(int)) ||
+      (p->det_slot && (h2d(p->det_slot, dslot.data(), dslot.size() * sizeof(int)) ||
+                       h2d(p->uptr, uptr.data(), uptr.size() * sizeof(int)) ||
+                       h2d(p->uij, uij.data(), uij.size() * sizeof(int)))) ||
       (p->delay && h2d(p->delay, delay_host.data(), delay_host.size() * sizeof(double)))) {
     p->err = "table upload failed";
     return bail(DDFD_E_CUDA);
@@ -952,6 +1020,7 @@ void destroy_problem(ddfd_problem *p) {
     if (p->ev[q]) cudaEventDestroy(p->ev[q]);
   drop_graphs(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  drop_fork(&p->fork);
   delete p;
 }
 

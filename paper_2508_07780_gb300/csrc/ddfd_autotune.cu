@@ -42,6 +42,7 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
   const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
   cudaStream_t sm = p->stream;
   p->kz = kz;
+  if (int bs = build_items(p)) return bs;  // the trial runs the dispatch order (and split) of this kz
   for (int q = 0; q < 2; ++q) {
     CK(cudaMemsetAsync(p->E[q], 0, fbytes, sm));
     if (p->Mu[q]) CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, sm));
@@ -56,7 +57,7 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
     set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
                      p->fonly ? nullptr : (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
     enqueue_ebe<T>(p, p->E[ic], false, sm, &nk, p->X[ic]);
-    launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm);
+    nk += launch_forward_step(single_launch(P, p->mE_halo[ic], p->mE_ctr[io], p), sm, &p->fork);
     std::swap(ic, io);
   }
   ic = 1, io = 0;
@@ -64,14 +65,14 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
     set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io], (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free,
                      steps);
     enqueue_ebe<T>(p, p->Mu[ic], true, sm, &nk, p->XMu[ic]);
-    launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm);
+    nk += launch_adjoint_step(single_launch(P, p->mM_halo[ic], p->mM_ctr[io], p), sm, &p->fork);
     std::swap(ic, io);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(p->ev[1], sm));
   CK(cudaEventSynchronize(p->ev[1]));
   CK(cudaEventElapsedTime(ms, p->ev[0], p->ev[1]));
-  p->launches += 2 * steps + nk;
+  p->launches += nk;
   return DDFD_OK;
 }
 
@@ -81,6 +82,7 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
   const size_t slab = fbytes * b->m.size();
   cudaStream_t sm = b->stream;
   b->kz = kz;
+  if (int bs = build_batch_items(b)) return bs;  // the trial runs the dispatch orders of this kz
   for (int q = 0; q < 2; ++q) {
     BCK(cudaMemsetAsync(b->E[q], 0, slab, sm));
     if (b->Mu[q]) BCK(cudaMemsetAsync(b->Mu[q], 0, slab, sm));
@@ -100,7 +102,7 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
           set_forward_step(P, p, 0, st, p->E[ic], p->E[io],
                            p->fonly ? nullptr : (T *)p->hist + trial_hist_index(p, st) * 3 * p->n_free);
         },
-        sm, &nk);
+        sm, &nk, &b->items_all);
     std::swap(ic, io);
   }
   bool any_fonly = false;
@@ -113,7 +115,7 @@ int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
           set_adjoint_step(P, p, 0, k, p->Mu[ic], p->Mu[io],
                            (const T *)p->hist + trial_hist_index(p, k - 1) * 3 * p->n_free, steps);
         },
-        sm, &nk);
+        sm, &nk, &b->items_all);
     std::swap(ic, io);
   }
   BCK(cudaGetLastError());

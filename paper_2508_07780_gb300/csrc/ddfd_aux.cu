@@ -163,6 +163,40 @@ void launch_residual(const double *trace, const double *eobs, const double *z, i
   k_residual<<<n_part, RB, 0, s>>>(trace, eobs, z, n_steps, n_det, total, tau, res, part);
 }
 
+__global__ void k_det_sources(const double *res, long long rows, int n_det, int n_unode, const int *uptr,
+                              const int *ulist, const int *uij, int n, double tau2, double inv_h3, float *out) {
+  const long long total = rows * n_unode;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long row = q / n_unode;  // (source, step)
+    const int u = (int)(q - row * n_unode);
+    const int i = uij[2 * u], j = uij[2 * u + 1];
+    const double wx = (i == 0 || i == n - 1) ? 0.5 : 1.0;
+    const double wy = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+    const double sc = tau2 * inv_h3 / (wx * wy * 0.5);
+    const double *r = res + row * n_det * 3;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int qq = uptr[u]; qq < uptr[u + 1]; ++qq) {
+      const int d = ulist[qq];
+      acc[0] += r[3 * d + 0];
+      acc[1] += r[3 * d + 1];
+      acc[2] += r[3 * d + 2];
+    }
+    for (int c = 0; c < 3; ++c) out[3 * q + c] = (float)(sc * acc[c]);
+  }
+}
+
+void launch_det_sources(const double *res, int n_steps, int n_det, int n_src, int n_unode, const int *uptr,
+                        const int *ulist, const int *uij, int n, double tau2, double inv_h3, float *out,
+                        cudaStream_t s) {
+  const long long rows = (long long)n_src * (n_steps + 1);
+  const long long total = rows * n_unode;
+  if (total <= 0) return;
+  const long long want = (total + 255) / 256;
+  const int blocks = (int)(want < 4096 ? want : 4096);
+  k_det_sources<<<blocks, 256, 0, s>>>(res, rows, n_det, n_unode, uptr, ulist, uij, n, tau2, inv_h3, out);
+}
+
 // sum_f (eps - eps0)^2 into part[0..n_part), sum_f (sig - sig0)^2 into part[n_part..2 n_part)
 __global__ void k_regul(const double *coef, int n_free, double *part, int n_part, const double *mass) {
   double ae = 0.0, as = 0.0;

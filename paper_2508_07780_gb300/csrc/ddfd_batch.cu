@@ -23,12 +23,13 @@ std::vector<int> all_members(const ddfd_batch *b) {
 }
 
 int build_batch_items(ddfd_batch *b) {
-  for (std::vector<int *> *v : {&b->items_all, &b->items_ck}) {
-    for (int *t : *v) {
+  for (ItemTables *v : {&b->items_all, &b->items_ck}) {
+    for (int *t : v->d) {
       cudaFree(t);
       b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)t));
     }
-    v->clear();
+    v->d.clear();
+    v->n_full.clear();
   }
   b->items_kz = 0;
   if (b->n > 1024 || (b->n + b->kz - 1) / b->kz > 512) return DDFD_OK;  // beyond the item packing: grid order
@@ -36,20 +37,21 @@ int build_batch_items(ddfd_batch *b) {
   for (size_t i = 0; i < b->m.size(); ++i)
     if (b->m[i]->nsnap) ck.push_back((int)i);
   const std::vector<int> all = all_members(b);
-  const std::pair<const std::vector<int> *, std::vector<int *> *> lists[2] = {{&all, &b->items_all},
-                                                                             {&ck, &b->items_ck}};
+  const std::pair<const std::vector<int> *, ItemTables *> lists[2] = {{&all, &b->items_all}, {&ck, &b->items_ck}};
   for (const auto &lt : lists)
     for (size_t g0 = 0; g0 < lt.first->size(); g0 += BATCH_MAX) {
       std::vector<const ddfd_problem *> ps;
       for (size_t g = g0; g < std::min(g0 + BATCH_MAX, lt.first->size()); ++g) ps.push_back(b->m[(*lt.first)[g]]);
-      const std::vector<int> it = step_item_order(ps, b->kz);
+      int n_full = 0;
+      const std::vector<int> it = step_item_order(ps, b->kz, &n_full);
       int *d = nullptr;
       if (cudaMalloc((void **)&d, it.size() * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, DDFD_E_OOM, "cudaMalloc of a dispatch table failed");
       }
       b->allocs.push_back(d);
-      lt.second->push_back(d);
+      lt.second->d.push_back(d);
+      lt.second->n_full.push_back(n_full);
       BCK(cudaMemcpy(d, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
   b->items_kz = b->kz;
@@ -299,6 +301,7 @@ int batch_adjoint_impl(ddfd_batch *b, const double *const *eobs, bool host) {
     }
     launch_residual(p->trace, e, p->z, p->Nt, p->n_det, 1, p->tau, p->res, p->part, p->n_part, b->stream);
     ++b->launches;
+    b->launches += enqueue_det_sources(p, b->stream);
   }
   for (ddfd_problem *p : b->m) p->state = ST_FORWARD;
   int st = run_batch_sequence(b, true);
@@ -323,6 +326,7 @@ void destroy_batch(ddfd_batch *b) {
     if (b->ev[q]) cudaEventDestroy(b->ev[q]);
   drop_batch_graphs(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  drop_fork(&b->fork);
   delete b;
 }
 
@@ -391,7 +395,7 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
   };
   for (int q = 0; q < 4; ++q)
     if (cudaEventCreate(&b->ev[q]) != cudaSuccess) return bail(DDFD_E_CUDA, "cudaEventCreate failed");
-  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess || make_fork(&b->fork))
     return bail(DDFD_E_CUDA, "stream creation failed");
   const size_t slab = 3 * (size_t)b->cs * b->esz * count;
   bool all_fonly = true;

@@ -37,6 +37,18 @@ struct FieldMaps {
   CUtensorMap E_halo[2], E_ctr[2], M_halo[2], M_ctr[2], S, Q;
 };
 
+// Dispatch orders of a batch's step launches over one member list: per group
+// of BATCH_MAX members, the device table and its count of leading items for
+// the full FP32 step kernel.
+struct ItemTables {
+  std::vector<int *> d;
+  std::vector<int> n_full;
+};
+
+// Creates (destroys) the side stream and the two events of a StepFork.
+int make_fork(ddfd::StepFork *f);
+void drop_fork(ddfd::StepFork *f);
+
 }  // namespace host
 }  // namespace ddfd
 
@@ -85,6 +97,12 @@ struct ddfd_problem {
   double *coef = nullptr, *coef_stage = nullptr, *z = nullptr, *part = nullptr, *scal = nullptr;
   double *gout = nullptr, *delay = nullptr, *pw[2] = {nullptr, nullptr};
   int *det_node = nullptr, *det_ptr = nullptr, *det_list = nullptr, *flag = nullptr;
+  // FP32 adjoint sources per detector node (distinct top nodes with detectors):
+  // slot of each top node (-1: none), CSR of its detectors into det_list, its
+  // (i, j), and the scaled residual sums [n_src][Nt+1][n_unode][3]
+  int *det_slot = nullptr, *uptr = nullptr, *uij = nullptr;
+  int n_unode = 0;
+  float *rsrc = nullptr;
   int *errflag = nullptr;     // kernel-side error bits (bounded waits)
 
   // TMA descriptors: [buffer] halo-box (current level) and centre-box (old level)
@@ -100,6 +118,8 @@ struct ddfd_problem {
   int kz = 16;
   int *items = nullptr;       // dispatch order of the step launches (heaviest tiles first), for items_kz
   int items_kz = 0;
+  int items_nfull = 0;        // FP32: leading items for the full step kernel, the rest lean
+  ddfd::StepFork fork;        // side stream of the lean step launches
   int n_part = 256;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double fwd_ms = 0.0, adj_ms = 0.0;
@@ -143,8 +163,9 @@ struct ddfd_batch {
   // dispatch orders of the batched step launches (heaviest tiles first), for
   // items_kz: one table per group of BATCH_MAX members of all members, and of
   // the checkpointing members (their replays)
-  std::vector<int *> items_all, items_ck;
+  ddfd::host::ItemTables items_all, items_ck;
   int items_kz = 0;
+  ddfd::StepFork fork;        // side stream of the lean step launches
   // conjugate gradient work space (FP64, free nodes): 14 vectors, partial
   // sums, the 6 reduced scalars
   double *cg = nullptr;
@@ -192,8 +213,10 @@ void dfree(ddfd_problem *p, void *ptr);
 // order) with z depth kz: whole z slabs (one problem's tiles of one z chunk,
 // in grid order within the slab) sorted by an estimate of their work, heaviest
 // first (node count, plus twice the FEM rows and once the free nodes they
-// hold), ties in grid order.
-std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz);
+// hold), ties in grid order.  FP32: the tiles that hold a node strictly inside
+// the FEM cube or a free node come first (their count in *n_full), then the
+// finite-difference-only tiles, each part in that order; FP64: *n_full = all.
+std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int *n_full);
 // (Re)builds p->items for p->kz.
 int build_items(ddfd_problem *p);
 // (Re)builds the batch's tables for b->kz.
@@ -205,6 +228,10 @@ int dalloc_t(ddfd_problem *p, size_t count, X **out) {
   *out = (X *)v;
   return st;
 }
+
+// FP32: the adjoint's detector sources from p->res (after launch_residual);
+// returns the number of kernels launched (0 or 1).
+int enqueue_det_sources(ddfd_problem *p, cudaStream_t s);
 
 // Absorbing faces of source s at step `step` (the top face only after its source phase).
 uint32_t faces_at(const ddfd_problem *p, int s, long long step);
@@ -267,6 +294,7 @@ StepParams<T> base_params(const ddfd_problem *p) {
   P.det_node = p->det_node;
   P.det_ptr = p->det_ptr;
   P.det_list = p->det_list;
+  P.det_slot = p->det_slot;
   P.inv_h3 = 1.0 / (p->h * p->h * p->h);
   P.tau2 = p->tau * p->tau;
   P.n_free = p->n_free;
@@ -307,6 +335,7 @@ void set_adjoint_step(StepParams<T> &P, const ddfd_problem *p, int s, int k, con
   P.abs_now = faces_at(p, s, k - 1);
   P.abs_next = faces_at(p, s, k + 1);
   P.res_k = p->res + ((size_t)s * (p->Nt + 1) + k) * p->n_det * 3;
+  P.src_k = p->rsrc ? p->rsrc + ((size_t)s * (p->Nt + 1) + k) * p->n_unode * 3 : nullptr;
   P.hist_r = hist_r;
 }
 
@@ -321,6 +350,7 @@ StepLaunch<T, 1> single_launch(const StepParams<T> &P, const CUtensorMap &cur, c
   L.nprob = 1;
   L.zchunks = (p->n + P.kz - 1) / P.kz;
   L.items = P.kz == p->items_kz ? p->items : nullptr;
+  L.n_full = p->items_nfull;
   L.p[0] = P;
   return L;
 }
@@ -408,7 +438,7 @@ void enqueue_new_step(ddfd_problem *p, const void *cur, void *old, bool adj, con
 template <typename T, typename Fill>
 void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const CUtensorMap &cur,
                    const CUtensorMap &old, Fill fill, cudaStream_t sm, int64_t *nk,
-                   const std::vector<int *> *tables = nullptr) {
+                   const ItemTables *tables = nullptr) {
   for (size_t g0 = 0; g0 < idx.size(); g0 += BATCH_MAX) {
     StepLaunch<T, BATCH_MAX> L;
     std::memset(&L, 0, sizeof(L));
@@ -418,8 +448,10 @@ void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const C
     L.q = b->maps.Q;
     L.nprob = (int)std::min<size_t>(BATCH_MAX, idx.size() - g0);
     L.zchunks = (b->n + b->kz - 1) / b->kz;
-    L.items = (tables && b->kz == b->items_kz && g0 / BATCH_MAX < tables->size()) ? (*tables)[g0 / BATCH_MAX]
-                                                                                  : nullptr;
+    const size_t gi = g0 / BATCH_MAX;
+    const bool tab = tables && b->kz == b->items_kz && gi < tables->d.size();
+    L.items = tab ? tables->d[gi] : nullptr;
+    L.n_full = tab ? tables->n_full[gi] : 0;
     for (int g = 0; g < L.nprob; ++g) {
       ddfd_problem *p = b->m[idx[g0 + g]];
       StepParams<T> P = base_params<T>(p);
@@ -430,11 +462,7 @@ void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const C
       fill(P, p);
       L.p[g] = P;
     }
-    if (adj)
-      launch_adjoint_step(L, sm);
-    else
-      launch_forward_step(L, sm);
-    ++*nk;
+    *nk += adj ? launch_adjoint_step(L, sm, &b->fork) : launch_forward_step(L, sm, &b->fork);
   }
 }
 

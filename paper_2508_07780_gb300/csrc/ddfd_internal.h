@@ -86,6 +86,8 @@ struct StepParams {
   const int *det_ptr;    // adjoint: CSR over top-plane nodes (i + n j; n^2 + 1)
   const int *det_list;
   const double *res_k;   // adjoint: residual tau z (E^k - Eobs^k), [n_det][3]
+  const int *det_slot;   // FP32 adjoint: detector-node index u of each top node (i + n j), or -1
+  const float *src_k;    // FP32 adjoint: step k's detector sources, [u][3] (k_det_sources)
   double inv_h3;         // 1 / h^3
   double tau2;           // tau^2
   // history of E on the free nodes
@@ -122,11 +124,25 @@ struct StepLaunch {
   int nprob;
   int zchunks;
   // optional dispatch order: block b of a 1-D grid takes the tile items[b],
-  // packed by pack_step_item (heaviest tiles first, so that the last wave is
-  // made of light ones); NULL: a 3-D grid of (tile x, tile y, z chunk +
-  // zchunks x problem)
+  // packed by pack_step_item (whole z slabs, heaviest first, so that the last
+  // wave is made of light ones); NULL: a 3-D grid of (tile x, tile y, z chunk
+  // + zchunks x problem)
   const int *items;
+  // FP32 with a dispatch order: items[0, n_full) hold FEM-cube or free nodes
+  // and run on the full step kernel; the rest are finite-difference tiles
+  // only and run on the lean one (concurrently, on StepFork's side stream)
+  int n_full;
   StepParams<T> p[NB];
+};
+
+// Side stream and fork/join events of a step whose FP32 tiles are split
+// between the full and the lean kernel: the lean launch runs on `side`,
+// ordered after the work queued before the step (ev_fork) and before the work
+// queued after it (ev_join), so that both kernels of one step run side by side,
+// also inside a captured graph.
+struct StepFork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Tiles per axis of the step kernels' launch grid (FP32: 32 x 16 tiles,
@@ -143,10 +159,12 @@ __host__ __device__ inline int pack_step_item(int tx, int ty, int zc, int prob) 
 // before any launch or capture).
 cudaError_t prepare_step_kernels();
 
+// One step: returns the number of kernels launched (1, or 2 when the FP32
+// tiles are split; the lean launch goes to fk->side when fk has one, else to s).
 template <typename T, int NB>
-void launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s);
+int launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s, const StepFork *fk = nullptr);
 template <typename T, int NB>
-void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s);
+int launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s, const StepFork *fk = nullptr);
 
 // Element-by-element FEM apply over an explicit tetrahedral mesh, staged in
 // shared memory block by block.  A block holds up to EBE_RB rows (nearby
@@ -305,6 +323,15 @@ void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, do
                          int *flag, cudaStream_t s);
 // residual r = tau z (trace - eobs) for n >= 1 (r[0] = 0); partial sums of
 // z |trace - eobs|^2 per block into part[] (deterministic two-pass sum).
+// Adjoint sources of the FP32 step kernel, per detector node u (the distinct
+// top nodes that carry detectors) and step: tau^2 / (h^3 m_u) times the sum of
+// the residuals of u's detectors, summed in FP64 in detector order and rounded
+// to FP32 (m_u: lumped mass of the top node, h^3 w_x w_y / 2).
+// res: [n_src][n_steps+1][n_det][3]; out: [n_src][n_steps+1][n_unode][3];
+// uptr/ulist: CSR of each node's detectors; uij: (i, j) of each node.
+void launch_det_sources(const double *res, int n_steps, int n_det, int n_src, int n_unode, const int *uptr,
+                        const int *ulist, const int *uij, int n, double tau2, double inv_h3, float *out,
+                        cudaStream_t s);
 void launch_residual(const double *trace, const double *eobs, const double *z, int n_steps,
                      int n_det, int n_src, double tau, double *res, double *part, int n_part,
                      cudaStream_t s);

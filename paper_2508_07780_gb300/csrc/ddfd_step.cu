@@ -145,9 +145,13 @@ struct Stage {
 };
 
 // FP32 stage: 32 x 16 tile, each computing thread owns two x-adjacent nodes
-// (so every staged row is read as float2 pairs); 5 stages, 2 CTAs per SM.
+// (so every staged row is read as float2 pairs); 5 stages.  Full kernel
+// (tiles with FEM-cube or free nodes): the current and previous levels, s and
+// (q1, q2), 2 CTAs per SM.  Lean kernel (finite-difference tiles only): the
+// two levels alone, 74 KB, 3 CTAs per SM.
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
-struct PairStage {
+template <bool LEAN>
+struct PairStageT {
   static constexpr int TX = STEP_TX;
   static constexpr int TY = StepTile<float>::TY;
   static constexpr int HX = 4;                     // x halo: one 16-byte unit
@@ -157,8 +161,8 @@ struct PairStage {
   static constexpr int TXY = TX * TY;
   static constexpr int E_BYTES = 3 * RE * 4;
   static constexpr int O_BYTES = 3 * TXY * 4;
-  static constexpr int S_BYTES = RE * 4;
-  static constexpr int Q_BYTES = 2 * TXY * 4;
+  static constexpr int S_BYTES = LEAN ? 0 : RE * 4;
+  static constexpr int Q_BYTES = LEAN ? 0 : 2 * TXY * 4;
   static constexpr int E_OFF = 0;
   static constexpr int O_OFF = round128(E_BYTES);
   static constexpr int S_OFF = O_OFF + round128(O_BYTES);
@@ -168,6 +172,7 @@ struct PairStage {
   // stages, full and empty barriers, release counters, two ints, alignment
   static constexpr int SMEM = RING * BYTES + 2 * RING * 8 + RING * 4 + 8 + 128;
 };
+using PairStage = PairStageT<false>;
 
 // Warp roles: warps 0..7 compute, warp 8 stages planes.
 constexpr int STEP_CONSUMERS = 256;
@@ -663,17 +668,21 @@ __device__ __forceinline__ const float *S0f(const unsigned char *stage) {
 // stages the plane that reuses it (per-slot release counters in shared
 // memory); 8 warps per CTA and 2 CTAs per SM leave up to 128 registers per
 // thread.  The adjoint CTA has a producer warp (warp 8) fed by per-slot
-// "empty" mbarriers; it measured faster there (80 vs 84 us per 201^3 step).
-template <bool ADJ>
+// "empty" mbarriers; it measured faster there (full kernel: 80 vs 84 us per
+// 201^3 step; lean kernel: 54.6 vs 56.9 us).  The lean kernels (no FEM or
+// free nodes) run 3 CTAs per SM (forward: 80 registers a thread, adjoint: 72).
+template <bool ADJ, bool LEAN>
 struct PairMode {
   static constexpr bool PRODUCER_WARP = ADJ;
   static constexpr int THREADS = PRODUCER_WARP ? STEP_THREADS : STEP_CONSUMERS;
+  static constexpr int MIN_CTAS = LEAN ? 3 : 2;
 };
 
-template <bool ADJ, int NB>
-__global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const __grid_constant__ StepLaunch<float, NB> L) {
-  constexpr bool PW = PairMode<ADJ>::PRODUCER_WARP;
-  using S = PairStage;
+template <bool ADJ, int NB, bool LEAN>
+__global__ void __launch_bounds__(PairMode<ADJ, LEAN>::THREADS, PairMode<ADJ, LEAN>::MIN_CTAS)
+    k_step_pair(const __grid_constant__ StepLaunch<float, NB> L) {
+  constexpr bool PW = PairMode<ADJ, LEAN>::PRODUCER_WARP;
+  using S = PairStageT<LEAN>;
   constexpr int RE = S::RE, BW = S::BXW, TXY = S::TXY;
   const CtaTile ct = cta_tile(L);
   const int zc = ct.zc, zchunks = L.zchunks;
@@ -702,7 +711,8 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
   const int k0 = zc * P.kz;
   if (k0 >= n) return;  // uniform per CTA
   const int k1 = min(k0 + P.kz, n);
-  const bool tile_fem = x0 <= P.b - 1 && x0 + S::TX - 1 >= P.a + 1 && y0 <= P.b - 1 && y0 + S::TY - 1 >= P.a + 1;
+  const bool tile_fem =
+      !LEAN && x0 <= P.b - 1 && x0 + S::TX - 1 >= P.a + 1 && y0 <= P.b - 1 && y0 + S::TY - 1 >= P.a + 1;
   const int nplanes = k1 - k0 + 2;
 
   if (tid == 0) {
@@ -778,20 +788,12 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
       }
     }
     if (ADJ && k == n - 1 && P.n_det > 0) {
-      const int q0 = P.det_ptr[xn + n * y], q1 = P.det_ptr[xn + n * y + 1];
-      if (q1 > q0) {
-        const double wx = (xn == 0 || xn == n - 1) ? 0.5 : 1.0;
-        const double wy = (y == 0 || y == n - 1) ? 0.5 : 1.0;
-        const double sc = P.tau2 * P.inv_h3 / (wx * wy * 0.5);
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int qq = q0; qq < q1; ++qq) {
-          const int d = P.det_list[qq];
-          acc[0] += P.res_k[3 * d + 0];
-          acc[1] += P.res_k[3 * d + 1];
-          acc[2] += P.res_k[3 * d + 2];
-        }
+      // detector residual sources of this node at step k, summed and scaled
+      // by k_det_sources
+      const int u = P.det_slot[xn + n * y];
+      if (u >= 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) R[c] += (float)(sc * acc[c]);
+        for (int c = 0; c < 3; ++c) R[c] += P.src_k[3 * u + c];
       }
     }
   };
@@ -860,8 +862,9 @@ __global__ void __launch_bounds__(PairMode<ADJ>::THREADS, 2) k_step_pair(const _
       }
       float2 A2 = kOne, B2 = kZero, C2 = kOne;
       float2 SX[3] = {kZero, kZero, kZero};
-      const bool fre_a = free_a && kfree, fre_b = free_b && kfree;
-      const bool fem_pair = colfem && kfem;
+      // (a lean launch carries no tile with FEM-cube or free nodes)
+      const bool fre_a = !LEAN && free_a && kfree, fre_b = !LEAN && free_b && kfree;
+      const bool fem_pair = !LEAN && colfem && kfem;
       if (fem_pair) {
         const float *Q0 = (const float *)(b0 + S::Q_OFF);
         A2 = ld2(Q0 + oi);
@@ -1068,7 +1071,11 @@ static cudaError_t set_smem_f64() {
 }
 template <bool ADJ, int NB>
 static cudaError_t set_smem_f32() {
-  return cudaFuncSetAttribute(k_step_pair<ADJ, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairStage::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_step_pair<ADJ, NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PairStageT<false>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_step_pair<ADJ, NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              PairStageT<true>::SMEM);
 }
 
 cudaError_t prepare_step_kernels() {
@@ -1096,26 +1103,53 @@ static dim3 step_grid(const StepLaunch<T, NB> &L) {
 }
 
 template <bool ADJ, int NB>
-static void launch_step(const StepLaunch<double, NB> &L, cudaStream_t s) {
+static int launch_step(const StepLaunch<double, NB> &L, cudaStream_t s, const StepFork *) {
   k_step<double, ADJ, NB><<<step_grid(L), STEP_THREADS, Stage<double>::SMEM, s>>>(L);
+  return 1;
 }
+// FP32: the dispatch order's FEM/free tiles on the full kernel, the others on
+// the lean one, side by side when fk provides a side stream.
 template <bool ADJ, int NB>
-static void launch_step(const StepLaunch<float, NB> &L, cudaStream_t s) {
-  k_step_pair<ADJ, NB><<<step_grid(L), PairMode<ADJ>::THREADS, PairStage::SMEM, s>>>(L);
+static int launch_step(const StepLaunch<float, NB> &L, cudaStream_t s, const StepFork *fk) {
+  using Full = PairMode<ADJ, false>;
+  using Lean = PairMode<ADJ, true>;
+  const dim3 g = step_grid(L);
+  if (!L.items || L.n_full >= (int)g.x) {
+    k_step_pair<ADJ, NB, false><<<g, Full::THREADS, PairStageT<false>::SMEM, s>>>(L);
+    return 1;
+  }
+  StepLaunch<float, NB> F = L;
+  F.items = L.items + L.n_full;
+  const unsigned n_lean = g.x - (unsigned)L.n_full;
+  if (L.n_full == 0) {
+    k_step_pair<ADJ, NB, true><<<n_lean, Lean::THREADS, PairStageT<true>::SMEM, s>>>(F);
+    return 1;
+  }
+  cudaStream_t s2 = s;
+  if (fk && fk->side && cudaEventRecord(fk->ev_fork, s) == cudaSuccess &&
+      cudaStreamWaitEvent(fk->side, fk->ev_fork, 0) == cudaSuccess)
+    s2 = fk->side;
+  k_step_pair<ADJ, NB, false><<<(unsigned)L.n_full, Full::THREADS, PairStageT<false>::SMEM, s>>>(L);
+  k_step_pair<ADJ, NB, true><<<n_lean, Lean::THREADS, PairStageT<true>::SMEM, s2>>>(F);
+  if (s2 != s) {
+    // a failure here is left in the runtime's last error for the caller's check
+    if (cudaEventRecord(fk->ev_join, s2) == cudaSuccess) cudaStreamWaitEvent(s, fk->ev_join, 0);
+  }
+  return 2;
 }
 
 template <typename T, int NB>
-void launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
-  launch_step<false, NB>(L, s);
+int launch_forward_step(const StepLaunch<T, NB> &L, cudaStream_t s, const StepFork *fk) {
+  return launch_step<false, NB>(L, s, fk);
 }
 template <typename T, int NB>
-void launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s) {
-  launch_step<true, NB>(L, s);
+int launch_adjoint_step(const StepLaunch<T, NB> &L, cudaStream_t s, const StepFork *fk) {
+  return launch_step<true, NB>(L, s, fk);
 }
 
-#define DDFD_STEP_INST(T, NB)                                                      \
-  template void launch_forward_step<T, NB>(const StepLaunch<T, NB> &, cudaStream_t); \
-  template void launch_adjoint_step<T, NB>(const StepLaunch<T, NB> &, cudaStream_t);
+#define DDFD_STEP_INST(T, NB)                                                                           \
+  template int launch_forward_step<T, NB>(const StepLaunch<T, NB> &, cudaStream_t, const StepFork *); \
+  template int launch_adjoint_step<T, NB>(const StepLaunch<T, NB> &, cudaStream_t, const StepFork *);
 DDFD_STEP_INST(float, 1)
 DDFD_STEP_INST(double, 1)
 DDFD_STEP_INST(float, BATCH_MAX)
