@@ -67,77 +67,102 @@ void dfree(ddfd_problem *p, void *ptr) {
     }
 }
 
-std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int *n_full) {
+std::vector<uint32_t> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int kz_lean,
+                                      int *n_full) {
   const int n = ps[0]->n;
   const bool f32 = ps[0]->fp32 != 0;
-  const int gx = step_tiles_x(n, f32), gy = step_tiles_y(n, f32), gz = (n + kz - 1) / kz;
+  const int gx = step_tiles_x(n, f32), gy = step_tiles_y(n, f32);
   const int ty_rows = f32 ? StepTile<float>::TY : StepTile<double>::TY;
-  // nodes of [z0, z1) inside [first, last]
-  auto ov = [](int lo, int hi, int first, int last) {
-    return (long long)std::max(0, std::min(hi, last + 1) - std::max(lo, first));
-  };
-  // whole z slabs (one problem's tiles of one z chunk) are ordered, so that
-  // tiles that share halos still run side by side
+  // A slab is one problem's z range [z0, z1) over a set of its tile columns:
+  // the items of a slab are dispatched together, so that tiles that share
+  // halos run side by side.
   struct Slab {
     long long cost;
-    int q, zc;
+    int q, z0, z1;
+    bool fem;  // FP32: the columns that meet the FEM cube or the free box
   };
-  std::vector<Slab> v;
+  auto ov = [](int lo, int hi, int first, int last) {  // nodes of [lo, hi) inside [first, last]
+    return (long long)std::max(0, std::min(hi, last + 1) - std::max(lo, first));
+  };
+  // does tile column (tx, ty) meet [lo, hi]^2 in x and y (the x tail column
+  // n - 1 is never a FEM or free node)
+  auto meets = [&](int tx, int ty, int lo, int hi) {
+    const int x0 = tx * STEP_TX, y0 = ty * ty_rows;
+    return lo <= hi && x0 <= hi && x0 + STEP_TX - 1 >= lo && y0 <= hi && y0 + ty_rows - 1 >= lo;
+  };
+  std::vector<Slab> full, lean;
+  std::vector<std::vector<char>> colfem(ps.size());
   for (size_t q = 0; q < ps.size(); ++q) {
     const ddfd_problem *p = ps[q];
     const long long fem2 = (long long)(p->b - p->a - 1) * (p->b - p->a - 1), fre2 = (long long)p->nf * p->nf;
-    for (int zc = 0; zc < gz; ++zc) {
-      const int z0 = zc * kz, z1 = std::min(z0 + kz, n);
-      Slab sl;
-      sl.cost = (long long)n * n * (z1 - z0) + 2 * fem2 * ov(z0, z1, p->a + 1, p->b - 1) +
-                fre2 * ov(z0, z1, p->f0, p->f0 + p->nf - 1);
-      sl.q = (int)q;
-      sl.zc = zc;
-      v.push_back(sl);
-    }
-  }
-  std::stable_sort(v.begin(), v.end(), [](const Slab &l, const Slab &r) { return l.cost > r.cost; });
-  // does tile (tx, ty) of chunk [z0, z1) hold a node strictly inside the FEM
-  // cube or a free node (the x tail column n - 1 is neither)
-  auto full = [&](const ddfd_problem *p, int tx, int ty, int z0, int z1) {
-    const int x0 = tx * STEP_TX, x1 = x0 + STEP_TX - 1, y0 = ty * ty_rows, y1 = y0 + ty_rows - 1;
-    auto box = [&](int lo, int hi) {
-      return lo <= hi && x0 <= hi && x1 >= lo && y0 <= hi && y1 >= lo && z0 <= hi && z1 - 1 >= lo;
+    auto cost = [&](int z0, int z1) {
+      return (long long)n * n * (z1 - z0) + 2 * fem2 * ov(z0, z1, p->a + 1, p->b - 1) +
+             fre2 * ov(z0, z1, p->f0, p->f0 + p->nf - 1);
     };
-    return box(p->a + 1, p->b - 1) || box(p->f0, p->f0 + p->nf - 1);
-  };
-  std::vector<int> out, lean;
-  out.reserve(v.size() * gx * gy);
-  for (const Slab &sl : v) {
-    const ddfd_problem *p = ps[sl.q];
-    const int z0 = sl.zc * kz, z1 = std::min(z0 + kz, n);
-    for (int ty = 0; ty < gy; ++ty)
-      for (int tx = 0; tx < gx; ++tx) {
-        const int it = pack_step_item(tx, ty, sl.zc, sl.q);
-        if (!f32 || full(p, tx, ty, z0, z1))
-          out.push_back(it);
-        else
-          lean.push_back(it);
-      }
+    colfem[q].assign((size_t)gx * gy, 0);
+    // FP32: the z range [zf0, zf1) of the FEM columns that holds FEM-cube or
+    // free nodes (the hull of the two boxes' z ranges)
+    int zf0 = n, zf1 = 0;
+    if (f32) {
+      for (int ty = 0; ty < gy; ++ty)
+        for (int tx = 0; tx < gx; ++tx) {
+          const bool c1 = meets(tx, ty, p->a + 1, p->b - 1), c2 = p->nf > 0 && meets(tx, ty, p->f0, p->f0 + p->nf - 1);
+          colfem[q][(size_t)tx + (size_t)gx * ty] = c1 || c2;
+          if (c1) zf0 = std::min(zf0, p->a + 1), zf1 = std::max(zf1, p->b);
+          if (c2) zf0 = std::min(zf0, p->f0), zf1 = std::max(zf1, p->f0 + p->nf);
+        }
+    }
+    if (zf0 >= zf1) {  // FP64, or no FEM columns: every column in chunks of kz on the full kernel
+      for (int z0 = 0; z0 < n; z0 += kz) full.push_back({cost(z0, std::min(z0 + kz, n)), (int)q, z0, std::min(z0 + kz, n), false});
+      continue;
+    }
+    // FEM columns: [zf0, zf1) in chunks of kz on the full kernel, the rest in
+    // chunks of kz_lean on the lean one; the other columns: all lean
+    for (int z0 = zf0; z0 < zf1; z0 += kz) full.push_back({cost(z0, std::min(z0 + kz, zf1)), (int)q, z0, std::min(z0 + kz, zf1), true});
+    for (int z0 = 0; z0 < zf0; z0 += kz_lean) lean.push_back({cost(z0, std::min(z0 + kz_lean, zf0)), (int)q, z0, std::min(z0 + kz_lean, zf0), true});
+    for (int z0 = zf1; z0 < n; z0 += kz_lean) lean.push_back({cost(z0, std::min(z0 + kz_lean, n)), (int)q, z0, std::min(z0 + kz_lean, n), true});
+    for (int z0 = 0; z0 < n; z0 += kz_lean) lean.push_back({cost(z0, std::min(z0 + kz_lean, n)), (int)q, z0, std::min(z0 + kz_lean, n), false});
   }
+  auto heavy_first = [](const Slab &l, const Slab &r) { return l.cost > r.cost; };
+  std::stable_sort(full.begin(), full.end(), heavy_first);
+  std::stable_sort(lean.begin(), lean.end(), heavy_first);
+  std::vector<uint32_t> out;
+  auto emit = [&](const std::vector<Slab> &v, bool all_cols_full) {
+    for (const Slab &sl : v)
+      for (int ty = 0; ty < gy; ++ty)
+        for (int tx = 0; tx < gx; ++tx) {
+          const bool cf = colfem[sl.q][(size_t)tx + (size_t)gx * ty] != 0;
+          // full slabs of FP64 / FEM-free problems hold every column; the
+          // others only the FEM columns (fem) or only the rest (!fem)
+          if (!(all_cols_full && !sl.fem) && cf != sl.fem) continue;
+          out.push_back(pack_step_item(tx, ty, sl.z0, sl.z1 - sl.z0, sl.q));
+        }
+  };
+  emit(full, true);
   *n_full = (int)out.size();
-  out.insert(out.end(), lean.begin(), lean.end());
+  emit(lean, false);
   return out;
 }
 
+// Dispatch items fit the packing (n < 1024, z ranges of at most ITEM_MAX_NZ planes).
+static bool items_fit(int n, int kz, int kz_lean) {
+  return n <= 1024 && kz >= 1 && kz <= ITEM_MAX_NZ && kz_lean >= 1 && kz_lean <= ITEM_MAX_NZ;
+}
+
 int build_items(ddfd_problem *p) {
-  if (p->n > 1024 || (p->n + p->kz - 1) / p->kz > 512) return DDFD_OK;  // beyond the item packing: grid order
-  int n_full = 0;
-  const std::vector<int> it = step_item_order({p}, p->kz, &n_full);
   if (p->items) {
     dfree(p, p->items);
     p->items = nullptr;
     p->items_kz = 0;
   }
+  if (!items_fit(p->n, p->kz, p->kz_lean)) return DDFD_OK;  // beyond the item packing: grid order
+  int n_full = 0;
+  const std::vector<uint32_t> it = step_item_order({p}, p->kz, p->kz_lean, &n_full);
   int st = dalloc_t(p, it.size(), &p->items);
   if (st) return st;
-  CK(cudaMemcpy(p->items, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->items, it.data(), it.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   p->items_kz = p->kz;
+  p->n_items = (int)it.size();
   p->items_nfull = n_full;
   return DDFD_OK;
 }
@@ -853,6 +878,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   p->esz = p->fp32 ? 4 : 8;
   p->stream = (cudaStream_t)cfg->stream;
   p->kz = cfg->tile_kz ? cfg->tile_kz : (p->n >= 128 ? 16 : 8);
+  p->kz_lean = p->n >= 128 ? 16 : 8;
 
   auto bail = [&](int code) {
     g_create_err = p->err;

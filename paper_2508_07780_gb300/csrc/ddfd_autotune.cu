@@ -1,7 +1,8 @@
 // The tile autotuner (ddfd_autotune, ddfd_batch_autotune): times a few
 // forward and adjoint step launches per candidate z depth of the thread-block
-// tile with CUDA events and keeps the fastest.  A GPU tuning aid; the paper
-// has no counterpart.
+// tiles with CUDA events and keeps the fastest: first the full kernel's depth
+// (the lean one's fixed), then, in FP32, the lean kernel's depth.  A GPU
+// tuning aid; the paper has no counterpart.
 #include "ddfd_host.h"
 
 using namespace ddfd;
@@ -11,24 +12,34 @@ namespace {
 
 const int kTileKz[] = {4, 6, 8, 12, 16, 24, 32};
 
-// Runs trial(kz, &ms) for every candidate z depth (after one untimed warm-up
-// trial) and returns the fastest in *best.
+// Runs trial(kz, kz_lean, &ms) for every candidate z depth of one kernel
+// (after one untimed warm-up trial), the other's held, and returns the
+// fastest in *kz (lean = false) or *kz_lean (lean = true).
 template <typename Trial>
-int autotune_kz(int n, Trial trial, int *best) {
+int autotune_one(int n, bool lean, Trial trial, int *kz, int *kz_lean) {
   int st;
   float ms = 0.0f;
-  if ((st = trial(kTileKz[0] <= n ? kTileKz[0] : n, &ms))) return st;
+  auto run = [&](int c) { return lean ? trial(*kz, c, &ms) : trial(c, *kz_lean, &ms); };
+  if ((st = run(kTileKz[0] <= n ? kTileKz[0] : n))) return st;
   float best_ms = 3.4e38f;
-  *best = 0;
-  for (int kz : kTileKz) {
-    if (kz > n) break;
-    if ((st = trial(kz, &ms))) return st;
+  int best = lean ? *kz_lean : *kz;
+  for (int c : kTileKz) {
+    if (c > n) break;
+    if ((st = run(c))) return st;
     if (ms < best_ms) {
       best_ms = ms;
-      *best = kz;
+      best = c;
     }
   }
+  (lean ? *kz_lean : *kz) = best;
   return DDFD_OK;
+}
+
+template <typename Trial>
+int autotune_kz(int n, bool fp32, Trial trial, int *kz, int *kz_lean) {
+  int st = autotune_one(n, false, trial, kz, kz_lean);
+  if (!st && fp32) st = autotune_one(n, true, trial, kz, kz_lean);
+  return st;
 }
 
 // E^n on the free nodes for trial step st (any valid slot of the history).
@@ -37,12 +48,13 @@ long long trial_hist_index(const ddfd_problem *p, int st) {
 }
 
 template <typename T>
-int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
+int single_trial(ddfd_problem *p, int steps, int kz, int kz_lean, float *ms) {
   const size_t fbytes = 3 * (size_t)p->cs * sizeof(T);
   const size_t trn = (size_t)p->n_src * (p->Nt + 1) * p->n_det * 3;
   cudaStream_t sm = p->stream;
   p->kz = kz;
-  if (int bs = build_items(p)) return bs;  // the trial runs the dispatch order (and split) of this kz
+  p->kz_lean = kz_lean;
+  if (int bs = build_items(p)) return bs;  // the trial runs the dispatch order (and split) of these depths
   for (int q = 0; q < 2; ++q) {
     CK(cudaMemsetAsync(p->E[q], 0, fbytes, sm));
     if (p->Mu[q]) CK(cudaMemsetAsync(p->Mu[q], 0, fbytes, sm));
@@ -77,12 +89,13 @@ int single_trial(ddfd_problem *p, int steps, int kz, float *ms) {
 }
 
 template <typename T>
-int batch_trial(ddfd_batch *b, int steps, int kz, float *ms) {
+int batch_trial(ddfd_batch *b, int steps, int kz, int kz_lean, float *ms) {
   const size_t fbytes = 3 * (size_t)b->cs * sizeof(T);
   const size_t slab = fbytes * b->m.size();
   cudaStream_t sm = b->stream;
   b->kz = kz;
-  if (int bs = build_batch_items(b)) return bs;  // the trial runs the dispatch orders of this kz
+  b->kz_lean = kz_lean;
+  if (int bs = build_batch_items(b)) return bs;  // the trial runs the dispatch orders of these depths
   for (int q = 0; q < 2; ++q) {
     BCK(cudaMemsetAsync(b->E[q], 0, slab, sm));
     if (b->Mu[q]) BCK(cudaMemsetAsync(b->Mu[q], 0, slab, sm));
@@ -134,13 +147,17 @@ int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out) {
   if (!p) return DDFD_E_ARG;
   p->err.clear();
   if (steps < 1 || steps > p->Nt) return fail(p, DDFD_E_ARG, "steps must be in [1, n_steps]");
-  int best = 0;
+  const int kz0 = p->kz, kzl0 = p->kz_lean;
+  int kz = kz0, kzl = kzl0;
   int st = autotune_kz(
-      p->n,
-      [&](int kz, float *ms) { return p->fp32 ? single_trial<float>(p, steps, kz, ms) : single_trial<double>(p, steps, kz, ms); },
-      &best);
-  if (!st && (st = check_err(p))) best = 0;
-  p->kz = best ? best : p->kz;
+      p->n, p->fp32 != 0,
+      [&](int a, int l, float *ms) {
+        return p->fp32 ? single_trial<float>(p, steps, a, l, ms) : single_trial<double>(p, steps, a, l, ms);
+      },
+      &kz, &kzl);
+  if (!st && (st = check_err(p))) kz = kz0, kzl = kzl0;
+  p->kz = kz;
+  p->kz_lean = kzl;
   p->state = ST_READY;
   drop_graphs(p);
   if (!st) st = build_items(p);
@@ -158,16 +175,21 @@ int ddfd_batch_autotune(ddfd_batch *b, int32_t steps, int32_t *tile_kz_out) {
   if (!b) return DDFD_E_ARG;
   b->err.clear();
   if (steps < 1 || steps > b->Nt) return bfail(b, DDFD_E_ARG, "steps must be in [1, n_steps]");
-  int best = 0;
+  const int kz0 = b->kz, kzl0 = b->kz_lean;
+  int kz = kz0, kzl = kzl0;
   int st = autotune_kz(
-      b->n,
-      [&](int kz, float *ms) { return b->fp32 ? batch_trial<float>(b, steps, kz, ms) : batch_trial<double>(b, steps, kz, ms); },
-      &best);
-  if (!st && (st = batch_check_err(b))) best = 0;
-  b->kz = best ? best : b->kz;
+      b->n, b->fp32 != 0,
+      [&](int a, int l, float *ms) {
+        return b->fp32 ? batch_trial<float>(b, steps, a, l, ms) : batch_trial<double>(b, steps, a, l, ms);
+      },
+      &kz, &kzl);
+  if (!st && (st = batch_check_err(b))) kz = kz0, kzl = kzl0;
+  b->kz = kz;
+  b->kz_lean = kzl;
   drop_batch_graphs(b);
   for (ddfd_problem *p : b->m) {
     p->kz = b->kz;
+    p->kz_lean = b->kz_lean;
     p->state = ST_READY;
     drop_graphs(p);
     if (!st && (st = build_items(p))) b->err = p->err;

@@ -24,15 +24,14 @@ std::vector<int> all_members(const ddfd_batch *b) {
 
 int build_batch_items(ddfd_batch *b) {
   for (ItemTables *v : {&b->items_all, &b->items_ck}) {
-    for (int *t : v->d) {
+    for (uint32_t *t : v->d) {
       cudaFree(t);
       b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)t));
     }
-    v->d.clear();
-    v->n_full.clear();
+    *v = ItemTables();
   }
   b->items_kz = 0;
-  if (b->n > 1024 || (b->n + b->kz - 1) / b->kz > 512) return DDFD_OK;  // beyond the item packing: grid order
+  if (b->n > 1024 || b->kz > ITEM_MAX_NZ || b->kz_lean > ITEM_MAX_NZ) return DDFD_OK;  // grid order
   std::vector<int> ck;
   for (size_t i = 0; i < b->m.size(); ++i)
     if (b->m[i]->nsnap) ck.push_back((int)i);
@@ -43,16 +42,17 @@ int build_batch_items(ddfd_batch *b) {
       std::vector<const ddfd_problem *> ps;
       for (size_t g = g0; g < std::min(g0 + BATCH_MAX, lt.first->size()); ++g) ps.push_back(b->m[(*lt.first)[g]]);
       int n_full = 0;
-      const std::vector<int> it = step_item_order(ps, b->kz, &n_full);
-      int *d = nullptr;
-      if (cudaMalloc((void **)&d, it.size() * sizeof(int)) != cudaSuccess) {
+      const std::vector<uint32_t> it = step_item_order(ps, b->kz, b->kz_lean, &n_full);
+      uint32_t *d = nullptr;
+      if (cudaMalloc((void **)&d, it.size() * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, DDFD_E_OOM, "cudaMalloc of a dispatch table failed");
       }
       b->allocs.push_back(d);
       lt.second->d.push_back(d);
+      lt.second->n_items.push_back((int)it.size());
       lt.second->n_full.push_back(n_full);
-      BCK(cudaMemcpy(d, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice));
+      BCK(cudaMemcpy(d, it.data(), it.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     }
   b->items_kz = b->kz;
   return DDFD_OK;
@@ -388,6 +388,7 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
   b->seg = seg;
   b->stream = (cudaStream_t)cfgs[0].stream;
   b->kz = cfgs[0].tile_kz ? cfgs[0].tile_kz : (b->n >= 128 ? 16 : 8);
+  b->kz_lean = b->n >= 128 ? 16 : 8;
   auto bail = [&](int code, const std::string &m) {
     ddfd::set_thread_error(m);
     destroy_batch(b);

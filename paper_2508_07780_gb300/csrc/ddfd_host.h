@@ -41,8 +41,8 @@ struct FieldMaps {
 // of BATCH_MAX members, the device table and its count of leading items for
 // the full FP32 step kernel.
 struct ItemTables {
-  std::vector<int *> d;
-  std::vector<int> n_full;
+  std::vector<uint32_t *> d;
+  std::vector<int> n_items, n_full;
 };
 
 // Creates (destroys) the side stream and the two events of a StepFork.
@@ -115,9 +115,10 @@ struct ddfd_problem {
   int state = ddfd::host::ST_READY;
   int64_t generation = 0;     // +1 whenever the coefficients or the forward state change
   int64_t launches = 0, fwd_steps = 0;
-  int kz = 16;
-  int *items = nullptr;       // dispatch order of the step launches (heaviest tiles first), for items_kz
-  int items_kz = 0;
+  int kz = 16;                // z depth of the full step kernel's items (and of the FP64 kernel's)
+  int kz_lean = 16;           // z depth of the lean FP32 step kernel's items
+  uint32_t *items = nullptr;  // dispatch order of the step launches (heaviest slabs first), for items_kz
+  int items_kz = 0, n_items = 0;
   int items_nfull = 0;        // FP32: leading items for the full step kernel, the rest lean
   ddfd::StepFork fork;        // side stream of the lean step launches
   int n_part = 256;
@@ -146,7 +147,7 @@ struct ddfd_problem {
 struct ddfd_batch {
   std::vector<ddfd_problem *> m;
   std::string err;
-  int n = 0, Nt = 0, px = 0, fp32 = 0, kz = 16, seg = 0;
+  int n = 0, Nt = 0, px = 0, fp32 = 0, kz = 16, kz_lean = 16, seg = 0;
   long long cs = 0;
   size_t esz = 8;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
@@ -210,14 +211,17 @@ int dalloc(ddfd_problem *p, size_t bytes, void **out);
 void dfree(ddfd_problem *p, void *ptr);
 
 // Dispatch order of one step launch over the problems `ps` (stacked in that
-// order) with z depth kz: whole z slabs (one problem's tiles of one z chunk,
-// in grid order within the slab) sorted by an estimate of their work, heaviest
+// order): z slabs (one problem's z range over a set of its tile columns, in
+// grid order within the slab) sorted by an estimate of their work, heaviest
 // first (node count, plus twice the FEM rows and once the free nodes they
-// hold), ties in grid order.  FP32: the tiles that hold a node strictly inside
-// the FEM cube or a free node come first (their count in *n_full), then the
-// finite-difference-only tiles, each part in that order; FP64: *n_full = all.
-std::vector<int> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int *n_full);
-// (Re)builds p->items for p->kz.
+// hold), ties in order of creation.  FP64: every column in z chunks of kz.
+// FP32: first (their count in *n_full) the columns that meet the FEM cube's
+// interior or the free box, over the z range of those boxes, in chunks of kz
+// (full kernel); then the rest of those columns and every other column in
+// chunks of kz_lean (lean kernel).
+std::vector<uint32_t> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int kz_lean,
+                                      int *n_full);
+// (Re)builds p->items for p->kz and p->kz_lean.
 int build_items(ddfd_problem *p);
 // (Re)builds the batch's tables for b->kz.
 int build_batch_items(ddfd_batch *b);
@@ -350,6 +354,7 @@ StepLaunch<T, 1> single_launch(const StepParams<T> &P, const CUtensorMap &cur, c
   L.nprob = 1;
   L.zchunks = (p->n + P.kz - 1) / P.kz;
   L.items = P.kz == p->items_kz ? p->items : nullptr;
+  L.n_items = p->n_items;
   L.n_full = p->items_nfull;
   L.p[0] = P;
   return L;
@@ -451,6 +456,7 @@ void launch_groups(ddfd_batch *b, bool adj, const std::vector<int> &idx, const C
     const size_t gi = g0 / BATCH_MAX;
     const bool tab = tables && b->kz == b->items_kz && gi < tables->d.size();
     L.items = tab ? tables->d[gi] : nullptr;
+    L.n_items = tab ? tables->n_items[gi] : 0;
     L.n_full = tab ? tables->n_full[gi] : 0;
     for (int g = 0; g < L.nprob; ++g) {
       ddfd_problem *p = b->m[idx[g0 + g]];

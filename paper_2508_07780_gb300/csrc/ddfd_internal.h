@@ -123,13 +123,14 @@ struct StepLaunch {
   CUtensorMap cur, old, s, q;
   int nprob;
   int zchunks;
-  // optional dispatch order: block b of a 1-D grid takes the tile items[b],
-  // packed by pack_step_item (whole z slabs, heaviest first, so that the last
-  // wave is made of light ones); NULL: a 3-D grid of (tile x, tile y, z chunk
-  // + zchunks x problem)
-  const int *items;
+  // optional dispatch order: block b of a 1-D grid of n_items blocks takes
+  // the item items[b] (a tile, a z range and a problem, pack_step_item);
+  // NULL: a 3-D grid of (tile x, tile y, z chunk + zchunks x problem), z
+  // chunks of kz planes
+  const uint32_t *items;
+  int n_items;
   // FP32 with a dispatch order: items[0, n_full) hold FEM-cube or free nodes
-  // and run on the full step kernel; the rest are finite-difference tiles
+  // and run on the full step kernel; the rest are finite-difference z ranges
   // only and run on the lean one (concurrently, on StepFork's side stream)
   int n_full;
   StepParams<T> p[NB];
@@ -149,11 +150,13 @@ struct StepFork {
 // with n = 32 m + 1 covered by m x tiles; FP64: 32 x 8 tiles).
 int step_tiles_x(int n, bool fp32);
 int step_tiles_y(int n, bool fp32);
-// One dispatch item: tile x (< 32), tile y (< 128), z chunk (< 512), problem
-// of the launch (< 16).
-__host__ __device__ inline int pack_step_item(int tx, int ty, int zc, int prob) {
-  return tx | (ty << 5) | (zc << 12) | (prob << 21);
+// One dispatch item: tile x (< 32), tile y (< 128), first plane z0 (< 1024),
+// plane count nz (1..64), problem of the launch (< 16).
+__host__ __device__ inline uint32_t pack_step_item(int tx, int ty, int z0, int nz, int prob) {
+  return (uint32_t)tx | ((uint32_t)ty << 5) | ((uint32_t)z0 << 12) | ((uint32_t)(nz - 1) << 22) |
+         ((uint32_t)prob << 28);
 }
+constexpr int ITEM_MAX_NZ = 64;
 
 // Sets the dynamic shared-memory limit of every step-kernel instance (once,
 // before any launch or capture).

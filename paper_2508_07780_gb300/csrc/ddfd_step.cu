@@ -251,27 +251,48 @@ __device__ __forceinline__ int step_tiles_dev_y(int n) {
   return (n + StepTile<T>::TY - 1) / StepTile<T>::TY;
 }
 
-// Tile of this CTA: (problem of the launch, tile x, tile y, z chunk), from the
-// launch's dispatch order if it has one, else from the 3-D grid.
+// Tile of this CTA: (problem of the launch, tile x, tile y) and its planes
+// [k0, k1), from the launch's dispatch order if it has one, else from the 3-D
+// grid (z chunks of kz planes).
 struct CtaTile {
-  int prob, tx, ty, zc;
+  int prob, tx, ty, k0, k1;
 };
 template <typename LT>
 __device__ __forceinline__ CtaTile cta_tile(const LT &L) {
   CtaTile t;
   if (L.items) {
-    const int it = L.items[blockIdx.x];
-    t.tx = it & 31;
-    t.ty = (it >> 5) & 127;
-    t.zc = (it >> 12) & 511;
-    t.prob = it >> 21;
+    const uint32_t it = L.items[blockIdx.x];
+    t.tx = (int)(it & 31u);
+    t.ty = (int)((it >> 5) & 127u);
+    t.k0 = (int)((it >> 12) & 1023u);
+    t.k1 = t.k0 + (int)((it >> 22) & 63u) + 1;
+    t.prob = (int)(it >> 28);
   } else {
     t.tx = (int)blockIdx.x;
     t.ty = (int)blockIdx.y;
     t.prob = (int)blockIdx.z / L.zchunks;
-    t.zc = (int)blockIdx.z - t.prob * L.zchunks;
+    const int zc = (int)blockIdx.z - t.prob * L.zchunks;
+    const int kz = L.p[sizeof(L.p) == sizeof(L.p[0]) ? 0 : t.prob].kz;
+    t.k0 = zc * kz;
+    t.k1 = t.k0 + kz;
   }
   return t;
+}
+
+// Forward detector sampling of E^n (read-only in the step kernels): the CTAs
+// that own the bottom planes (k0 = 0) of a tile column, one per column
+// whatever the z chunking, share the 3 n_det values by the first 256 threads'
+// index within the column grid.
+template <typename T>
+__device__ __forceinline__ void sample_detectors(const StepParams<T> &P, const CtaTile &ct, int tid) {
+  if (P.n_det <= 0 || ct.k0 != 0 || tid >= STEP_CONSUMERS) return;
+  const int n = P.n;
+  const int gx = step_tiles_dev_x<T>(n), gy = step_tiles_dev_y<T>(n);
+  const long long nb = (long long)gx * gy * STEP_CONSUMERS;
+  for (long long t = ((long long)ct.tx + (long long)gx * ct.ty) * STEP_CONSUMERS + tid; t < 3LL * P.n_det; t += nb) {
+    const int d = (int)(t / 3), c = (int)(t - 3LL * d);
+    P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
+  }
 }
 
 template <typename T, bool ADJ, int NB>
@@ -280,7 +301,6 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   using S = Stage<T>;
   // problem of this CTA (uniform), its tile and z chunk
   const CtaTile ct = cta_tile(L);
-  const int zc = ct.zc, zchunks = L.zchunks;
   const StepParams<T> &P = L.p[NB == 1 ? 0 : ct.prob];
   constexpr int RE = S::ROWS * S::BXW;  // component stride of a staged plane
   constexpr int BW = S::BXW;
@@ -293,23 +313,15 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
   const int n = P.n;
   const int tid = threadIdx.x;
 
-  if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
-    const int gx = step_tiles_dev_x<T>(n), gy = step_tiles_dev_y<T>(n);
-    const long long nb = (long long)gx * gy * zchunks * blockDim.x;
-    long long t = ((long long)ct.tx + gx * ((long long)ct.ty + (long long)gy * zc)) * blockDim.x + tid;
-    for (; t < 3LL * P.n_det; t += nb) {
-      const int d = (int)(t / 3), c = (int)(t - 3LL * d);
-      P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
-    }
-  }
+  if (!ADJ) sample_detectors(P, ct, tid);
 
   const int tx = tid & 31, ty = tid >> 5;
-  // one CTA per (tile, z chunk): planes k0-1 .. k1 are staged, plane index
+  // one CTA per (tile, z range): planes k0-1 .. k1 are staged, plane index
   // p = kk - (k0 - 1) in slot p % RING
   const int x0 = ct.tx * STEP_TX, y0 = ct.ty * S::TY;
-  const int k0 = zc * P.kz;
+  const int k0 = ct.k0;
   if (k0 >= n) return;  // uniform per CTA
-  const int k1 = min(k0 + P.kz, n);
+  const int k1 = min(ct.k1, n);
   const bool tile_fem = x0 <= P.b - 1 && x0 + STEP_TX - 1 >= P.a + 1 && y0 <= P.b - 1 &&
                         y0 + S::TY - 1 >= P.a + 1;
 
@@ -685,7 +697,6 @@ __global__ void __launch_bounds__(PairMode<ADJ, LEAN>::THREADS, PairMode<ADJ, LE
   using S = PairStageT<LEAN>;
   constexpr int RE = S::RE, BW = S::BXW, TXY = S::TXY;
   const CtaTile ct = cta_tile(L);
-  const int zc = ct.zc, zchunks = L.zchunks;
   const StepParams<float> &P = L.p[NB == 1 ? 0 : ct.prob];
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -697,20 +708,12 @@ __global__ void __launch_bounds__(PairMode<ADJ, LEAN>::THREADS, PairMode<ADJ, LE
   const int n = P.n;
   const int tid = threadIdx.x;
 
-  if (!ADJ && P.n_det > 0) {  // detector sampling of E^n (read-only in this kernel)
-    const int gx = step_tiles_dev_x<float>(n), gy = step_tiles_dev_y<float>(n);
-    const long long nb = (long long)gx * gy * zchunks * blockDim.x;
-    long long t = ((long long)ct.tx + gx * ((long long)ct.ty + (long long)gy * zc)) * blockDim.x + tid;
-    for (; t < 3LL * P.n_det; t += nb) {
-      const int d = (int)(t / 3), c = (int)(t - 3LL * d);
-      P.trace_n[t] = (double)P.cur[c * P.cs + P.det_node[d]];
-    }
-  }
+  if (!ADJ) sample_detectors(P, ct, tid);
 
   const int x0 = ct.tx * S::TX, y0 = ct.ty * S::TY;
-  const int k0 = zc * P.kz;
+  const int k0 = ct.k0;
   if (k0 >= n) return;  // uniform per CTA
-  const int k1 = min(k0 + P.kz, n);
+  const int k1 = min(ct.k1, n);
   const bool tile_fem =
       !LEAN && x0 <= P.b - 1 && x0 + S::TX - 1 >= P.a + 1 && y0 <= P.b - 1 && y0 + S::TY - 1 >= P.a + 1;
   const int nplanes = k1 - k0 + 2;
@@ -1098,7 +1101,7 @@ int step_tiles_y(int n, bool fp32) {
 template <typename T, int NB>
 static dim3 step_grid(const StepLaunch<T, NB> &L) {
   const int gx = step_tiles_x(L.p[0].n, sizeof(T) == 4), gy = step_tiles_y(L.p[0].n, sizeof(T) == 4);
-  if (L.items) return dim3((unsigned)(gx * gy * L.zchunks * L.nprob));
+  if (L.items) return dim3((unsigned)L.n_items);
   return dim3(gx, gy, L.zchunks * L.nprob);
 }
 
