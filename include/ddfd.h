@@ -269,6 +269,22 @@ int ddfd_time_gather(ddfd_problem *p, int32_t reps, double *fwd_ms, double *adj_
  * DDFD_FEM_MESH (DDFD_E_ARG otherwise). */
 int ddfd_test_gather_timeout(ddfd_problem *p, int32_t fault, uint32_t spin_limit);
 
+/* Host-only inspection of the step kernels' dispatch order (no device call,
+ * no handle; the paper has no counterpart).  Builds the item list of one step
+ * launch over nprob problems of n^3 nodes (precision DDFD_FP32 or DDFD_FP64)
+ * whose FEM cube spans nodes [a, b] and free box [f0, f0 + nf) on each axis,
+ * boxes[4 q .. 4 q + 3] = (a, b, f0, nf) for problem q, with z depths kz (full
+ * kernel, FP64 kernel) and kz_lean (lean FP32 kernel).  Each item packs tile x
+ * (bits 0-4, 32 nodes a tile), tile y (bits 5-11; 16 rows FP32, 8 FP64), the
+ * first plane z0 (bits 12-21), the plane count minus one (bits 22-27) and the
+ * problem (bits 28-31); the first *n_full items run on the full kernel.  Up to
+ * cap items are written to items (may be NULL with cap = 0); *n_items gets
+ * the count.  DDFD_E_ARG: n outside [7, 1024], nprob outside [1, 16], a depth
+ * outside [1, 64], a box outside the grid, or cap too small (with *n_items
+ * set). */
+int ddfd_test_step_items(int32_t n, int32_t precision, int32_t nprob, const int32_t *boxes, int32_t kz,
+                         int32_t kz_lean, uint32_t *items, int64_t cap, int64_t *n_items, int64_t *n_full);
+
 /* Tile autotuner for the step kernels of one handle.  Times `steps` forward
  * and `steps` adjoint step kernels (CUDA events on the handle's stream) for
  * each candidate z depth of the thread-block tile (32 x 8 x kz nodes; kz in

@@ -39,6 +39,7 @@ ABI_SYMBOLS = (
     "ddfd_batch_member", "ddfd_batch_forward", "ddfd_batch_forward_dev", "ddfd_batch_adjoint",
     "ddfd_batch_adjoint_dev", "ddfd_batch_autotune", "ddfd_batch_get_info",
     "ddfd_cg_params_default", "ddfd_cg_run", "ddfd_test_gather_timeout", "ddfd_time_gather",
+    "ddfd_test_step_items",
 )
 
 
@@ -159,6 +160,8 @@ def load_library(path: str = LIB_PATH):
     lib.ddfd_batch_autotune.argtypes = [P, c_int32, POINTER(c_int32)]
     lib.ddfd_batch_get_info.argtypes = [P, POINTER(ddfd_batch_info)]
     lib.ddfd_test_gather_timeout.argtypes = [P, c_int32, ctypes.c_uint32]
+    lib.ddfd_test_step_items.argtypes = [c_int32, c_int32, c_int32, POINTER(c_int32), c_int32, c_int32,
+                                         POINTER(ctypes.c_uint32), c_int64, POINTER(c_int64), POINTER(c_int64)]
     lib.ddfd_time_gather.argtypes = [P, c_int32, P, P, P, P]
     lib.ddfd_cg_params_default.argtypes = [POINTER(ddfd_cg_params)]
     lib.ddfd_cg_params_default.restype = None
@@ -212,6 +215,26 @@ def misfit_noalloc(trace, eobs, n_src, n_steps, n_det, tau, z_delta_frac, J, str
                                  _ptr(J), c_void_p(stream) if stream else None)
     if st != DDFD_OK:
         raise DDFDError(st, lib.ddfd_create_error().decode())
+
+
+def step_items(n, precision, boxes, kz, kz_lean):
+    """ddfd_test_step_items (host only): the dispatch items of one step launch
+    over len(boxes) problems of n^3 nodes, boxes = [(a, b, f0, nf), ...].
+    Returns (items as a uint32 array, n_full)."""
+    lib = load_library()
+    prec = {"fp64": DDFD_FP64, "fp32": DDFD_FP32}[precision]
+    bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1))
+    ni, nf = c_int64(), c_int64()
+    args = (int(n), prec, len(boxes), bx.ctypes.data_as(POINTER(c_int32)), int(kz), int(kz_lean))
+    st = lib.ddfd_test_step_items(*args, None, 0, ctypes.byref(ni), ctypes.byref(nf))
+    if st != DDFD_OK:
+        raise DDFDError(st, "ddfd_test_step_items rejected its arguments")
+    out = np.zeros(ni.value, dtype=np.uint32)
+    st = lib.ddfd_test_step_items(*args, out.ctypes.data_as(POINTER(ctypes.c_uint32)), ni.value,
+                                  ctypes.byref(ni), ctypes.byref(nf))
+    if st != DDFD_OK:
+        raise DDFDError(st, "ddfd_test_step_items rejected its arguments")
+    return out, nf.value
 
 
 def make_config(lib, kw, keep):

@@ -1182,6 +1182,35 @@ int ddfd_time_gather(ddfd_problem *p, int32_t reps, double *fwd_ms, double *adj_
   return DDFD_OK;
 }
 
+int ddfd_test_step_items(int32_t n, int32_t precision, int32_t nprob, const int32_t *boxes, int32_t kz,
+                         int32_t kz_lean, uint32_t *items, int64_t cap, int64_t *n_items, int64_t *n_full) {
+  if (n < 7 || n > 1024 || nprob < 1 || nprob > BATCH_MAX || !boxes || !n_items || !n_full || kz < 1 ||
+      kz > ITEM_MAX_NZ || kz_lean < 1 || kz_lean > ITEM_MAX_NZ || cap < 0 || (cap > 0 && !items) ||
+      (precision != DDFD_FP32 && precision != DDFD_FP64))
+    return DDFD_E_ARG;
+  std::vector<ddfd_problem> pv((size_t)nprob);
+  std::vector<const ddfd_problem *> ps;
+  for (int q = 0; q < nprob; ++q) {
+    ddfd_problem &p = pv[(size_t)q];
+    p.n = n;
+    p.fp32 = precision == DDFD_FP32;
+    p.a = boxes[4 * q];
+    p.b = boxes[4 * q + 1];
+    p.f0 = boxes[4 * q + 2];
+    p.nf = boxes[4 * q + 3];
+    if (p.a < 0 || p.b >= n || p.a > p.b || p.nf < 0 || (p.nf > 0 && (p.f0 < 0 || p.f0 + p.nf > n)))
+      return DDFD_E_ARG;
+    ps.push_back(&p);
+  }
+  int nf = 0;
+  const std::vector<uint32_t> it = step_item_order(ps, kz, kz_lean, &nf);
+  *n_items = (int64_t)it.size();
+  *n_full = nf;
+  if ((int64_t)it.size() > cap) return cap == 0 && !items ? DDFD_OK : DDFD_E_ARG;
+  std::copy(it.begin(), it.end(), items);
+  return DDFD_OK;
+}
+
 int ddfd_test_gather_timeout(ddfd_problem *p, int32_t fault, uint32_t spin_limit) {
   if (!p) return DDFD_E_ARG;
   p->err.clear();
