@@ -108,8 +108,9 @@ typedef struct {
   int32_t cfl_check;     /* nonzero: estimate the stability bound by power iteration
                             at ddfd_set_coeffs and fail with DDFD_E_CFL above it */
   int64_t mem_budget;    /* device bytes the handle may allocate; 0 = no limit */
-  int32_t tile_kz;       /* z planes per thread block of the step kernels (tuning;
-                            0 = library default, else 2..n) */
+  int32_t tile_kz;       /* z planes per thread block of the full step kernel (FP32 tiles
+                            holding FEM-cube or free nodes; every FP64 tile); tuning:
+                            0 = library default (16 for n >= 128, else 8), else 2..n */
   int32_t forward_only;  /* nonzero: keep neither the E history nor snapshots (for
                             data generation); ddfd_adjoint then fails with DDFD_E_STATE */
   /* fem_kind = DDFD_FEM_MESH: the tetrahedra of the FEM cube [a, b]^3, a locally
@@ -133,6 +134,9 @@ typedef struct {
                             literal variant keeps E on every FEM-updated node for every step
                             and takes neither n_snapshots, forward_only, fem_kind other than
                             DDFD_FEM_STENCIL, nor batches. */
+  int32_t tile_kz_lean;  /* z planes per thread block of the lean FP32 step kernel (the
+                            finite-difference-only tiles, run beside the full kernel);
+                            tuning: 0 = library default (16 for n >= 128, else 8), else 2..64 */
 } ddfd_config;
 
 /* Fill *cfg with defaults: cfl 0.3, FP64, stencil FEM, 1 normal-incidence
@@ -286,10 +290,12 @@ int ddfd_test_step_items(int32_t n, int32_t precision, int32_t nprob, const int3
                          int32_t kz_lean, uint32_t *items, int64_t cap, int64_t *n_items, int64_t *n_full);
 
 /* Tile autotuner for the step kernels of one handle.  Times `steps` forward
- * and `steps` adjoint step kernels (CUDA events on the handle's stream) for
- * each candidate z depth of the thread-block tile (32 x 8 x kz nodes; kz in
- * 4, 6, 8, 12, 16, 24, 32, up to n) and keeps the fastest; *tile_kz_out (may
- * be NULL) receives it.  The trial steps overwrite the fields, so forward
+ * and `steps` adjoint steps (CUDA events on the handle's stream) for each
+ * candidate z depth of the full kernel's thread-block tiles (4, 6, 8, 12, 16,
+ * 24, 32, up to n), the lean kernel's depth held, and keeps the fastest; in
+ * FP32 it then does the same for the lean kernel's depth.  *tile_kz_out (may
+ * be NULL) receives the full kernel's depth (ddfd_batch_get_info reports
+ * both for a batch).  The trial steps overwrite the fields, so forward
  * and adjoint state are invalidated (run ddfd_forward again).  1 <= steps
  * <= n_steps.  The paper has no counterpart (a GPU tuning aid). */
 int ddfd_autotune(ddfd_problem *p, int32_t steps, int32_t *tile_kz_out);
@@ -340,15 +346,18 @@ int ddfd_batch_adjoint_dev(ddfd_batch *b, const double *const *eobs);
 int ddfd_batch_autotune(ddfd_batch *b, int32_t steps, int32_t *tile_kz_out);
 
 /* Bookkeeping of a batch: timing of the last batched forward / adjoint
- * sequences (device time, CUDA events on the batch stream; step kernels
- * counts one per batched launch), kernels launched, device bytes of the
- * batch and its members, and the tile depth in use. */
+ * sequences (device time, CUDA events on the batch stream; the step-kernel
+ * counts count one per batched step of a group of up to 16 members, which
+ * runs one kernel, or in FP32 the full and the lean kernel side by side),
+ * kernels launched, device bytes of the batch and its members, and the tile
+ * depths in use (full kernel, lean kernel). */
 typedef struct {
   int32_t count, tile_kz;
   double forward_loop_ms, adjoint_loop_ms;
   int64_t forward_step_kernels, adjoint_step_kernels;
   int64_t kernel_launches;
   int64_t device_bytes;
+  int32_t tile_kz_lean;
 } ddfd_batch_info;
 int ddfd_batch_get_info(const ddfd_batch *b, ddfd_batch_info *info);
 

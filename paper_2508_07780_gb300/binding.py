@@ -55,6 +55,7 @@ class ddfd_config(ctypes.Structure):
         ("mem_budget", c_int64), ("tile_kz", c_int32), ("forward_only", c_int32),
         ("mesh_n_new", c_int32), ("mesh_parents", POINTER(c_int32)), ("mesh_n_tets", c_int64),
         ("mesh_tets", POINTER(c_int32)), ("stream", c_void_p), ("grad_variant", c_int32),
+        ("tile_kz_lean", c_int32),
     ]
 
 
@@ -80,7 +81,7 @@ class ddfd_batch_info(ctypes.Structure):
         ("count", c_int32), ("tile_kz", c_int32),
         ("forward_loop_ms", c_double), ("adjoint_loop_ms", c_double),
         ("forward_step_kernels", c_int64), ("adjoint_step_kernels", c_int64),
-        ("kernel_launches", c_int64), ("device_bytes", c_int64),
+        ("kernel_launches", c_int64), ("device_bytes", c_int64), ("tile_kz_lean", c_int32),
     ]
 
 

@@ -241,6 +241,8 @@ int validate(const ddfd_config *c, std::string *m) {
   if (c->n_snapshots < 0 || c->n_snapshots > c->n_steps) return *m = "n_snapshots must be in [0, n_steps]", DDFD_E_ARG;
   if (c->mem_budget < 0) return *m = "mem_budget must be >= 0", DDFD_E_ARG;
   if (c->tile_kz != 0 && (c->tile_kz < 2 || c->tile_kz > c->n)) return *m = "tile_kz must be 0 or in [2, n]", DDFD_E_ARG;
+  if (c->tile_kz_lean != 0 && (c->tile_kz_lean < 2 || c->tile_kz_lean > ITEM_MAX_NZ))
+    return *m = "tile_kz_lean must be 0 or in [2, 64]", DDFD_E_ARG;
   if (c->src_dir)
     for (int s = 0; s < c->n_src; ++s) {
       const double *k = c->src_dir + 3 * s;
@@ -878,7 +880,7 @@ int create_impl(const ddfd_config *cfg, const MemberSlot *ext, ddfd_problem **ou
   p->esz = p->fp32 ? 4 : 8;
   p->stream = (cudaStream_t)cfg->stream;
   p->kz = cfg->tile_kz ? cfg->tile_kz : (p->n >= 128 ? 16 : 8);
-  p->kz_lean = p->n >= 128 ? 16 : 8;
+  p->kz_lean = cfg->tile_kz_lean ? cfg->tile_kz_lean : (p->n >= 128 ? 16 : 8);
 
   auto bail = [&](int code) {
     g_create_err = p->err;

@@ -388,7 +388,7 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
   b->seg = seg;
   b->stream = (cudaStream_t)cfgs[0].stream;
   b->kz = cfgs[0].tile_kz ? cfgs[0].tile_kz : (b->n >= 128 ? 16 : 8);
-  b->kz_lean = b->n >= 128 ? 16 : 8;
+  b->kz_lean = cfgs[0].tile_kz_lean ? cfgs[0].tile_kz_lean : (b->n >= 128 ? 16 : 8);
   auto bail = [&](int code, const std::string &m) {
     ddfd::set_thread_error(m);
     destroy_batch(b);
@@ -426,6 +426,7 @@ int ddfd_create_batch(const ddfd_config *cfgs, int32_t count, ddfd_batch **out) 
     ddfd_config c = cfgs[i];
     c.stream = cfgs[0].stream;
     c.tile_kz = b->kz;
+    c.tile_kz_lean = b->kz_lean;
     MemberSlot ms;
     for (int q = 0; q < 2; ++q) {
       ms.E[q] = (char *)b->E[q] + i * fb;
@@ -486,6 +487,7 @@ int ddfd_batch_get_info(const ddfd_batch *b, ddfd_batch_info *info) {
   if (!b || !info) return DDFD_E_ARG;
   info->count = (int32_t)b->m.size();
   info->tile_kz = b->kz;
+  info->tile_kz_lean = b->kz_lean;
   info->forward_loop_ms = b->fwd_ms;
   info->adjoint_loop_ms = b->adj_ms;
   info->forward_step_kernels = b->fwd_kernels;
