@@ -13,8 +13,10 @@ Prints ONE JSON line (rank 0):
               pass, forward + adjoint), device-resident inputs;
   e2e         the same through the host-pointer entry points, with the
               host<->device copies inside the timed region;
-  roofline    the dominant step kernel (the batched adjoint step) against the
-              measured HBM copy bandwidth, with the forward kernel and the
+  roofline    the dominant step (the batched adjoint step: its full kernel
+              for the tiles with FEM-cube or free nodes and its lean kernel
+              for the finite-difference tiles, side by side) against the
+              measured HBM copy bandwidth, with the forward step and the
               whole pass beside it;
   fp64_plain  the plain FP64 GPU path on the same 16 problems, solved one at a
               time, its FP64 ALU roofline, and the FP32 speedup;
@@ -104,9 +106,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def traffic_per_launch(key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current step-kernel source (sha256 prefix match); else None."""
+def traffic_per_launch(*keys):
+    """DRAM bytes per launch (the sum over `keys`: the kernels of one step)
+    from the committed ncu summary, if it was taken on the current
+    step-kernel source (sha256 prefix match); else None."""
     try:
         src_hash = hashlib.sha256(open(STEP_SRC, "rb").read()).hexdigest()[:16]
         vals = {}
@@ -118,7 +121,7 @@ def traffic_per_launch(key):
             vals[k.strip()] = v.strip()
         if vals.get("source_sha256_16") != src_hash:
             return None
-        return float(vals[key])
+        return float(sum(float(vals[k]) for k in keys))
     except Exception:
         return None
 
@@ -365,9 +368,11 @@ def run_batched(args, dev, stream, rank, world, peak):
     from paper_2508_07780_gb300 import Batch
 
     probs = batched_problems(first=16 * rank, n_steps=args.batch_steps)
+    kzs = {} if args.batch_kz == "auto" else dict(zip(("tile_kz", "tile_kz_lean"),
+                                                       (int(v) for v in args.batch_kz.split(","))))
     cfgs = [dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, precision="fp32",
                  src_dir=d[None, :], det_ij=w.detectors(), z_delta_frac=w.z_delta_frac,
-                 stream=stream.cuda_stream) for w, d in probs]
+                 stream=stream.cuda_stream, **kzs) for w, d in probs]
     b = Batch(cfgs)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     # observed data: each member's layers-only model trace (FP64 forward of the
@@ -386,7 +391,9 @@ def run_batched(args, dev, stream, rank, world, peak):
     coefs = [tuple(T(a) for a in w.model()) for w, _ in probs]
     grads = [(torch.empty(m.n_free, dtype=torch.float64, device=dev),
               torch.empty(m.n_free, dtype=torch.float64, device=dev)) for m in b.members]
-    kz = b.autotune(steps=8)
+    if args.batch_kz == "auto":
+        b.autotune(steps=8)
+    kz = (b.get_info().tile_kz, b.get_info().tile_kz_lean)
 
     def step():
         for m, (e, s) in zip(b.members, coefs):
@@ -497,14 +504,17 @@ def run_batched(args, dev, stream, rank, world, peak):
     res["roofline"] = {
         "bound": "hbm", "achieved": ab / (adj_avg / 1e3) / 1e9, "peak": peak[0], "unit": "GB/s",
         "frac": ab / (adj_avg / 1e3) / 1e9 / peak[0],
-        "traffic": traffic_per_launch("batched_adjoint_dram_bytes_per_launch"),
-        "kernel": "k_step_pair<adjoint,16> (one launch = one adjoint step of all 16 problems)",
+        "traffic": traffic_per_launch("batched_adjoint_full_dram_bytes", "batched_adjoint_lean_dram_bytes"),
+        "kernel": "k_step_pair<adjoint,16>: full kernel (tiles with FEM-cube or free nodes) and lean kernel "
+                  "(finite-difference tiles) side by side; one launch = one adjoint step of all 16 problems",
         "algorithmic_bytes_per_launch": ab, "avg_launch_ms": adj_avg,
         "peak_kind": f"{peak[1]} (HBM copy, MEASURED_PEAKS.json hbm_gbs)",
-        "forward": {"kernel": "k_step_pair<forward,16>", "algorithmic_bytes_per_launch": fb,
+        "forward": {"kernel": "k_step_pair<forward,16>, full and lean kernels side by side",
+                    "algorithmic_bytes_per_launch": fb,
                     "avg_launch_ms": fwd_avg, "achieved": fb / (fwd_avg / 1e3) / 1e9,
                     "frac": fb / (fwd_avg / 1e3) / 1e9 / peak[0],
-                    "traffic": traffic_per_launch("batched_forward_dram_bytes_per_launch")},
+                    "traffic": traffic_per_launch("batched_forward_full_dram_bytes",
+                                                  "batched_forward_lean_dram_bytes")},
         "whole_pass": {"algorithmic_bytes": (fb + ab) * nt, "ms": ms,
                        "achieved": (fb + ab) * nt / (ms / 1e3) / 1e9,
                        "frac": (fb + ab) * nt / (ms / 1e3) / 1e9 / peak[0],
@@ -637,14 +647,16 @@ def run_single_201(args, dev, stream, peak):
     return {"workload": describe(w), "gradient": args.grad_variant, "value": w.updates / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"],
             "device_bytes": int(a["bytes"]),
             "roofline": {"bound": "hbm", "peak": peak[0], "unit": "GB/s",
-                         "forward": {"kernel": "k_step_pair<forward,1>", "avg_launch_ms": a["fwd"],
-                                     "algorithmic_bytes_per_launch": fb,
+                         "forward": {"kernel": "k_step_pair<forward,1>, full and lean kernels side by side",
+                                     "avg_launch_ms": a["fwd"], "algorithmic_bytes_per_launch": fb,
                                      "frac": fb / (a["fwd"] / 1e3) / 1e9 / peak[0],
-                                     "traffic": traffic_per_launch("forward_dram_bytes_per_launch_full")},
-                         "adjoint": {"kernel": "k_step_pair<adjoint,1>", "avg_launch_ms": a["adj"],
-                                     "algorithmic_bytes_per_launch": ab,
+                                     "traffic": traffic_per_launch("single_forward_full_dram_bytes",
+                                                                   "single_forward_lean_dram_bytes")},
+                         "adjoint": {"kernel": "k_step_pair<adjoint,1>, full and lean kernels side by side",
+                                     "avg_launch_ms": a["adj"], "algorithmic_bytes_per_launch": ab,
                                      "frac": ab / (a["adj"] / 1e3) / 1e9 / peak[0],
-                                     "traffic": traffic_per_launch("adjoint_dram_bytes_per_launch_full")}},
+                                     "traffic": traffic_per_launch("single_adjoint_full_dram_bytes",
+                                                                   "single_adjoint_lean_dram_bytes")}},
             "fp64_plain": {"value": w.updates / (b["ms"] / 1e3), "ms_per_step": b["ms"],
                            "fp32_speedup": b["ms"] / a["ms"]},
             "accuracy_vs_fp64": {"trace": rel(a["trace"], b["trace"]),
@@ -805,6 +817,8 @@ def main():
                          "(default) or the paper-literal one of Sec. 4")
     ap.add_argument("--no-refined", action="store_true", help="skip the refined-mesh element-gather leg")
     ap.add_argument("--cpu-workers", type=int, default=min(8, os.cpu_count() or 1))
+    ap.add_argument("--batch-kz", default="auto",
+                    help="z depths 'FULL,LEAN' of the batched step kernels, or 'auto' (autotuned)")
     ap.add_argument("--single-steps", type=int, default=2000,
                     help="time steps of the single-source 201^3 workload (2000; fewer only for profiler captures)")
     ap.add_argument("--batch-steps", type=int, default=1600,

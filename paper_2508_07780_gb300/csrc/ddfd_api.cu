@@ -116,31 +116,46 @@ std::vector<uint32_t> step_item_order(const std::vector<const ddfd_problem *> &p
       for (int z0 = 0; z0 < n; z0 += kz) full.push_back({cost(z0, std::min(z0 + kz, n)), (int)q, z0, std::min(z0 + kz, n), false});
       continue;
     }
-    // FEM columns: [zf0, zf1) in chunks of kz on the full kernel, the rest in
-    // chunks of kz_lean on the lean one; the other columns: all lean
+    // FEM columns: [zf0, zf1) in chunks of kz on the full kernel; the rest of
+    // them and every other column on the lean one (below)
     for (int z0 = zf0; z0 < zf1; z0 += kz) full.push_back({cost(z0, std::min(z0 + kz, zf1)), (int)q, z0, std::min(z0 + kz, zf1), true});
-    for (int z0 = 0; z0 < zf0; z0 += kz_lean) lean.push_back({cost(z0, std::min(z0 + kz_lean, zf0)), (int)q, z0, std::min(z0 + kz_lean, zf0), true});
-    for (int z0 = zf1; z0 < n; z0 += kz_lean) lean.push_back({cost(z0, std::min(z0 + kz_lean, n)), (int)q, z0, std::min(z0 + kz_lean, n), true});
-    for (int z0 = 0; z0 < n; z0 += kz_lean) lean.push_back({cost(z0, std::min(z0 + kz_lean, n)), (int)q, z0, std::min(z0 + kz_lean, n), false});
+    lean.push_back({0, (int)q, zf0, zf1, true});
   }
   auto heavy_first = [](const Slab &l, const Slab &r) { return l.cost > r.cost; };
   std::stable_sort(full.begin(), full.end(), heavy_first);
-  std::stable_sort(lean.begin(), lean.end(), heavy_first);
   std::vector<uint32_t> out;
-  auto emit = [&](const std::vector<Slab> &v, bool all_cols_full) {
-    for (const Slab &sl : v)
+  for (const Slab &sl : full)
+    for (int ty = 0; ty < gy; ++ty)
+      for (int tx = 0; tx < gx; ++tx) {
+        // full slabs of FP64 / FEM-free problems hold every column, the others
+        // only the FEM columns
+        if (sl.fem && !colfem[sl.q][(size_t)tx + (size_t)gx * ty]) continue;
+        out.push_back(pack_step_item(tx, ty, sl.z0, sl.z1 - sl.z0, sl.q));
+      }
+  *n_full = (int)out.size();
+  // lean items: every node's work is the same, so they go by problem and z
+  // chunk (chunks of kz_lean from z = 0), all the chunk's columns together,
+  // which keeps the planes that neighbouring items share (x, y and z halos)
+  // in L2 between their reads; a FEM column contributes the parts of the chunk
+  // outside its full range [zf0, zf1)
+  for (const Slab &sl : lean) {
+    const int zf0 = sl.z0, zf1 = sl.z1;
+    for (int z0 = 0; z0 < n; z0 += kz_lean) {
+      const int z1 = std::min(z0 + kz_lean, n);
       for (int ty = 0; ty < gy; ++ty)
         for (int tx = 0; tx < gx; ++tx) {
-          const bool cf = colfem[sl.q][(size_t)tx + (size_t)gx * ty] != 0;
-          // full slabs of FP64 / FEM-free problems hold every column; the
-          // others only the FEM columns (fem) or only the rest (!fem)
-          if (!(all_cols_full && !sl.fem) && cf != sl.fem) continue;
-          out.push_back(pack_step_item(tx, ty, sl.z0, sl.z1 - sl.z0, sl.q));
+          if (!colfem[sl.q][(size_t)tx + (size_t)gx * ty]) {
+            out.push_back(pack_step_item(tx, ty, z0, z1 - z0, sl.q));
+            continue;
+          }
+          if (z0 < zf0) out.push_back(pack_step_item(tx, ty, z0, std::min(z1, zf0) - z0, sl.q));
+          if (z1 > zf1) {
+            const int lo = std::max(z0, zf1);
+            out.push_back(pack_step_item(tx, ty, lo, z1 - lo, sl.q));
+          }
         }
-  };
-  emit(full, true);
-  *n_full = (int)out.size();
-  emit(lean, false);
+    }
+  }
   return out;
 }
 

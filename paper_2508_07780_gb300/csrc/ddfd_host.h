@@ -211,14 +211,15 @@ int dalloc(ddfd_problem *p, size_t bytes, void **out);
 void dfree(ddfd_problem *p, void *ptr);
 
 // Dispatch order of one step launch over the problems `ps` (stacked in that
-// order): z slabs (one problem's z range over a set of its tile columns, in
-// grid order within the slab) sorted by an estimate of their work, heaviest
-// first (node count, plus twice the FEM rows and once the free nodes they
-// hold), ties in order of creation.  FP64: every column in z chunks of kz.
-// FP32: first (their count in *n_full) the columns that meet the FEM cube's
-// interior or the free box, over the z range of those boxes, in chunks of kz
-// (full kernel); then the rest of those columns and every other column in
-// chunks of kz_lean (lean kernel).
+// order).  Full-kernel items first (their count in *n_full): z slabs (one
+// problem's z range over a set of its tile columns, in grid order within the
+// slab) sorted by an estimate of their work, heaviest first (node count, plus
+// twice the FEM rows and once the free nodes they hold), ties in order of
+// creation; FP64: every column in z chunks of kz; FP32: the columns that meet
+// the FEM cube's interior or the free box, over the z range of those boxes,
+// in chunks of kz.  Then (FP32) the lean-kernel items, problem by problem and
+// z chunk by z chunk (chunks of kz_lean from z = 0): every other column, and
+// the FEM columns' planes outside their full range.
 std::vector<uint32_t> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int kz_lean,
                                       int *n_full);
 // (Re)builds p->items for p->kz and p->kz_lean.
