@@ -574,6 +574,11 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 2)
 
 __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 
+// Moves the line holding p into L2 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
+
 // Packed FP32 (sm_100+): one instruction for the two nodes of a pair.  These
 // round exactly like the scalar operations; a - b is written fma(b, -1, a),
 // which is exact in its negation.
@@ -843,6 +848,19 @@ __global__ void __launch_bounds__(PairMode<ADJ, LEAN>::THREADS, PairMode<ADJ, LE
       ab[c] = ld2(Ep + c * RE + ci);
     }
     if (live_a) {
+      if (ADJ && !LEAN && (free_a || free_b) && kfree) {
+        // the gradient operands of this plane's free nodes (E^k history, block
+        // sums, at a fold the FP64 sums), read after the update below: fetched
+        // into L2 now, so that the stencil work hides their DRAM latency
+        const long long fp = (x - P.f0) + (long long)P.nf * ((y - P.f0) + (long long)P.nf * (k - P.f0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) prefetch_l2(P.hist_r + c * P.n_free + fp);
+        prefetch_l2(reinterpret_cast<const float2 *>(P.gpart) + fp);
+        if (P.gmode & GM_FOLD) {
+          prefetch_l2(P.gacc_e + fp);
+          prefetch_l2(P.gacc_s + fp);
+        }
+      }
       // The pair's arithmetic runs in packed FP32 (x: node a, y: node b).  Q
       // holds -R, so that every subtraction is a multiply-add with a constant
       // (exact negations); a boundary node converts to R for the scalar
@@ -971,32 +989,36 @@ __global__ void __launch_bounds__(PairMode<ADJ, LEAN>::THREADS, PairMode<ADJ, LE
             }
           }
         } else {
+          // both nodes' gradient terms in packed FP32 (a node that is not free
+          // adds nothing: its E^k operand is zero and nothing is stored)
+          const float *hr = P.hist_r + fi;
+          float2 ge = kZero, gs = kZero;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (h == 0 ? !fre_a : !fre_b) continue;
-            const long long f = fi + h;
-            float ge = 0.f, gs = 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float hv = __ldg(P.hist_r + c * P.n_free + f);
-              const float nv = h ? nw[c].y : nw[c].x, cv = h ? cen[c].y : cen[c].x, ov = h ? od[c].y : od[c].x;
-              const float sv = h ? SX[c].y : SX[c].x;
-              ge += hv * ((nv - 2.f * cv + ov) + P.r2 * sv);
-              gs += hv * (nv - ov);
+          for (int c = 0; c < 3; ++c) {
+            const float2 hv = make_float2(fre_a ? __ldg(hr + c * P.n_free) : 0.f, fre_b ? __ldg(hr + c * P.n_free + 1) : 0.f);
+            const float2 te = fma2(R2, SX[c], add2(fma2(cen[c], f2(-2.f), nw[c]), od[c]));
+            ge = fma2(hv, te, ge);
+            gs = fma2(hv, fma2(od[c], kM1, nw[c]), gs);
+          }
+          // block sums in FP32, folded into the FP64 accumulators
+          float2 *gp = reinterpret_cast<float2 *>(P.gpart) + fi;
+          if (!(P.gmode & GM_FIRST)) {
+            const float2 pa = fre_a ? gp[0] : kZero, pb = fre_b ? gp[1] : kZero;
+            ge = add2(make_float2(pa.x, pb.x), ge);
+            gs = add2(make_float2(pa.y, pb.y), gs);
+          }
+          if (P.gmode & GM_FOLD) {
+            if (fre_a) {
+              P.gacc_e[fi] += (double)ge.x;
+              P.gacc_s[fi] += (double)gs.x;
             }
-            // block sums in FP32, folded into the FP64 accumulators
-            float2 *gp = reinterpret_cast<float2 *>(P.gpart) + f;
-            if (!(P.gmode & GM_FIRST)) {
-              const float2 prev = *gp;
-              ge = prev.x + ge;
-              gs = prev.y + gs;
+            if (fre_b) {
+              P.gacc_e[fi + 1] += (double)ge.y;
+              P.gacc_s[fi + 1] += (double)gs.y;
             }
-            if (P.gmode & GM_FOLD) {
-              P.gacc_e[f] += (double)ge;
-              P.gacc_s[f] += (double)gs;
-            } else {
-              *gp = make_float2(ge, gs);
-            }
+          } else {
+            if (fre_a) gp[0] = make_float2(ge.x, gs.x);
+            if (fre_b) gp[1] = make_float2(ge.y, gs.y);
           }
         }
       }
