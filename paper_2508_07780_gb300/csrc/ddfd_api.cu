@@ -122,7 +122,23 @@ std::vector<uint32_t> step_item_order(const std::vector<const ddfd_problem *> &p
     lean.push_back({0, (int)q, zf0, zf1, true});
   }
   auto heavy_first = [](const Slab &l, const Slab &r) { return l.cost > r.cost; };
-  std::stable_sort(full.begin(), full.end(), heavy_first);
+  if (lean.empty()) {
+    std::stable_sort(full.begin(), full.end(), heavy_first);
+  } else {
+    // problems by FEM work, heaviest first; both kernels take them in that order, z ascending
+    std::vector<long long> pc(ps.size(), 0);
+    for (const Slab &sl : full) pc[sl.q] += sl.cost;
+    std::vector<int> rank(ps.size());
+    std::vector<int> ord(ps.size());
+    for (size_t q = 0; q < ps.size(); ++q) ord[q] = (int)q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int l, int r) { return pc[l] > pc[r]; });
+    for (size_t i = 0; i < ord.size(); ++i) rank[ord[i]] = (int)i;
+    auto by_problem = [&](const Slab &l, const Slab &r) {
+      return rank[l.q] != rank[r.q] ? rank[l.q] < rank[r.q] : l.z0 < r.z0;
+    };
+    std::stable_sort(full.begin(), full.end(), by_problem);
+    std::stable_sort(lean.begin(), lean.end(), by_problem);
+  }
   std::vector<uint32_t> out;
   for (const Slab &sl : full)
     for (int ty = 0; ty < gy; ++ty)

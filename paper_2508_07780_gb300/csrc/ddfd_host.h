@@ -211,15 +211,17 @@ int dalloc(ddfd_problem *p, size_t bytes, void **out);
 void dfree(ddfd_problem *p, void *ptr);
 
 // Dispatch order of one step launch over the problems `ps` (stacked in that
-// order).  Full-kernel items first (their count in *n_full): z slabs (one
-// problem's z range over a set of its tile columns, in grid order within the
-// slab) sorted by an estimate of their work, heaviest first (node count, plus
-// twice the FEM rows and once the free nodes they hold), ties in order of
-// creation; FP64: every column in z chunks of kz; FP32: the columns that meet
-// the FEM cube's interior or the free box, over the z range of those boxes,
-// in chunks of kz.  Then (FP32) the lean-kernel items, problem by problem and
-// z chunk by z chunk (chunks of kz_lean from z = 0): every other column, and
-// the FEM columns' planes outside their full range.
+// order), in z slabs (one problem's z range over a set of its tile columns,
+// in grid order within the slab).  Full-kernel items first (their count in
+// *n_full).  FP64: every column in z chunks of kz, the slabs sorted by an
+// estimate of their work, heaviest first (node count, plus twice the FEM rows
+// and once the free nodes they hold), ties in order of creation.  FP32: the
+// columns that meet the FEM cube's interior or the free box, over the z range
+// of those boxes, in chunks of kz; then the lean-kernel items in chunks of
+// kz_lean from z = 0: every other column, and the FEM columns' planes outside
+// their full range.  Both FP32 kernels take the problems in the same order
+// (by their full-kernel work, heaviest first) and each problem's slabs in
+// ascending z, so that they stay near each other in time and share halos.
 std::vector<uint32_t> step_item_order(const std::vector<const ddfd_problem *> &ps, int kz, int kz_lean,
                                       int *n_full);
 // (Re)builds p->items for p->kz and p->kz_lean.
