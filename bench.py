@@ -118,7 +118,7 @@ def traffic_per_launch(*keys):
             if not line or line.startswith("#"):
                 continue
             k, v = line.split("=", 1)
-            vals[k.strip()] = v.strip()
+            vals[k.strip()] = v.split("#", 1)[0].strip()
         if vals.get("source_sha256_16") != src_hash:
             return None
         return float(sum(float(vals[k]) for k in keys))
