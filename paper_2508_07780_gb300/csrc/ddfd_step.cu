@@ -1,13 +1,18 @@
 // Explicit step kernels of the hybrid FE/FD scheme (forward and adjoint).
 //
-// Work decomposition: one CTA owns an (x, y) tile and a chunk of kz
-// consecutive z planes, which it marches through plane by plane.
+// Work decomposition: one CTA owns an (x, y) tile and a range of consecutive
+// z planes (a dispatch item, or a z chunk of the 3-D grid), which it marches
+// through plane by plane.
 //   - FP32 (k_step_pair): 32 x 16 tiles, 8 compute warps; each thread owns
 //     two x-adjacent nodes, whose arithmetic runs in packed FP32 (one
 //     instruction for both nodes); on a grid of n = 32 m + 1 nodes the last
-//     tile also updates the column x = n - 1.
+//     tile also updates the column x = n - 1.  One step is two launches side
+//     by side: the full kernel for the items that hold FEM-cube or free nodes
+//     (2 CTAs per SM) and the lean kernel, without the block stencil, the
+//     gradient or the coefficient stages, for the finite-difference items
+//     (3 CTAs per SM).
 //   - FP64 (k_step): 32 x 8 tiles, one node per thread, 8 compute warps and
-//     a producer warp.
+//     a producer warp, every tile on one kernel.
 // The planes of the current field (with a one-node halo in y and a
 // 16-byte-aligned halo in x), the centre tile of the previous level, and (on
 // tiles that touch the FEM cube) the coefficient planes are staged into
