@@ -199,3 +199,26 @@ def test_batch_state_errors():
         b.adjoint([np.zeros((1, w.n_steps + 1, 9, 3))] * 2)
     assert e.value.code == -3
     b.close()
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_lean_kernel_matches_the_full_kernel_bitwise(batched):
+    """FP32 steps split into the full kernel (FEM-cube and free tiles) and the
+    lean kernel (finite-difference tiles).  A tile depth beyond the dispatch
+    item packing (65 > 64 planes) runs every tile on the full kernel over the
+    3-D grid; the finite-difference nodes must come out bitwise the same."""
+    from paper_2508_07780_gb300 import Batch, Problem
+    ms = [(w.with_(n=65, n_steps=40, fem_n=f), s) for (w, s), f in zip(members(n=65, n_steps=40)[:3], (21, 33, 15))]
+    eobs = [0.01 * np.random.default_rng(i).standard_normal((1, 41, w.detectors().shape[0], 3))
+            for i, (w, _) in enumerate(ms)]
+    out = {}
+    for kz in (16, 65):
+        if batched:
+            b = Batch([problem_kwargs(w, "fp32", s, tile_kz=kz) for w, s in ms])
+            out[kz] = run_batch(b, ms, eobs)
+            b.close()
+        else:
+            out[kz] = [run_alone(w, "fp32", s, e, tile_kz=kz) for (w, s), e in zip(ms, eobs)]
+    for x, y in zip(out[16], out[65]):
+        assert np.array_equal(x[0], y[0]) and x[1] == y[1]
+        assert np.array_equal(x[2], y[2]) and np.array_equal(x[3], y[3])
