@@ -461,11 +461,18 @@ def run_batched(args, dev, stream, rank, world, peak):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    sampler2 = ClockSampler(dev.index) if rank == 0 else None
+    if sampler2:
+        sampler2.start()
+    e2e_iter = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
+        ti = time.perf_counter()
         step_e2e()
-    torch.cuda.synchronize(dev)
+        torch.cuda.synchronize(dev)
+        e2e_iter.append((time.perf_counter() - ti) * 1e3)
     e2e_s = (time.perf_counter() - t0) / args.steps
+    clocks_e2e = sampler2.stop() if sampler2 else None
     ntr = sum(int(np.prod(m.trace_shape)) for m in b.members)
     nfr = sum(m.n_free for m in b.members)
     h2d = 2 * nfr * 8 + 2 * ntr * 8
@@ -499,7 +506,8 @@ def run_batched(args, dev, stream, rank, world, peak):
     fwd_avg = fwd_ms / (args.steps * nt * n_groups)
     adj_avg = adj_ms / (args.steps * nt * n_groups)
     updates = sum(w.updates for w in ws)
-    res = dict(ms=ms, updates=updates, e2e_s=e2e_s, h2d=h2d, d2h=d2h, launches=launches, clocks=clocks,
+    res = dict(ms=ms, updates=updates, e2e_s=e2e_s, e2e_iter=e2e_iter, clocks_e2e=clocks_e2e, h2d=h2d, d2h=d2h,
+               launches=launches, clocks=clocks,
                kz=kz, dev_bytes=dev_bytes, out32=out32, probs=probs)
     res["roofline"] = {
         "bound": "hbm", "achieved": ab / (adj_avg / 1e3) / 1e9, "peak": peak[0], "unit": "GB/s",
@@ -779,7 +787,8 @@ def run_ours(args, rank, world, local_rank):
                        f"{world} GPUs, 16 independent problems each (problems 16 r .. 16 r + 15 on rank r), "
                        f"no data-path collective"},
             "e2e": {"value": world * bat["updates"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bat["h2d"],
-                    "d2h_bytes_per_step": bat["d2h"]},
+                    "d2h_bytes_per_step": bat["d2h"], "ms_per_step": e2e_s * 1e3,
+                    "ms_each_step": [round(v, 1) for v in bat["e2e_iter"]], "clocks": bat["clocks_e2e"]},
             "roofline": bat["roofline"],
             "gpu_launches": int(bat["launches"]),
             "clocks": bat["clocks"]}

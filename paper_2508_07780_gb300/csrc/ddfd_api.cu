@@ -686,19 +686,17 @@ int set_coeffs_impl(ddfd_problem *p, const double *eps, const double *sig, const
   const size_t nfb = (size_t)p->n_free * sizeof(double);
   CK(cudaMemcpyAsync(p->coef_stage, eps, nfb, kind, p->stream));
   CK(cudaMemcpyAsync(p->coef_stage + p->n_free, sig, nfb, kind, p->stream));
-  std::vector<double> fill;
-  if (!eps0 || !sig0) fill.assign((size_t)p->n_free, 0.0);
+  // default references eps0 = 1, sig0 = 0, filled on the device
   if (eps0) {
     CK(cudaMemcpyAsync(p->coef_stage + 2 * p->n_free, eps0, nfb, kind, p->stream));
   } else {
-    std::vector<double> ones((size_t)p->n_free, 1.0);
-    CK(cudaMemcpyAsync(p->coef_stage + 2 * p->n_free, ones.data(), nfb, cudaMemcpyHostToDevice, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
+    launch_fill(p->coef_stage + 2 * p->n_free, p->n_free, 1.0, p->stream);
+    ++p->launches;
   }
   if (sig0)
     CK(cudaMemcpyAsync(p->coef_stage + 3 * p->n_free, sig0, nfb, kind, p->stream));
   else
-    CK(cudaMemcpyAsync(p->coef_stage + 3 * p->n_free, fill.data(), nfb, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemsetAsync(p->coef_stage + 3 * p->n_free, 0, nfb, p->stream));
   CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream));
   launch_check_coeffs(p->coef_stage, (int)p->n_free, p->cfg.eps_max, p->cfg.sig_max, p->flag, p->stream);
   ++p->launches;

@@ -120,6 +120,17 @@ void launch_expand_new(int fp32, const double *coef_free, long long stride, long
     k_expand_new<double><<<blocks, 256, 0, s>>>(coef_free, stride, first, n_new, tau, (double *)xcoef);
 }
 
+__global__ void k_fill(double *x, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+void launch_fill(double *x, long long n, double v, cudaStream_t s) {
+  if (n <= 0) return;
+  const long long want = (n + 255) / 256;
+  k_fill<<<(int)(want < 1024 ? want : 1024), 256, 0, s>>>(x, n, v);
+}
+
 __global__ void k_check(const double *coef, int n_free, double eps_max, double sig_max, int *flag) {
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n_free; f += gridDim.x * blockDim.x) {
     const double e = coef[f], g = coef[n_free + f], e0 = coef[2 * n_free + f], g0 = coef[3 * n_free + f];

@@ -322,6 +322,8 @@ void launch_expand_coeffs(int fp32, const double *coef_free, int nf, int f0, int
 void launch_expand_new(int fp32, const double *coef_free, long long stride, long long first, int n_new,
                        double tau, void *xcoef, cudaStream_t s);
 void launch_coef_vacuum(int fp32, long long cs, void *coef, cudaStream_t s);
+// x[0, n) = v on the device (the default regularisation references).
+void launch_fill(double *x, long long n, double v, cudaStream_t s);
 void launch_check_coeffs(const double *coef_free, int n_free, double eps_max, double sig_max,
                          int *flag, cudaStream_t s);
 // residual r = tau z (trace - eobs) for n >= 1 (r[0] = 0); partial sums of
