@@ -395,14 +395,27 @@ def run_batched(args, dev, stream, rank, world, peak):
         b.autotune(steps=8)
     kz = (b.get_info().tile_kz, b.get_info().tile_kz_lean)
 
-    def step():
+    def mark(parts, name):  # optional per-call wall time (with a device sync), outside the timed steps
+        if parts is not None:
+            torch.cuda.synchronize(dev)
+            now = time.perf_counter()
+            parts[name] = round((now - parts.pop("_t", now)) * 1e3, 1)
+            parts["_t"] = now
+
+    def step(parts=None):
+        mark(parts, "start")
         for m, (e, s) in zip(b.members, coefs):
             m.set_coeffs_dev(e, s)
+        mark(parts, "set_coeffs")
         b.forward_dev(None)
+        mark(parts, "batch_forward")
         J = sum(m.functional_dev(e) for m, e in zip(b.members, eobs))
+        mark(parts, "functional")
         b.adjoint_dev(eobs)
+        mark(parts, "batch_adjoint")
         for m, (ge, gs) in zip(b.members, grads):
             m.gradient_dev(ge, gs)
+        mark(parts, "gradient")
         return J
 
     for _ in range(args.warmup):
@@ -441,20 +454,26 @@ def run_batched(args, dev, stream, rank, world, peak):
     lib = b._lib
     import ctypes
 
-    def step_e2e():
+    def step_e2e(parts=None):
+        mark(parts, "start")
         for m, (e, s) in zip(b.members, coefs_h):
             m._check(lib.ddfd_set_coeffs(m._h, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(s.data_ptr()),
                                          None, None))
+        mark(parts, "set_coeffs")
         b._check(lib.ddfd_batch_forward(b._h, None))
+        mark(parts, "batch_forward")
         J = 0.0
         for m, e in zip(b.members, eobs_h):
             Jm = ctypes.c_double()
             m._check(lib.ddfd_functional(m._h, ctypes.c_void_p(e.data_ptr()), ctypes.byref(Jm)))
             J += Jm.value
+        mark(parts, "functional")
         ptrs = (ctypes.c_void_p * len(eobs_h))(*[e.data_ptr() for e in eobs_h])
         b._check(lib.ddfd_batch_adjoint(b._h, ptrs))
+        mark(parts, "batch_adjoint")
         for m, (ge, gs) in zip(b.members, grads_h):
             m._check(lib.ddfd_gradient(m._h, ctypes.c_void_p(ge.data_ptr()), ctypes.c_void_p(gs.data_ptr())))
+        mark(parts, "gradient")
         return J
 
     step_e2e()
@@ -473,6 +492,21 @@ def run_batched(args, dev, stream, rank, world, peak):
         e2e_iter.append((time.perf_counter() - ti) * 1e3)
     e2e_s = (time.perf_counter() - t0) / args.steps
     clocks_e2e = sampler2.stop() if sampler2 else None
+    # the plain rate of a pinned host -> device copy in this process (torch), beside the calls' copies
+    probe_d = torch.empty_like(eobs_h[0], device=dev)
+    torch.cuda.synchronize(dev)
+    tc = time.perf_counter()
+    for e in eobs_h:
+        probe_d.copy_(e, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    host_copy_gbs = sum(e.numel() * 8 for e in eobs_h) / (time.perf_counter() - tc) / 1e9
+    del probe_d
+    e2e_parts, dev_parts = {}, {}
+    step_e2e(e2e_parts)  # one more of each, untimed, with a sync after each call
+    step(dev_parts)
+    for d in (e2e_parts, dev_parts):
+        d.pop("_t", None)
+        d.pop("start", None)
     ntr = sum(int(np.prod(m.trace_shape)) for m in b.members)
     nfr = sum(m.n_free for m in b.members)
     h2d = 2 * nfr * 8 + 2 * ntr * 8
@@ -506,7 +540,9 @@ def run_batched(args, dev, stream, rank, world, peak):
     fwd_avg = fwd_ms / (args.steps * nt * n_groups)
     adj_avg = adj_ms / (args.steps * nt * n_groups)
     updates = sum(w.updates for w in ws)
-    res = dict(ms=ms, updates=updates, e2e_s=e2e_s, e2e_iter=e2e_iter, clocks_e2e=clocks_e2e, h2d=h2d, d2h=d2h,
+    res = dict(ms=ms, updates=updates, e2e_s=e2e_s, e2e_iter=e2e_iter, clocks_e2e=clocks_e2e, e2e_parts=e2e_parts,
+               dev_parts=dev_parts, host_copy_gbs=host_copy_gbs,
+               h2d=h2d, d2h=d2h,
                launches=launches, clocks=clocks,
                kz=kz, dev_bytes=dev_bytes, out32=out32, probs=probs)
     res["roofline"] = {
@@ -788,7 +824,10 @@ def run_ours(args, rank, world, local_rank):
                        f"no data-path collective"},
             "e2e": {"value": world * bat["updates"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bat["h2d"],
                     "d2h_bytes_per_step": bat["d2h"], "ms_per_step": e2e_s * 1e3,
-                    "ms_each_step": [round(v, 1) for v in bat["e2e_iter"]], "clocks": bat["clocks_e2e"]},
+                    "ms_each_step": [round(v, 1) for v in bat["e2e_iter"]], "clocks": bat["clocks_e2e"],
+                    "ms_by_call_one_more_step": bat["e2e_parts"],
+                    "device_resident_ms_by_call_one_more_step": bat["dev_parts"],
+                    "torch_pinned_h2d_gbs": bat["host_copy_gbs"]},
             "roofline": bat["roofline"],
             "gpu_launches": int(bat["launches"]),
             "clocks": bat["clocks"]}
