@@ -630,24 +630,32 @@ def run_fp64_plain(args, dev, stream, probs, out32, fp64_peak):
 
 
 def run_single_201(args, dev, stream, peak):
-    """The one-source FP32 workload (201^3, FEM cube 101^3, 2000 steps) with
-    its FP64 counterpart: throughput, step-kernel rooflines and the FP32
-    errors against FP64, measured here."""
+    """One single-source FP32 workload (`--workload`, by default the 201^3 grid
+    with its 101^3 FEM cube and 2000 steps) with its FP64 counterpart:
+    throughput, step rooflines and the FP32 errors against FP64, measured
+    here.  `--snapshots K` checkpoints the FP32 run (K state snapshots, each
+    segment replayed) instead of keeping the E history; `--no-fp64` skips the
+    FP64 pass (its observed data still comes from an FP64 forward run)."""
     import torch
     from paper_2508_07780_gb300 import Problem
-    w = workload("c2_fp32_201", n_steps=args.single_steps)
+    w = workload(args.workload)
+    if args.single_steps:
+        w = w.with_(n_steps=args.single_steps)
     eps, sig = w.model()
     e_lay, s_lay = w.model(inclusions=False)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, src_dir=w.directions(), det_ij=w.detectors(),
               z_delta_frac=w.z_delta_frac, grad_variant=args.grad_variant, stream=stream.cuda_stream)
+    # observed data: the layers-only model's FP64 trace
+    q = Problem(precision="fp64", forward_only=1, **kw)
+    q.set_coeffs(e_lay, s_lay)
+    eobs = torch.empty(q.trace_shape, dtype=torch.float64, device=dev)
+    q.forward_dev(eobs)
+    q.close()
     out = {}
-    for prec in ("fp64", "fp32"):
-        p = Problem(precision=prec, **kw)
-        if prec == "fp64":
-            p.set_coeffs(e_lay, s_lay)
-            eobs = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
-            p.forward_dev(eobs)
+    for prec in ("fp32",) if args.no_fp64 else ("fp64", "fp32"):
+        extra = {"n_snapshots": args.snapshots} if prec == "fp32" and args.snapshots else {}
+        p = Problem(precision=prec, **kw, **extra)
         eps_d, sig_d = T(eps), T(sig)
         tr = torch.empty(p.trace_shape, dtype=torch.float64, device=dev)
         ge = torch.empty(p.n_free, dtype=torch.float64, device=dev)
@@ -662,7 +670,8 @@ def run_single_201(args, dev, stream, peak):
             return J
 
         reps = 1 if prec == "fp64" else max(args.steps, 3)
-        step()
+        for _ in range(1 if prec == "fp64" else max(args.warmup, 1)):
+            step()
         torch.cuda.synchronize(dev)
         fwd = adj = nk = 0.0
         e0 = torch.cuda.Event(enable_timing=True)
@@ -677,6 +686,8 @@ def run_single_201(args, dev, stream, peak):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
+        # per forward step; the adjoint sequence per adjoint step (with a
+        # replayed forward step in each when checkpointing)
         out[prec] = dict(ms=ms, fwd=fwd / nk, adj=adj / nk, trace=tr.cpu().numpy(), J=J,
                          g_eps=ge.cpu().numpy(), g_sig=gs.cpu().numpy(), bytes=p.get_info().device_bytes)
         p.close()
@@ -684,30 +695,41 @@ def run_single_201(args, dev, stream, peak):
     eo = eobs.cpu().numpy()
     del eobs
     torch.cuda.empty_cache()
-    a, b = out["fp32"], out["fp64"]
+    a = out["fp32"]
     fb, ab = algorithmic_bytes(w.n, w.fem_n, 4)
-    rn = float(np.linalg.norm(b["trace"] - eo))
-    kappa = float(np.linalg.norm(b["trace"]) / rn) if rn > 0 else None
-    return {"workload": describe(w), "gradient": args.grad_variant, "value": w.updates / (a["ms"] / 1e3), "unit": UNIT, "ms_per_step": a["ms"],
-            "device_bytes": int(a["bytes"]),
-            "roofline": {"bound": "hbm", "peak": peak[0], "unit": "GB/s",
-                         "forward": {"kernel": "k_step_pair<forward,1>, full and lean kernels side by side",
-                                     "avg_launch_ms": a["fwd"], "algorithmic_bytes_per_launch": fb,
-                                     "frac": fb / (a["fwd"] / 1e3) / 1e9 / peak[0],
-                                     "traffic": traffic_per_launch("single_forward_full_dram_bytes",
-                                                                   "single_forward_lean_dram_bytes")},
-                         "adjoint": {"kernel": "k_step_pair<adjoint,1>, full and lean kernels side by side",
-                                     "avg_launch_ms": a["adj"], "algorithmic_bytes_per_launch": ab,
-                                     "frac": ab / (a["adj"] / 1e3) / 1e9 / peak[0],
-                                     "traffic": traffic_per_launch("single_adjoint_full_dram_bytes",
-                                                                   "single_adjoint_lean_dram_bytes")}},
-            "fp64_plain": {"value": w.updates / (b["ms"] / 1e3), "ms_per_step": b["ms"],
-                           "fp32_speedup": b["ms"] / a["ms"]},
-            "accuracy_vs_fp64": {"trace": rel(a["trace"], b["trace"]),
-                                 "J": abs(a["J"] - b["J"]) / abs(b["J"]) if b["J"] != 0 else None,
-                                 "g_eps": rel(a["g_eps"], b["g_eps"]), "g_sig": rel(a["g_sig"], b["g_sig"]),
-                                 "kappa": kappa,
-                                 "observed_data": "the layers-only model's FP64 trace (unmodified)"}}
+    kernel_note = "full and lean kernels side by side"
+    res = {"workload": describe(w), "gradient": args.grad_variant, "value": w.updates / (a["ms"] / 1e3),
+           "unit": UNIT, "ms_per_step": a["ms"], "device_bytes": int(a["bytes"]),
+           "e_history": (f"checkpointed: {args.snapshots} state snapshots, each segment replayed"
+                         if args.snapshots else "kept in HBM for every step"),
+           "roofline": {"bound": "hbm", "peak": peak[0], "unit": "GB/s",
+                        "forward": {"kernel": f"k_step_pair<forward,1>, {kernel_note}", "avg_launch_ms": a["fwd"],
+                                    "algorithmic_bytes_per_launch": fb,
+                                    "frac": fb / (a["fwd"] / 1e3) / 1e9 / peak[0]}}}
+    if args.workload == "c2_fp32_201" and not args.snapshots:
+        res["roofline"]["forward"]["traffic"] = traffic_per_launch("single_forward_full_dram_bytes",
+                                                                   "single_forward_lean_dram_bytes")
+    if not args.snapshots:
+        res["roofline"]["adjoint"] = {"kernel": f"k_step_pair<adjoint,1>, {kernel_note}", "avg_launch_ms": a["adj"],
+                                      "algorithmic_bytes_per_launch": ab,
+                                      "frac": ab / (a["adj"] / 1e3) / 1e9 / peak[0]}
+        if args.workload == "c2_fp32_201":
+            res["roofline"]["adjoint"]["traffic"] = traffic_per_launch("single_adjoint_full_dram_bytes",
+                                                                       "single_adjoint_lean_dram_bytes")
+    else:
+        res["adjoint_sequence_ms_per_step"] = a["adj"]
+    if "fp64" in out:
+        b = out["fp64"]
+        rn = float(np.linalg.norm(b["trace"] - eo))
+        kappa = float(np.linalg.norm(b["trace"]) / rn) if rn > 0 else None
+        res["fp64_plain"] = {"value": w.updates / (b["ms"] / 1e3), "ms_per_step": b["ms"],
+                             "fp32_speedup": b["ms"] / a["ms"]}
+        res["accuracy_vs_fp64"] = {"trace": rel(a["trace"], b["trace"]),
+                                   "J": abs(a["J"] - b["J"]) / abs(b["J"]) if b["J"] != 0 else None,
+                                   "g_eps": rel(a["g_eps"], b["g_eps"]), "g_sig": rel(a["g_sig"], b["g_sig"]),
+                                   "kappa": kappa,
+                                   "observed_data": "the layers-only model's FP64 trace (unmodified)"}
+    return res
 
 
 def run_ebe(args, dev, stream, peak):
@@ -799,8 +821,18 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     peak = measured_peaks()
     single = None
-    if world == 1 and not args.no_single:
+    if world == 1 and (not args.no_single or args.no_batched):
         single = run_single_201(args, dev, stream, peak)
+    if args.no_batched:
+        # an auxiliary run of the single-source leg alone (not the headline workload)
+        if rank == 0:
+            line = {"metric": METRIC, "value": single["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": single["ms_per_step"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                    "config": {"workload": single["workload"], "leg": "single source only (--no-batched)"},
+                    "single": single}
+            print(json.dumps(line), flush=True)
+        return
     bat = run_batched(args, dev, stream, rank, world, peak)
     ms_t = torch.tensor([bat["ms"], bat["e2e_s"]], device=dev)
     if world > 1:
@@ -865,10 +897,16 @@ def main():
                          "(default) or the paper-literal one of Sec. 4")
     ap.add_argument("--no-refined", action="store_true", help="skip the refined-mesh element-gather leg")
     ap.add_argument("--cpu-workers", type=int, default=min(8, os.cpu_count() or 1))
+    ap.add_argument("--no-batched", action="store_true",
+                    help="run only the single-source leg (an auxiliary measurement, not the headline)")
+    ap.add_argument("--workload", default="c2_fp32_201", help="the single-source leg's workload (synth)")
+    ap.add_argument("--snapshots", type=int, default=0,
+                    help="the single-source FP32 run checkpoints with this many state snapshots")
     ap.add_argument("--batch-kz", default="auto",
                     help="z depths 'FULL,LEAN' of the batched step kernels, or 'auto' (autotuned)")
-    ap.add_argument("--single-steps", type=int, default=2000,
-                    help="time steps of the single-source 201^3 workload (2000; fewer only for profiler captures)")
+    ap.add_argument("--single-steps", type=int, default=0,
+                    help="time steps of the single-source workload (0: its own, 2000 for the 201^3 one; "
+                         "fewer only for profiler captures)")
     ap.add_argument("--batch-steps", type=int, default=1600,
                     help="time steps of the batched workload (1600; fewer only for profiler captures: "
                          "every step launch does the same work at any step count)")
