@@ -647,7 +647,7 @@ def run_single_201(args, dev, stream, peak):
     kw = dict(n=w.n, fem_n=w.fem_n, n_steps=w.n_steps, cfl=w.cfl, src_dir=w.directions(), det_ij=w.detectors(),
               z_delta_frac=w.z_delta_frac, grad_variant=args.grad_variant, stream=stream.cuda_stream)
     # observed data: the layers-only model's FP64 trace
-    q = Problem(precision="fp64", forward_only=1, **kw)
+    q = Problem(precision="fp64", forward_only=1, **dict(kw, grad_variant="exact"))
     q.set_coeffs(e_lay, s_lay)
     eobs = torch.empty(q.trace_shape, dtype=torch.float64, device=dev)
     q.forward_dev(eobs)
