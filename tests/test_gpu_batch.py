@@ -222,3 +222,26 @@ def test_lean_kernel_matches_the_full_kernel_bitwise(batched):
     for x, y in zip(out[16], out[65]):
         assert np.array_equal(x[0], y[0]) and x[1] == y[1]
         assert np.array_equal(x[2], y[2]) and np.array_equal(x[3], y[3])
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_odd_tile_depths_change_no_bit(batched):
+    """Dispatch items of odd depths (5 planes on the full kernel, 3 on the lean
+    one) cut the FEM columns' z ranges and the other columns at other planes;
+    every node must still come out bitwise as with the default depths."""
+    from paper_2508_07780_gb300 import Batch
+    ms = [(w.with_(n_steps=30), s) for w, s in members(n=33, n_steps=30)[:3]]
+    eobs = [0.01 * np.random.default_rng(7 + i).standard_normal((1, 31, w.detectors().shape[0], 3))
+            for i, (w, _) in enumerate(ms)]
+    out = {}
+    for kz in ((0, 0), (5, 3)):
+        kw = dict(tile_kz=kz[0], tile_kz_lean=kz[1])
+        if batched:
+            b = Batch([problem_kwargs(w, "fp32", s, **kw) for w, s in ms])
+            out[kz] = run_batch(b, ms, eobs)
+            b.close()
+        else:
+            out[kz] = [run_alone(w, "fp32", s, e, **kw) for (w, s), e in zip(ms, eobs)]
+    for x, y in zip(out[(0, 0)], out[(5, 3)]):
+        assert np.array_equal(x[0], y[0]) and x[1] == y[1]
+        assert np.array_equal(x[2], y[2]) and np.array_equal(x[3], y[3])
